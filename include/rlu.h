@@ -1,0 +1,170 @@
+/*
+ * rlu.h — C ABI of the GB300 sparse randomized LU library (librlu.so).
+ *
+ * The library computes a rank-k LU factorization P A Q ~= L U of an m x n
+ * matrix A (dense row-major, or CSR) with the method of Aizenbud, Shabat and
+ * Averbuch, "Randomized LU decomposition using sparse projections"
+ * (arXiv 1601.04280): the problem statement of Sec. 1 (Eq. (1): find L m x k
+ * lower, U k x n upper and permutations P, Q with ||LU - PAQ||_F = O(Delta_r))
+ * and Algorithm 1 (Sec. 3), with the second projection of step 5 replaced by
+ * the exact pseudo-inverse of Corollary 3.3 (col:A_LLA):
+ *
+ *   1. draw the sparse embedding matrix S (Sec. 2.2: hash h, signs s) and the
+ *      real FFT-based projection (Sec. 2.1: signs d, Hartley transform, a
+ *      subsample R of l of the l1 outputs) from a counter-based generator;
+ *   2. Y = A S D H R / sqrt(l1)                     (m x l sketch, step 2);
+ *   3. P Y = L_Y U_Y, partial (row) pivoting;      L_y = L_Y[:, :k] (step 3);
+ *   4. B = L_y^+ P A                                (k x n, Corollary 3.3);
+ *   5. B Q = L_b U_b, right (column) pivoting       (step 6);
+ *   6. L = L_y L_b, U = U_b                         (step 7).
+ *
+ * Every step runs in the library's own CUDA kernels for sm_103a on the
+ * caller's stream.  There is no CPU fallback: without a usable GPU every
+ * compute entry point returns RLU_ECUDA.
+ *
+ * Conventions for every entry point
+ *   - Return value: an rlu_status code (0 = success).  No entry point aborts,
+ *     traps or prints.  RLU_WRANK is a warning: the factors are valid.
+ *   - Pointers named "device" must be device memory of the current CUDA
+ *     device (for example from torch or cudaMalloc); the caller owns them and
+ *     keeps them alive until the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Matrices are row-major with 0-based indices.  (PA)[i,:] = A[p[i],:] and
+ *     (AQ)[:,j] = A[:,q[j]].
+ */
+#ifndef RLU_H_
+#define RLU_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlu_ctx* rlu_t; /* opaque; owns every device workspace of a factorization */
+
+typedef enum {
+  RLU_OK = 0,
+  RLU_EINVAL = 1,     /* invalid argument (sizes, dtype, null pointer); nothing was launched */
+  RLU_ENOMEM = 2,     /* workspace allocation failed */
+  RLU_ECUDA = 3,      /* a CUDA call failed, or no usable GPU */
+  RLU_ETIMEOUT = 4,   /* a bounded device wait gave up (co-residency lost); outputs undefined */
+  RLU_ENONFINITE = 5, /* A holds NaN or Inf; outputs undefined */
+  RLU_EBADCSR = 6,    /* CSR structure invalid (found on the device); outputs undefined */
+  RLU_WRANK = 100     /* warning: an exactly zero pivot was met (rank deficiency); outputs valid */
+} rlu_status;
+
+/* Storage type of A's values. */
+typedef enum { RLU_F64 = 0, RLU_F32 = 1, RLU_BF16 = 2 } rlu_dtype;
+
+/* Arithmetic of the path.  In every mode the pivoted LU of the sketch and the
+ * Gram / Cholesky / triangular solve that form L_y^+ run in FP64.
+ *   RLU_PREC_F64:         sketch, B = L_y^+ P A, LU of B and L in FP64; outputs f64.
+ *   RLU_PREC_F32:         sketch and LU of B in FP32, B = L_y^+ P A with FP32
+ *                         accuracy (three-pass TF32 split); outputs f32.
+ *   RLU_PREC_BF16:        B from one BF16 pass (L_y^+ rounded to BF16, FP32 accumulate).
+ *   RLU_PREC_BF16_REFINE: B from L_y^+ split into BF16 hi + lo parts (two
+ *                         passes, FP32 accumulate): the one-step refinement of B. */
+typedef enum { RLU_PREC_F64 = 0, RLU_PREC_F32 = 1, RLU_PREC_BF16 = 2, RLU_PREC_BF16_REFINE = 3 } rlu_prec;
+
+/* Create a handle for m x n inputs, output rank k, FJL width l and CountSketch
+ * width l1 (Algorithm 1, step 1: k plays the role of the output rank, l of k1,
+ * l1 of l1).  Requires 1 <= k <= l <= l1, l <= m, k <= min(m, n), m and n
+ * below 2^31, l <= 1024 and l1 <= 16384.  l1 > n is allowed (empty buckets
+ * stay zero).  `seed` fixes S, D and R: two calls with the same seed draw the
+ * same projection.  Allocates the device workspace (see rlu_workspace_bytes)
+ * on the current device; the default precision is RLU_PREC_F32.
+ * Errors: RLU_EINVAL for bad sizes or a null `out`, RLU_ENOMEM, RLU_ECUDA. */
+int rlu_create(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t seed, rlu_t* out);
+
+/* Select the arithmetic (rlu_prec).  Valid at any time between calls. */
+int rlu_set_precision(rlu_t h, int prec);
+
+/* Device bytes that rlu_create allocates for these sizes and precision
+ * (for admission by HBM footprint).  Errors: RLU_EINVAL. */
+int rlu_workspace_bytes(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, int prec, size_t* bytes);
+
+/* Factor dense A.
+ *   A:  device, m x n row-major values of type `dtype`, leading dimension
+ *       lda >= n (elements).  Not modified.
+ *   L:  device, m x k row-major, rows in P order, lower trapezoidal; f64 for
+ *       RLU_PREC_F64, else f32.
+ *   U:  device, k x n row-major, columns in Q order, unit upper trapezoidal
+ *       with |U| <= 1; same type as L.
+ *   p:  device, m int64: the row permutation.   q: device, n int64.
+ * Enqueues the whole path on `stream`, waits for it, and returns the status.
+ * The precision must match the dtype: RLU_PREC_F64 needs RLU_F64; the BF16
+ * precisions need RLU_BF16; RLU_PREC_F32 takes RLU_F32 or RLU_BF16.
+ * Errors: RLU_EINVAL (before any launch), RLU_ENONFINITE, RLU_ETIMEOUT,
+ * RLU_ECUDA; warning RLU_WRANK. */
+int rlu_factor_dense(rlu_t h, const void* A, int64_t lda, int dtype, void* L, void* U, int64_t* p, int64_t* q,
+                     void* stream);
+
+/* As rlu_factor_dense, but returns right after enqueueing: the status bits
+ * (0 = success, else an rlu_status code) are written to `status_dev`
+ * (device, one int32) on `stream`.  Launch-only: usable under CUDA graph
+ * capture once the handle has run one factorization of the same dtype. */
+int rlu_factor_dense_async(rlu_t h, const void* A, int64_t lda, int dtype, void* L, void* U, int64_t* p,
+                           int64_t* q, int32_t* status_dev, void* stream);
+
+/* Factor CSR A (m x n, nnz entries).
+ *   rowptr: device, m+1 int64, rowptr[0] = 0, non-decreasing, rowptr[m] = nnz.
+ *   colind: device, nnz int32 in [0, n).  Order within a row is free.
+ *   val:    device, nnz values of type `dtype` (RLU_F32 or RLU_F64).
+ * Outputs as rlu_factor_dense.  The structure is validated on the device
+ * (RLU_EBADCSR).  Errors as rlu_factor_dense. */
+int rlu_factor_csr(rlu_t h, const int64_t* rowptr, const int32_t* colind, const void* val, int64_t nnz, int dtype,
+                   void* L, void* U, int64_t* p, int64_t* q, void* stream);
+
+/* End-to-end variant of rlu_factor_dense on HOST buffers: copies A (host,
+ * m x n row-major, lda = n) to a device staging buffer owned by the handle
+ * (allocated on first use), factors it, and copies L, U, p, q back to the
+ * host buffers.  Host buffers should be page-locked for full copy speed. */
+int rlu_factor_dense_host(rlu_t h, const void* A_host, int dtype, void* L_host, void* U_host, int64_t* p_host,
+                          int64_t* q_host, void* stream);
+
+/* Release the handle and its workspace.  Null is accepted. */
+int rlu_destroy(rlu_t h);
+
+/* Static message for a status code. */
+const char* rlu_strerror(int code);
+
+/* ---- test hooks: copies of intermediates of the last factorization ---- */
+
+/* Sketch parameters (Sec. 2.2 and 2.1): hash h (n int32), signs s (n int8),
+ * signs d (l1 int8), subsample R (l int32).  Host buffers; synchronizes. */
+int rlu_debug_sketch_params(rlu_t h, int32_t* hash, int8_t* s, int8_t* d, int32_t* R);
+
+/* The sketch Y (m x l row-major f64) as written by the sketch kernel, before
+ * the panel LU overwrote it (kept only when debug capture is enabled with
+ * rlu_debug_enable(h, 1) before the factorization).  Host buffer. */
+int rlu_debug_Y(rlu_t h, double* Y_host);
+
+/* B = L_y^+ P A (k x n row-major, f64 on the host) as formed before its LU
+ * (also needs rlu_debug_enable). */
+int rlu_debug_B(rlu_t h, double* B_host);
+
+/* Keep copies of Y and B during factorizations (costs device memory and time). */
+int rlu_debug_enable(rlu_t h, int on);
+
+/* Record CUDA events on the factorization stream between the stages of the
+ * path (on = 1) so that rlu_debug_stage_ms can report their device times. */
+int rlu_debug_timing(rlu_t h, int on);
+
+/* Device milliseconds of the stages of the last factorization, in order:
+ * 0 sketch parameters and bucket lists, 1 sketch (CountSketch + FFT),
+ * 2 panel LU of Y, 3 Lk and Gram matrix, 4 Cholesky and R^{-1},
+ * 5 G^{-1} and W = L_y^+ P, 6 B = W A, 7 LU of B, 8 assembly of L, U, p, q.
+ * Writes min(max_stages, 9) values and their number to *count; waits for the
+ * last factorization to finish.  Errors: RLU_EINVAL if timing was off. */
+int rlu_debug_stage_ms(rlu_t h, float* ms, int max_stages, int* count);
+
+/* Number of CUDA kernels this library has launched in this process so far. */
+int rlu_debug_launch_count(int64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLU_H_ */

@@ -143,6 +143,7 @@ class LUResult:
     perm: np.ndarray  # (m,) int64: row i of the permuted input is input row perm[i]
     zero_pivot: bool  # an exactly zero pivot column was met
     gaps: np.ndarray  # (steps,) relative gap between the two largest candidates
+    top: np.ndarray = None  # (steps, 2) the two largest candidate magnitudes
 
 
 def lu_partial_pivot(X, steps=None):
@@ -154,7 +155,8 @@ def lu_partial_pivot(X, steps=None):
     is divided by it, and the trailing block receives the rank-1 update.  An
     exactly zero pivot skips the division (the column is zero anyway) and is
     reported.  The `gaps` record, per step, (top1 - top2) / top1 of the
-    candidate magnitudes, so that callers can tell well-separated pivots.
+    candidate magnitudes and `top` the two magnitudes themselves, so that
+    callers can tell well-separated pivots.
     """
     X = np.array(X, dtype=np.float64, copy=True)
     m, n = X.shape
@@ -162,6 +164,7 @@ def lu_partial_pivot(X, steps=None):
         steps = min(m, n)
     perm = np.arange(m, dtype=np.int64)
     gaps = np.zeros(steps)
+    top = np.zeros((steps, 2))
     zero_pivot = False
     for j in range(steps):
         col = np.abs(X[j:, j])
@@ -170,8 +173,10 @@ def lu_partial_pivot(X, steps=None):
             top2 = np.partition(col, col.size - 2)[-2:]
             t1, t2 = top2[1], top2[0]
             gaps[j] = (t1 - t2) / t1 if t1 > 0 else 0.0
+            top[j] = (t1, t2)
         else:
             gaps[j] = 1.0
+            top[j] = (col[0], 0.0)
         if pj != j:
             X[[j, pj], :] = X[[pj, j], :]
             perm[[j, pj]] = perm[[pj, j]]
@@ -181,7 +186,7 @@ def lu_partial_pivot(X, steps=None):
             X[j + 1:, j + 1:] -= np.outer(X[j + 1:, j], X[j, j + 1:])
         else:
             zero_pivot = True
-    return LUResult(lu=X, perm=perm, zero_pivot=zero_pivot, gaps=gaps)
+    return LUResult(lu=X, perm=perm, zero_pivot=zero_pivot, gaps=gaps, top=top)
 
 
 def unit_lower(lu, k):
@@ -229,6 +234,8 @@ class OracleResult:
     Ub: np.ndarray      # k x n unit upper
     gaps_y: np.ndarray  # pivot separation of the panel LU
     gaps_b: np.ndarray  # pivot separation of the LU of B
+    top_y: np.ndarray = None  # (l, 2) two largest candidate magnitudes per step
+    top_b: np.ndarray = None  # (k, 2)
 
 
 def check_sizes(m, n, k, l, l1):
@@ -273,7 +280,7 @@ def factor(A, k, l, l1, seed):
     L = Ly @ Lb
     return OracleResult(L=L, U=Ub, p=p, q=q, status=status, params=params,
                         Y=Y, Ly=Ly, W=W, B=B, Lb=Lb, Ub=Ub,
-                        gaps_y=ly.gaps, gaps_b=lb.gaps)
+                        gaps_y=ly.gaps, gaps_b=lb.gaps, top_y=ly.top, top_b=lb.top)
 
 
 def relative_residual(A, L, U, p, q):

@@ -1,0 +1,265 @@
+"""Python binding of librlu.so, the GB300 sparse randomized LU library.
+
+Argument marshalling only: every step of the factorization runs in the
+library's CUDA kernels.  torch supplies device memory and streams.  The
+functions mirror the C ABI in include/rlu.h (same names, same order of
+arguments); `RandLU` is a small convenience wrapper over them.
+
+If librlu.so has not been built (see `build`), importing works but every
+call raises RuntimeError: there is no CPU fallback.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librlu.so")
+
+RLU_OK, RLU_EINVAL, RLU_ENOMEM, RLU_ECUDA, RLU_ETIMEOUT, RLU_ENONFINITE, RLU_EBADCSR = 0, 1, 2, 3, 4, 5, 6
+RLU_WRANK = 100
+RLU_F64, RLU_F32, RLU_BF16 = 0, 1, 2
+RLU_PREC_F64, RLU_PREC_F32, RLU_PREC_BF16, RLU_PREC_BF16_REFINE = 0, 1, 2, 3
+PREC = {"f64": RLU_PREC_F64, "f32": RLU_PREC_F32, "bf16": RLU_PREC_BF16, "bf16_refine": RLU_PREC_BF16_REFINE}
+
+#: every entry point declared in include/rlu.h
+C_SYMBOLS = ("rlu_create", "rlu_set_precision", "rlu_workspace_bytes", "rlu_factor_dense",
+             "rlu_factor_dense_async", "rlu_factor_csr", "rlu_factor_dense_host", "rlu_destroy",
+             "rlu_strerror", "rlu_debug_sketch_params", "rlu_debug_Y", "rlu_debug_B", "rlu_debug_enable",
+             "rlu_debug_timing", "rlu_debug_stage_ms", "rlu_debug_launch_count")
+
+#: stage names reported by rlu_debug_stage_ms, in order
+STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
+
+_lib = None
+
+
+def build(force=False):
+    """Compile librlu.so for sm_103a (in-tree) and load it."""
+    from . import _build
+    _build.build(force=force)
+    return load(reload=True)
+
+
+def load(reload=False):
+    global _lib
+    if _lib is not None and not reload:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("librlu.so is not built; run paper_1601_04280_gb300.build() (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    c = ctypes
+    vp, i64, i32, u64 = c.c_void_p, c.c_int64, c.c_int32, c.c_uint64
+    sig = {
+        "rlu_create": ([i64, i64, i32, i32, i32, u64, c.POINTER(vp)], c.c_int),
+        "rlu_set_precision": ([vp, c.c_int], c.c_int),
+        "rlu_workspace_bytes": ([i64, i64, i32, i32, i32, c.c_int, c.POINTER(c.c_size_t)], c.c_int),
+        "rlu_factor_dense": ([vp, vp, i64, c.c_int, vp, vp, vp, vp, vp], c.c_int),
+        "rlu_factor_dense_async": ([vp, vp, i64, c.c_int, vp, vp, vp, vp, vp, vp], c.c_int),
+        "rlu_factor_csr": ([vp, vp, vp, vp, i64, c.c_int, vp, vp, vp, vp, vp], c.c_int),
+        "rlu_factor_dense_host": ([vp, vp, c.c_int, vp, vp, vp, vp, vp], c.c_int),
+        "rlu_destroy": ([vp], c.c_int),
+        "rlu_strerror": ([c.c_int], c.c_char_p),
+        "rlu_debug_sketch_params": ([vp, vp, vp, vp, vp], c.c_int),
+        "rlu_debug_Y": ([vp, vp], c.c_int),
+        "rlu_debug_B": ([vp, vp], c.c_int),
+        "rlu_debug_enable": ([vp, c.c_int], c.c_int),
+        "rlu_debug_timing": ([vp, c.c_int], c.c_int),
+        "rlu_debug_stage_ms": ([vp, vp, c.c_int, c.POINTER(c.c_int)], c.c_int),
+        "rlu_debug_launch_count": ([c.POINTER(i64)], c.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+class RluError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (status %d)" % (where, strerror(code), code))
+
+
+def strerror(code):
+    return load().rlu_strerror(int(code)).decode()
+
+
+def _check(code, where, allow_warn=True):
+    if code == RLU_OK or (allow_warn and code == RLU_WRANK):
+        return code
+    raise RluError(code, where)
+
+
+# ---- C-ABI mirrors -----------------------------------------------------------
+def rlu_create(m, n, k, l, l1, seed):
+    h = ctypes.c_void_p()
+    _check(load().rlu_create(m, n, k, l, l1, ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(h)), "rlu_create")
+    return h
+
+
+def rlu_set_precision(h, prec):
+    return _check(load().rlu_set_precision(h, PREC.get(prec, prec)), "rlu_set_precision")
+
+
+def rlu_workspace_bytes(m, n, k, l, l1, prec):
+    out = ctypes.c_size_t()
+    _check(load().rlu_workspace_bytes(m, n, k, l, l1, PREC.get(prec, prec), ctypes.byref(out)), "rlu_workspace_bytes")
+    return out.value
+
+
+def rlu_factor_dense(h, A_ptr, lda, dtype, L_ptr, U_ptr, p_ptr, q_ptr, stream_ptr):
+    return load().rlu_factor_dense(h, A_ptr, lda, dtype, L_ptr, U_ptr, p_ptr, q_ptr, stream_ptr)
+
+
+def rlu_factor_dense_async(h, A_ptr, lda, dtype, L_ptr, U_ptr, p_ptr, q_ptr, status_ptr, stream_ptr):
+    return load().rlu_factor_dense_async(h, A_ptr, lda, dtype, L_ptr, U_ptr, p_ptr, q_ptr, status_ptr, stream_ptr)
+
+
+def rlu_factor_csr(h, rowptr_ptr, colind_ptr, val_ptr, nnz, dtype, L_ptr, U_ptr, p_ptr, q_ptr, stream_ptr):
+    return load().rlu_factor_csr(h, rowptr_ptr, colind_ptr, val_ptr, nnz, dtype, L_ptr, U_ptr, p_ptr, q_ptr,
+                                 stream_ptr)
+
+
+def rlu_factor_dense_host(h, A_ptr, dtype, L_ptr, U_ptr, p_ptr, q_ptr, stream_ptr):
+    return load().rlu_factor_dense_host(h, A_ptr, dtype, L_ptr, U_ptr, p_ptr, q_ptr, stream_ptr)
+
+
+def rlu_destroy(h):
+    return load().rlu_destroy(h)
+
+
+def rlu_debug_launch_count():
+    out = ctypes.c_int64()
+    _check(load().rlu_debug_launch_count(ctypes.byref(out)), "rlu_debug_launch_count")
+    return out.value
+
+
+# ---- convenience wrapper (torch tensors) ---------------------------------------
+@dataclass
+class Factors:
+    L: object
+    U: object
+    p: object
+    q: object
+    status: int
+
+
+def _dtype_code(t):
+    import torch
+    return {torch.float64: RLU_F64, torch.float32: RLU_F32, torch.bfloat16: RLU_BF16}[t.dtype]
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class RandLU:
+    """One handle: fixed sizes, seed and precision; reusable across calls."""
+
+    def __init__(self, m, n, k, l, l1, seed, prec="f32"):
+        self.m, self.n, self.k, self.l, self.l1, self.seed = m, n, k, l, l1, seed
+        self.h = rlu_create(m, n, k, l, l1, seed)
+        self.prec = prec
+        rlu_set_precision(self.h, prec)
+
+    @property
+    def out_dtype(self):
+        import torch
+        return torch.float64 if self.prec == "f64" else torch.float32
+
+    def alloc_outputs(self, device="cuda"):
+        import torch
+        L = torch.empty((self.m, self.k), dtype=self.out_dtype, device=device)
+        U = torch.empty((self.k, self.n), dtype=self.out_dtype, device=device)
+        p = torch.empty(self.m, dtype=torch.int64, device=device)
+        q = torch.empty(self.n, dtype=torch.int64, device=device)
+        return L, U, p, q
+
+    def factor(self, A, out=None, stream=None, check=True):
+        assert A.is_cuda and A.dim() == 2 and A.shape == (self.m, self.n) and A.stride(1) == 1
+        L, U, p, q = out if out is not None else self.alloc_outputs(A.device)
+        code = rlu_factor_dense(self.h, ctypes.c_void_p(A.data_ptr()), A.stride(0), _dtype_code(A),
+                                ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(U.data_ptr()),
+                                ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(q.data_ptr()), _stream_ptr(stream))
+        if check:
+            _check(code, "rlu_factor_dense")
+        return Factors(L, U, p, q, code)
+
+    def factor_async(self, A, out, status, stream=None):
+        L, U, p, q = out
+        code = rlu_factor_dense_async(self.h, ctypes.c_void_p(A.data_ptr()), A.stride(0), _dtype_code(A),
+                                      ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(U.data_ptr()),
+                                      ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                      ctypes.c_void_p(status.data_ptr()), _stream_ptr(stream))
+        return _check(code, "rlu_factor_dense_async", allow_warn=False)
+
+    def factor_csr(self, rowptr, colind, val, out=None, stream=None, check=True):
+        L, U, p, q = out if out is not None else self.alloc_outputs(val.device)
+        code = rlu_factor_csr(self.h, ctypes.c_void_p(rowptr.data_ptr()), ctypes.c_void_p(colind.data_ptr()),
+                              ctypes.c_void_p(val.data_ptr()), val.numel(), _dtype_code(val),
+                              ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(U.data_ptr()),
+                              ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(q.data_ptr()), _stream_ptr(stream))
+        if check:
+            _check(code, "rlu_factor_csr")
+        return Factors(L, U, p, q, code)
+
+    def factor_host(self, A_host, out_host, stream=None, check=True):
+        """A_host, outputs: CPU tensors (pinned for full copy speed)."""
+        L, U, p, q = out_host
+        code = rlu_factor_dense_host(self.h, ctypes.c_void_p(A_host.data_ptr()), _dtype_code(A_host),
+                                     ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(U.data_ptr()),
+                                     ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                     _stream_ptr(stream))
+        if check:
+            _check(code, "rlu_factor_dense_host")
+        return Factors(L, U, p, q, code)
+
+    def debug_enable(self, on=True):
+        _check(load().rlu_debug_enable(self.h, 1 if on else 0), "rlu_debug_enable")
+
+    def debug_timing(self, on=True):
+        _check(load().rlu_debug_timing(self.h, 1 if on else 0), "rlu_debug_timing")
+
+    def debug_stage_ms(self):
+        import numpy as np
+        ms = np.zeros(len(STAGES), np.float32)
+        cnt = ctypes.c_int()
+        _check(load().rlu_debug_stage_ms(self.h, ms.ctypes.data, len(STAGES), ctypes.byref(cnt)),
+               "rlu_debug_stage_ms")
+        return dict(zip(STAGES, ms[: cnt.value].tolist()))
+
+    def debug_sketch_params(self):
+        import numpy as np
+        h = np.empty(self.n, np.int32)
+        s = np.empty(self.n, np.int8)
+        d = np.empty(self.l1, np.int8)
+        R = np.empty(self.l, np.int32)
+        _check(load().rlu_debug_sketch_params(self.h, h.ctypes.data, s.ctypes.data, d.ctypes.data, R.ctypes.data),
+               "rlu_debug_sketch_params")
+        return h, s, d, R
+
+    def debug_Y(self):
+        import numpy as np
+        Y = np.empty((self.m, self.l), np.float64)
+        _check(load().rlu_debug_Y(self.h, Y.ctypes.data), "rlu_debug_Y")
+        return Y
+
+    def debug_B(self):
+        import numpy as np
+        B = np.empty((self.k, self.n), np.float64)
+        _check(load().rlu_debug_B(self.h, B.ctypes.data), "rlu_debug_B")
+        return B
+
+    def close(self):
+        if getattr(self, "h", None):
+            rlu_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

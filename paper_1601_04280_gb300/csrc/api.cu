@@ -1,0 +1,498 @@
+// C ABI of the sparse randomized LU library: handle, workspace and the
+// orchestration of Algorithm 1 (with the exact L_y^+ of Corollary 3.3) on
+// one CUDA stream.  See include/rlu.h for the contract of each entry point.
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "pinv.cuh"
+#include "pivlu.cuh"
+#include "sketch.cuh"
+
+using namespace rlu;
+
+namespace rlu {
+static std::atomic<long long> g_launches{0};
+void note_launch(int count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+}  // namespace rlu
+
+// Stages whose device time the timing hook reports, in order.
+static const int kNumStages = 9;
+
+struct rlu_ctx {
+  int64_t m = 0, n = 0;
+  int k = 0, l = 0, l1 = 0;
+  uint64_t seed = 0;
+  int prec = RLU_PREC_F32;
+  int device = 0;
+  int num_sms = 0;
+  SketchWs sk{};
+  double* Y = nullptr;
+  PivLuWs pw{};
+  int64_t* perm_y = nullptr;
+  int64_t* perm_b = nullptr;
+  double* Lk = nullptr;
+  double* gram_part = nullptr;
+  int max_gram_splits = 0;
+  double* G = nullptr;
+  double* Rinv = nullptr;
+  double* Ginv = nullptr;
+  void* W = nullptr;
+  void* B = nullptr;
+  void* LyP = nullptr;
+  void* Lb = nullptr;
+  unsigned int* status_dev = nullptr;
+  unsigned int* bar2 = nullptr;
+  unsigned int* status_host = nullptr;  // pinned
+  int debug = 0;
+  double* Ydbg = nullptr;
+  void* Bdbg = nullptr;
+  int last_prec = -1;
+  // host-buffer entry point staging
+  void* A_stage = nullptr;
+  size_t A_stage_bytes = 0;
+  void* L_stage = nullptr;
+  void* U_stage = nullptr;
+  int64_t* p_stage = nullptr;
+  int64_t* q_stage = nullptr;
+  // per-stage device timing (test hook)
+  int timing = 0;
+  cudaEvent_t ev[kNumStages + 1] = {};
+  int ev_recorded = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+constexpr int kMaxL = 1024;
+constexpr int kMaxL1 = 16384;
+constexpr int kMaxPivCtas = 1024;
+
+struct Sizes {
+  size_t total = 0;
+  std::vector<size_t> parts;
+  void add(size_t b) {
+    b = (b + 255) & ~(size_t)255;
+    parts.push_back(b);
+    total += b;
+  }
+};
+
+int max_gram_splits_for(int k, int num_sms) {
+  int64_t tiles = cdiv(k, 64) * cdiv(k, 64);
+  int64_t s = cdiv(2 * (int64_t)num_sms, tiles);
+  return (int)(s < 1 ? 1 : s);
+}
+
+// The order of `add` calls is the allocation order in rlu_create.
+Sizes plan_sizes(int64_t m, int64_t n, int k, int l, int l1, int num_sms) {
+  Sizes s;
+  const int64_t nch = cdiv(n, 2048);  // smallest chunk of the dense sketch
+  s.add(sizeof(uint32_t) * n);                       // hs
+  s.add(sizeof(float) * l1);                         // dsign
+  s.add(sizeof(uint64_t) * l1);                      // keys
+  s.add(sizeof(int32_t) * l);                        // R
+  s.add(sizeof(int32_t) * (nch * l1 + 1));           // bcnt
+  s.add(sizeof(int32_t) * (nch * l1 + 1));           // bstart
+  s.add(sizeof(uint32_t) * n);                       // blist
+  s.add(sizeof(double2) * l1);                       // tw64
+  s.add(sizeof(float2) * l1);                        // tw32
+  s.add(sizeof(double) * m * l);                     // Y
+  const int64_t mx = m > n ? m : n;
+  s.add(sizeof(int32_t) * mx);                       // pos
+  s.add(sizeof(int32_t) * mx);                       // pstep
+  s.add(sizeof(int64_t) * m);                        // perm_y
+  s.add(sizeof(int64_t) * n);                        // perm_b
+  s.add(pivlu_cand_bytes(kMaxPivCtas));              // cand
+  s.add(sizeof(double) * 2 * kMaxPivCtas * (l > k ? l : k));  // candrow
+  s.add(sizeof(unsigned int) * 2);                   // bar (pivlu)
+  s.add(sizeof(double) * m * k);                     // Lk
+  s.add(sizeof(double) * max_gram_splits_for(k, num_sms) * k * k);  // gram partials
+  s.add(sizeof(double) * k * k);                     // G
+  s.add(sizeof(double) * k * k);                     // Rinv
+  s.add(sizeof(double) * k * k);                     // Ginv
+  s.add(sizeof(double) * k * m);                     // W
+  s.add(sizeof(double) * k * n);                     // B
+  s.add(sizeof(double) * m * k);                     // LyP
+  s.add(sizeof(double) * k * k);                     // Lb
+  s.add(sizeof(unsigned int) * 4);                   // status, bar2
+  return s;
+}
+
+bool sizes_ok(int64_t m, int64_t n, int k, int l, int l1) {
+  if (m < 1 || n < 1 || m >= (1ll << 31) || n >= (1ll << 31)) return false;
+  if (k < 1 || k > l || l > l1) return false;
+  if (l > m || k > (m < n ? m : n)) return false;
+  if (l > kMaxL || l1 > kMaxL1) return false;
+  return true;
+}
+
+int map_flags(unsigned int f) {
+  if (f & FLAG_TIMEOUT) return RLU_ETIMEOUT;
+  if (f & FLAG_BAD_CSR) return RLU_EBADCSR;
+  if (f & FLAG_NONFINITE) return RLU_ENONFINITE;
+  if (f & FLAG_ZERO_PIVOT) return RLU_WRANK;
+  return RLU_OK;
+}
+
+__global__ void k_status_code(const unsigned int* flags, int32_t* out) {
+  unsigned int f = *flags;
+  int code = RLU_OK;
+  if (f & FLAG_TIMEOUT) code = RLU_ETIMEOUT;
+  else if (f & FLAG_BAD_CSR) code = RLU_EBADCSR;
+  else if (f & FLAG_NONFINITE) code = RLU_ENONFINITE;
+  else if (f & FLAG_ZERO_PIVOT) code = RLU_WRANK;
+  *out = code;
+}
+
+bool prec_dtype_ok(int prec, int dtype) {
+  switch (prec) {
+    case RLU_PREC_F64: return dtype == RLU_F64;
+    case RLU_PREC_F32: return dtype == RLU_F32 || dtype == RLU_BF16;
+    case RLU_PREC_BF16:
+    case RLU_PREC_BF16_REFINE: return dtype == RLU_BF16;
+    default: return false;
+  }
+}
+
+int mark(rlu_ctx* h, int i, cudaStream_t st) {
+  if (!h->timing) return RLU_OK;
+  RLU_CUDA_TRY(cudaEventRecord(h->ev[i], st));
+  if (i == kNumStages) h->ev_recorded = 1;
+  return RLU_OK;
+}
+
+// Enqueue the dense path; the device status word receives the flags.
+int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, void* U, int64_t* p, int64_t* q,
+                  cudaStream_t st) {
+  const int64_t m = h->m, n = h->n;
+  const int k = h->k, l = h->l, l1 = h->l1;
+  const bool f64 = (h->prec == RLU_PREC_F64);
+  int rc;
+  RLU_CUDA_TRY(cudaMemsetAsync(h->status_dev, 0, sizeof(unsigned int), st));
+  h->ev_recorded = 0;
+  if ((rc = mark(h, 0, st))) return rc;
+  // step 1: S, D, R
+  h->sk.chunk = sketch_chunk_cols(dtype);
+  h->sk.nchunks = cdiv(n, h->sk.chunk);
+  if ((rc = launch_sketch_params(h->sk, n, l1, l, h->seed, st))) return rc;
+  if ((rc = mark(h, 1, st))) return rc;
+  // step 2: Y = A S D H R / sqrt(l1)
+  if ((rc = launch_sketch_dense(A, lda, dtype, f64, m, n, l1, l, h->sk, h->Y, h->status_dev, h->num_sms, st)))
+    return rc;
+  if ((rc = mark(h, 2, st))) return rc;
+  if (h->debug && h->Ydbg)
+    RLU_CUDA_TRY(cudaMemcpyAsync(h->Ydbg, h->Y, sizeof(double) * m * l, cudaMemcpyDeviceToDevice, st));
+  // step 3: P Y = L_Y U_Y (FP64, l steps)
+  h->pw.perm = h->perm_y;
+  if ((rc = launch_pivoted_lu<double>(h->Y, m, l, l, 1, l, h->pw, h->status_dev, h->num_sms, st))) return rc;
+  if ((rc = mark(h, 3, st))) return rc;
+  // W = L_y^+ P
+  PinvArgs pa{};
+  pa.m = m; pa.k = k; pa.l = l;
+  pa.Y = h->Y; pa.pstep = h->pw.pstep; pa.Lk = h->Lk;
+  pa.gram_part = h->gram_part; pa.max_gram_splits = h->max_gram_splits;
+  pa.G = h->G; pa.Rinv = h->Rinv; pa.Ginv = h->Ginv;
+  pa.W = h->W; pa.w64 = f64 ? 1 : 0;
+  pa.bar = h->bar2; pa.status = h->status_dev; pa.num_sms = h->num_sms;
+  if ((rc = launch_gram(pa, st))) return rc;
+  if ((rc = mark(h, 4, st))) return rc;
+  if ((rc = launch_chol(pa, st))) return rc;
+  if ((rc = mark(h, 5, st))) return rc;
+  if ((rc = launch_wform(pa, st))) return rc;
+  if ((rc = mark(h, 6, st))) return rc;
+  // B = W A
+  if ((rc = launch_bgemm_simt(h->W, f64 ? 1 : 0, A, lda, dtype, m, n, k, h->B, st))) return rc;
+  if ((rc = mark(h, 7, st))) return rc;
+  if (h->debug && h->Bdbg)
+    RLU_CUDA_TRY(cudaMemcpyAsync(h->Bdbg, h->B, (f64 ? 8 : 4) * (size_t)k * n, cudaMemcpyDeviceToDevice, st));
+  // step 6: B Q = L_b U_b as partial pivoting of B^T
+  h->pw.perm = h->perm_b;
+  if (f64)
+    rc = launch_pivoted_lu<double>(reinterpret_cast<double*>(h->B), n, k, 1, n, k, h->pw, h->status_dev,
+                                   h->num_sms, st);
+  else
+    rc = launch_pivoted_lu<float>(reinterpret_cast<float*>(h->B), n, k, 1, n, k, h->pw, h->status_dev, h->num_sms,
+                                  st);
+  if (rc) return rc;
+  if ((rc = mark(h, 8, st))) return rc;
+  // step 7: L = L_y L_b, U = U_b, p, q
+  AssembleArgs aa{};
+  aa.m = m; aa.n = n; aa.k = k;
+  aa.Lk = h->Lk; aa.perm_y = h->perm_y; aa.perm_b = h->perm_b; aa.Bp = h->B;
+  aa.LyP = h->LyP; aa.Lb = h->Lb; aa.L = L; aa.U = U; aa.p = p; aa.q = q;
+  rc = f64 ? launch_assemble<double>(aa, st) : launch_assemble<float>(aa, st);
+  if (rc) return rc;
+  if ((rc = mark(h, 9, st))) return rc;
+  h->last_prec = h->prec;
+  return RLU_OK;
+}
+
+int finish_sync(rlu_ctx* h, cudaStream_t st) {
+  RLU_CUDA_TRY(cudaMemcpyAsync(h->status_host, h->status_dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  RLU_CUDA_TRY(cudaStreamSynchronize(st));
+  return map_flags(*h->status_host);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rlu_strerror(int code) {
+  switch (code) {
+    case RLU_OK: return "success";
+    case RLU_EINVAL: return "invalid argument";
+    case RLU_ENOMEM: return "device workspace allocation failed";
+    case RLU_ECUDA: return "CUDA error or no usable GPU";
+    case RLU_ETIMEOUT: return "a bounded device wait timed out";
+    case RLU_ENONFINITE: return "input holds NaN or Inf";
+    case RLU_EBADCSR: return "invalid CSR structure";
+    case RLU_WRANK: return "warning: exactly zero pivot met (rank deficient input)";
+    default: return "unknown status";
+  }
+}
+
+int rlu_workspace_bytes(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, int prec, size_t* bytes) {
+  if (!bytes || !sizes_ok(m, n, k, l, l1) || prec < 0 || prec > 3) return RLU_EINVAL;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *bytes = plan_sizes(m, n, k, l, l1, sms).total;
+  return RLU_OK;
+}
+
+int rlu_create(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t seed, rlu_t* out) {
+  if (!out) return RLU_EINVAL;
+  *out = nullptr;
+  if (!sizes_ok(m, n, k, l, l1)) return RLU_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RLU_ECUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return RLU_ECUDA;
+  rlu_ctx* h = new (std::nothrow) rlu_ctx();
+  if (!h) return RLU_ENOMEM;
+  h->m = m; h->n = n; h->k = k; h->l = l; h->l1 = l1; h->seed = seed;
+  h->device = dev; h->num_sms = sms;
+  Sizes sz = plan_sizes(m, n, k, l, l1, sms);
+  char* base = nullptr;
+  if (cudaMalloc(&base, sz.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return RLU_ENOMEM;
+  }
+  h->allocs.push_back(base);
+  size_t off = 0;
+  int idx = 0;
+  auto next = [&](void) -> void* { void* p = base + off; off += sz.parts[idx++]; return p; };
+  h->sk.hs = (uint32_t*)next();
+  h->sk.dsign = (float*)next();
+  h->sk.keys = (uint64_t*)next();
+  h->sk.R = (int32_t*)next();
+  h->sk.bcnt = (int32_t*)next();
+  h->sk.bstart = (int32_t*)next();
+  h->sk.blist = (uint32_t*)next();
+  h->sk.tw64 = (double2*)next();
+  h->sk.tw32 = (float2*)next();
+  h->sk.plan = make_fft_plan(l1);
+  h->Y = (double*)next();
+  h->pw.pos = (int32_t*)next();
+  h->pw.pstep = (int32_t*)next();
+  h->perm_y = (int64_t*)next();
+  h->perm_b = (int64_t*)next();
+  h->pw.cand = next();
+  h->pw.candrow = next();
+  h->pw.bar = (unsigned int*)next();
+  h->pw.max_ctas = kMaxPivCtas;
+  h->pw.max_cols = l > k ? l : k;
+  h->Lk = (double*)next();
+  h->gram_part = (double*)next();
+  h->max_gram_splits = max_gram_splits_for(k, sms);
+  h->G = (double*)next();
+  h->Rinv = (double*)next();
+  h->Ginv = (double*)next();
+  h->W = next();
+  h->B = next();
+  h->LyP = next();
+  h->Lb = next();
+  h->status_dev = (unsigned int*)next();
+  h->bar2 = h->status_dev + 1;
+  if (cudaMallocHost(&h->status_host, sizeof(unsigned int)) != cudaSuccess) {
+    cudaGetLastError();
+    rlu_destroy(h);
+    return RLU_ENOMEM;
+  }
+  if (launch_twiddles(l1, h->sk.tw64, h->sk.tw32, 0) != RLU_OK || cudaDeviceSynchronize() != cudaSuccess) {
+    rlu_destroy(h);
+    return RLU_ECUDA;
+  }
+  *out = h;
+  return RLU_OK;
+}
+
+int rlu_set_precision(rlu_t h, int prec) {
+  if (!h || prec < 0 || prec > 3) return RLU_EINVAL;
+  h->prec = prec;
+  return RLU_OK;
+}
+
+int rlu_destroy(rlu_t h) {
+  if (!h) return RLU_OK;
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->status_host) cudaFreeHost(h->status_host);
+  if (h->Ydbg) cudaFree(h->Ydbg);
+  if (h->Bdbg) cudaFree(h->Bdbg);
+  if (h->A_stage) cudaFree(h->A_stage);
+  if (h->L_stage) cudaFree(h->L_stage);
+  if (h->U_stage) cudaFree(h->U_stage);
+  if (h->p_stage) cudaFree(h->p_stage);
+  if (h->q_stage) cudaFree(h->q_stage);
+  for (int i = 0; i <= kNumStages; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  delete h;
+  return RLU_OK;
+}
+
+int rlu_factor_dense_async(rlu_t h, const void* A, int64_t lda, int dtype, void* L, void* U, int64_t* p, int64_t* q,
+                           int32_t* status_dev, void* stream) {
+  if (!h || !A || !L || !U || !p || !q || !status_dev) return RLU_EINVAL;
+  if (lda < h->n || !prec_dtype_ok(h->prec, dtype)) return RLU_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = enqueue_dense(h, A, lda, dtype, L, U, p, q, st);
+  if (rc) return rc;
+  k_status_code<<<1, 1, 0, st>>>(h->status_dev, status_dev);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return RLU_OK;
+}
+
+int rlu_factor_dense(rlu_t h, const void* A, int64_t lda, int dtype, void* L, void* U, int64_t* p, int64_t* q,
+                     void* stream) {
+  if (!h || !A || !L || !U || !p || !q) return RLU_EINVAL;
+  if (lda < h->n || !prec_dtype_ok(h->prec, dtype)) return RLU_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = enqueue_dense(h, A, lda, dtype, L, U, p, q, st);
+  if (rc) return rc;
+  return finish_sync(h, st);
+}
+
+int rlu_factor_csr(rlu_t h, const int64_t* rowptr, const int32_t* colind, const void* val, int64_t nnz, int dtype,
+                   void* L, void* U, int64_t* p, int64_t* q, void* stream) {
+  (void)h; (void)rowptr; (void)colind; (void)val; (void)nnz; (void)dtype;
+  (void)L; (void)U; (void)p; (void)q; (void)stream;
+  return RLU_EINVAL;  // the CSR path is added in a later change
+}
+
+int rlu_factor_dense_host(rlu_t h, const void* A_host, int dtype, void* L_host, void* U_host, int64_t* p_host,
+                          int64_t* q_host, void* stream) {
+  if (!h || !A_host || !L_host || !U_host || !p_host || !q_host) return RLU_EINVAL;
+  if (!prec_dtype_ok(h->prec, dtype)) return RLU_EINVAL;
+  const size_t es = dtype == RLU_F64 ? 8 : (dtype == RLU_F32 ? 4 : 2);
+  const size_t abytes = es * (size_t)h->m * h->n;
+  const size_t os = h->prec == RLU_PREC_F64 ? 8 : 4;
+  if (h->A_stage_bytes < abytes) {
+    if (h->A_stage) cudaFree(h->A_stage);
+    h->A_stage = nullptr;
+    h->A_stage_bytes = 0;
+    if (cudaMalloc(&h->A_stage, abytes) != cudaSuccess) { cudaGetLastError(); return RLU_ENOMEM; }
+    h->A_stage_bytes = abytes;
+  }
+  if (!h->L_stage) {
+    if (cudaMalloc(&h->L_stage, 8 * (size_t)h->m * h->k) != cudaSuccess ||
+        cudaMalloc(&h->U_stage, 8 * (size_t)h->k * h->n) != cudaSuccess ||
+        cudaMalloc(&h->p_stage, 8 * (size_t)h->m) != cudaSuccess ||
+        cudaMalloc(&h->q_stage, 8 * (size_t)h->n) != cudaSuccess) {
+      cudaGetLastError();
+      return RLU_ENOMEM;
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  RLU_CUDA_TRY(cudaMemcpyAsync(h->A_stage, A_host, abytes, cudaMemcpyHostToDevice, st));
+  int rc = enqueue_dense(h, h->A_stage, h->n, dtype, h->L_stage, h->U_stage, h->p_stage, h->q_stage, st);
+  if (rc) return rc;
+  RLU_CUDA_TRY(cudaMemcpyAsync(L_host, h->L_stage, os * h->m * h->k, cudaMemcpyDeviceToHost, st));
+  RLU_CUDA_TRY(cudaMemcpyAsync(U_host, h->U_stage, os * h->k * h->n, cudaMemcpyDeviceToHost, st));
+  RLU_CUDA_TRY(cudaMemcpyAsync(p_host, h->p_stage, 8 * h->m, cudaMemcpyDeviceToHost, st));
+  RLU_CUDA_TRY(cudaMemcpyAsync(q_host, h->q_stage, 8 * h->n, cudaMemcpyDeviceToHost, st));
+  return finish_sync(h, st);
+}
+
+int rlu_debug_timing(rlu_t h, int on) {
+  if (!h) return RLU_EINVAL;
+  if (on && !h->ev[0])
+    for (int i = 0; i <= kNumStages; ++i) RLU_CUDA_TRY(cudaEventCreate(&h->ev[i]));
+  h->timing = on ? 1 : 0;
+  h->ev_recorded = 0;
+  return RLU_OK;
+}
+
+int rlu_debug_stage_ms(rlu_t h, float* ms, int max_stages, int* count) {
+  if (!h || !ms || !count) return RLU_EINVAL;
+  *count = 0;
+  if (!h->timing || !h->ev_recorded) return RLU_EINVAL;
+  RLU_CUDA_TRY(cudaEventSynchronize(h->ev[kNumStages]));
+  int cnt = max_stages < kNumStages ? max_stages : kNumStages;
+  for (int i = 0; i < cnt; ++i) RLU_CUDA_TRY(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
+  *count = cnt;
+  return RLU_OK;
+}
+
+int rlu_debug_launch_count(int64_t* out) {
+  if (!out) return RLU_EINVAL;
+  *out = (int64_t)rlu::g_launches.load();
+  return RLU_OK;
+}
+
+int rlu_debug_enable(rlu_t h, int on) {
+  if (!h) return RLU_EINVAL;
+  h->debug = on ? 1 : 0;
+  if (h->debug && !h->Ydbg) {
+    if (cudaMalloc(&h->Ydbg, sizeof(double) * h->m * h->l) != cudaSuccess ||
+        cudaMalloc(&h->Bdbg, sizeof(double) * h->k * h->n) != cudaSuccess) {
+      cudaGetLastError();
+      return RLU_ENOMEM;
+    }
+  }
+  return RLU_OK;
+}
+
+int rlu_debug_sketch_params(rlu_t h, int32_t* hash, int8_t* s, int8_t* d, int32_t* R) {
+  if (!h || !hash || !s || !d || !R) return RLU_EINVAL;
+  std::vector<uint32_t> hs(h->n);
+  std::vector<float> ds(h->l1);
+  RLU_CUDA_TRY(cudaDeviceSynchronize());
+  RLU_CUDA_TRY(cudaMemcpy(hs.data(), h->sk.hs, sizeof(uint32_t) * h->n, cudaMemcpyDeviceToHost));
+  RLU_CUDA_TRY(cudaMemcpy(ds.data(), h->sk.dsign, sizeof(float) * h->l1, cudaMemcpyDeviceToHost));
+  RLU_CUDA_TRY(cudaMemcpy(R, h->sk.R, sizeof(int32_t) * h->l, cudaMemcpyDeviceToHost));
+  for (int64_t j = 0; j < h->n; ++j) {
+    hash[j] = (int32_t)(hs[j] & 0x7fffffffu);
+    s[j] = (hs[j] >> 31) ? -1 : 1;
+  }
+  for (int b = 0; b < h->l1; ++b) d[b] = ds[b] < 0 ? -1 : 1;
+  return RLU_OK;
+}
+
+int rlu_debug_Y(rlu_t h, double* Y_host) {
+  if (!h || !Y_host || !h->Ydbg) return RLU_EINVAL;
+  RLU_CUDA_TRY(cudaDeviceSynchronize());
+  RLU_CUDA_TRY(cudaMemcpy(Y_host, h->Ydbg, sizeof(double) * h->m * h->l, cudaMemcpyDeviceToHost));
+  return RLU_OK;
+}
+
+int rlu_debug_B(rlu_t h, double* B_host) {
+  if (!h || !B_host || !h->Bdbg) return RLU_EINVAL;
+  RLU_CUDA_TRY(cudaDeviceSynchronize());
+  const size_t cnt = (size_t)h->k * h->n;
+  if (h->last_prec == RLU_PREC_F64) {
+    RLU_CUDA_TRY(cudaMemcpy(B_host, h->Bdbg, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> tmp(cnt);
+    RLU_CUDA_TRY(cudaMemcpy(tmp.data(), h->Bdbg, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < cnt; ++i) B_host[i] = tmp[i];
+  }
+  return RLU_OK;
+}
+
+}  // extern "C"

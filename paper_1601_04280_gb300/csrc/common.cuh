@@ -1,0 +1,144 @@
+// Shared device helpers of the sparse randomized LU library (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "../../include/rlu.h"
+
+namespace rlu {
+
+// ---------------------------------------------------------------------------
+// Device status word: bits set by kernels, read once by the host at the end.
+// ---------------------------------------------------------------------------
+enum : unsigned int {
+  FLAG_TIMEOUT = 1u << 0,    // a bounded device wait gave up
+  FLAG_NONFINITE = 1u << 1,  // NaN or Inf met in the input
+  FLAG_ZERO_PIVOT = 1u << 2, // an exactly zero pivot column / row was met
+  FLAG_BAD_CSR = 1u << 3,    // CSR structure invalid (row pointers or column range)
+};
+
+// Spin limit for every device wait: about a second at GB300 clocks.
+constexpr long long kSpinLimitCycles = 2000000000ll;
+
+__device__ __forceinline__ void set_flag(unsigned int* status, unsigned int bit) {
+  atomicOr(status, bit);
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_gpu_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for cooperative (co-resident) launches.  `counter` starts
+// at zero for the launch; barrier number e (1, 2, ...) waits until all
+// gridDim.x blocks have arrived e times.  The wait is bounded: on timeout it
+// sets FLAG_TIMEOUT and returns false, and the caller must leave the kernel.
+// Once any block has timed out, every later barrier returns false at once.
+__device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int epoch,
+                                             unsigned int* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    red_release_gpu_add(counter, 1u);
+    const unsigned int target = epoch * gridDim.x;
+    long long t0 = clock64();
+    int ok = 1;
+    while (true) {
+      unsigned int v = ld_acquire_gpu(counter);
+      if ((int)(v - target) >= 0) break;
+      if (ld_acquire_gpu(status) & FLAG_TIMEOUT) { ok = 0; break; }
+      if (clock64() - t0 > kSpinLimitCycles) {
+        set_flag(status, FLAG_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from its
+// published definition: per round, two 64x64->128 products of counter words
+// 0 and 2 with the multipliers, xor-mixed with words 1 and 3 and the key;
+// the key is bumped by two Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct Philox4 {
+  uint64_t w[4];
+};
+
+__host__ __device__ __forceinline__ void mul64_wide(uint64_t a, uint64_t b, uint64_t& hi, uint64_t& lo) {
+#ifdef __CUDA_ARCH__
+  lo = a * b;
+  hi = __umul64hi(a, b);
+#else
+  unsigned __int128 p = (unsigned __int128)a * b;
+  lo = (uint64_t)p;
+  hi = (uint64_t)(p >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ Philox4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                                          uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint64_t hi0, lo0, hi1, lo1;
+    mul64_wide(M0, c0, hi0, lo0);
+    mul64_wide(M1, c2, hi1, lo1);
+    uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  Philox4 o;
+  o.w[0] = c0; o.w[1] = c1; o.w[2] = c2; o.w[3] = c3;
+  return o;
+}
+
+// Second key word of every stream of the method: "RANDLU" in ASCII.
+constexpr uint64_t kKeyTag = 0x52414E444C5500ull;
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T abs_(T x) { return x < T(0) ? -x : x; }
+
+template <typename T> __device__ __forceinline__ double to_double(T x) { return (double)x; }
+template <> __device__ __forceinline__ double to_double<__nv_bfloat16>(__nv_bfloat16 x) {
+  return (double)__bfloat162float(x);
+}
+template <typename T> __device__ __forceinline__ float to_float(T x) { return (float)x; }
+template <> __device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+
+template <typename T> __device__ __forceinline__ bool finite_(T x) { return isfinite(to_float(x)); }
+template <> __device__ __forceinline__ bool finite_<double>(double x) { return isfinite(x); }
+
+// Process-wide count of kernels this library has launched (a test hook).
+void note_launch(int count = 1);
+
+__host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+}  // namespace rlu
+
+#define RLU_CUDA_TRY(expr)                         \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) return RLU_ECUDA;       \
+  } while (0)

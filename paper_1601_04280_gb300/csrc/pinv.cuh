@@ -1,0 +1,49 @@
+// Declarations of B = L_y^+ P A and of the output assembly.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rlu {
+
+struct PinvArgs {
+  int64_t m;
+  int k, l;
+  const double* Y;       // m x l packed panel LU (original row order)
+  const int32_t* pstep;  // m
+  double* Lk;            // m x k
+  double* gram_part;     // max_gram_splits x k x k
+  int max_gram_splits;
+  double* G;             // k x k (Cholesky overwrites its upper triangle)
+  double* Rinv;          // k x k
+  double* Ginv;          // k x k
+  void* W;               // k x m, double if w64 else float
+  int w64;
+  unsigned int* bar;
+  unsigned int* status;
+  int num_sms;
+};
+
+struct AssembleArgs {
+  int64_t m, n;
+  int k;
+  const double* Lk;
+  const int64_t* perm_y;  // m
+  const int64_t* perm_b;  // n
+  const void* Bp;         // k x n packed LU of B
+  void* LyP;              // m x k scratch
+  void* Lb;               // k x k scratch
+  void* L;                // m x k output
+  void* U;                // k x n output
+  int64_t* p;
+  int64_t* q;
+};
+
+int launch_gram(const PinvArgs& a, cudaStream_t st);
+int launch_chol(const PinvArgs& a, cudaStream_t st);
+int launch_wform(const PinvArgs& a, cudaStream_t st);
+template <typename T>
+int launch_assemble(const AssembleArgs& a, cudaStream_t st);
+int launch_bgemm_simt(const void* W, int w64, const void* A, int64_t lda, int dtype, int64_t m, int64_t n, int k,
+                      void* B, cudaStream_t st);
+
+}  // namespace rlu

@@ -1,0 +1,268 @@
+// Partial-pivoted LU of a tall matrix X (rows >= cols), `steps` elimination
+// steps, in one persistent cooperative kernel.  Used twice:
+//   * step 3 of Algorithm 1: P Y = L_Y U_Y on the m x l sketch (FP64), and
+//   * step 6: the LU of B with right (column) pivoting, run as partial
+//     pivoting on B^T (rows = columns of B) through strides.
+//
+// Semantics follow LAPACK getf2: at step j the pivot is the row with the
+// largest |X[., j]| among the rows not yet pivoted, ties going to the row
+// with the smallest current position (positions change by the getf2 swap
+// of position j with the pivot's position); a nonzero pivot divides the
+// column below it; the rank-1 update runs on the trailing block.  An exactly
+// zero pivot skips the division and raises FLAG_ZERO_PIVOT.
+//
+// Rows are never moved.  Each CTA owns a contiguous slab of rows (kept in
+// shared memory when it fits) and tracks their current positions; every CTA
+// keeps an identical copy of the occupants of positions 0..steps-1, so the
+// whole permutation follows from one broadcast pivot per step.  One grid
+// barrier per step: before it each CTA publishes its best candidate and that
+// row's trailing values; after it every CTA picks the same winner.
+#include "common.cuh"
+#include "pivlu.cuh"
+
+namespace rlu {
+
+struct __align__(16) Cand {
+  double v;     // |pivot candidate|, -1 if the CTA has no candidate
+  int pos;      // current position of the candidate row
+  int row;      // original row index
+};
+
+__device__ __forceinline__ bool cand_better(double va, int pa, double vb, int pb) {
+  return va > vb || (va == vb && pa < pb);
+}
+
+template <typename T>
+__device__ __forceinline__ T& xref(T* X, int64_t rs, int64_t cs, int64_t i, int c) {
+  return X[i * rs + (int64_t)c * cs];
+}
+
+template <typename T, bool SMEM, int NT>
+__global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t rows, int cols, int64_t rs,
+                                                   int64_t cs, int steps, int64_t rpc, int32_t* __restrict__ pos_out,
+                                                   int32_t* __restrict__ pstep_out, int64_t* __restrict__ perm_out,
+                                                   Cand* __restrict__ cand, T* __restrict__ candrow,
+                                                   unsigned int* bar, unsigned int* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int G = gridDim.x;
+  const int tid = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rpc;
+  const int nr = (int)max((int64_t)0, min(rpc, rows - r0));
+  // shared layout
+  T* slab = reinterpret_cast<T*>(smem);                               // nr x cols (SMEM variant)
+  T* urow = slab + (SMEM ? (size_t)rpc * cols : 0);                   // cols
+  T* lval = urow + cols;                                              // rpc
+  int32_t* lpos = reinterpret_cast<int32_t*>(lval + rpc);             // rpc
+  int32_t* lstep = lpos + rpc;                                        // rpc
+  int32_t* pwin = lstep + rpc;                                        // steps
+  __shared__ double red_v[NT / 32];
+  __shared__ int red_p[NT / 32];
+  __shared__ int red_r[NT / 32];
+  __shared__ double s_piv;
+  __shared__ int s_wrow, s_wpos, s_wcta;
+
+  const bool row_fast = (cs != 1);  // B^T: consecutive rows are contiguous
+  auto at = [&](int r, int c) -> T& {
+    if (SMEM) return slab[(size_t)r * cols + c];
+    return xref(X, rs, cs, r0 + r, c);
+  };
+
+  // load slab, init bookkeeping
+  if (SMEM) {
+    const int64_t tot = (int64_t)nr * cols;
+    for (int64_t idx = tid; idx < tot; idx += NT) {
+      int r, c;
+      if (row_fast) { r = (int)(idx % nr); c = (int)(idx / nr); }
+      else { c = (int)(idx % cols); r = (int)(idx / cols); }
+      slab[(size_t)r * cols + c] = xref(X, rs, cs, r0 + r, c);
+    }
+  }
+  for (int r = tid; r < rpc; r += NT) {
+    lpos[r] = (int32_t)(r0 + r);
+    lstep[r] = -1;
+  }
+  for (int t = tid; t < steps; t += NT) pwin[t] = t;
+  __syncthreads();
+
+  for (int j = 0; j < steps; ++j) {
+    // 1. local candidate for column j
+    double bv = -1.0;
+    int bp = 0x7fffffff, br = -1;
+    for (int r = tid; r < nr; r += NT) {
+      if (lstep[r] < 0) {
+        double v = (double)abs_(at(r, j));
+        int p = lpos[r];
+        if (cand_better(v, p, bv, bp)) { bv = v; bp = p; br = r; }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      int op = __shfl_down_sync(0xffffffffu, bp, o);
+      int orr = __shfl_down_sync(0xffffffffu, br, o);
+      if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; br = orr; }
+    }
+    if ((tid & 31) == 0) { red_v[tid >> 5] = bv; red_p[tid >> 5] = bp; red_r[tid >> 5] = br; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < NT / 32; ++w)
+        if (cand_better(red_v[w], red_p[w], bv, bp)) { bv = red_v[w]; bp = red_p[w]; br = red_r[w]; }
+      Cand cd;
+      cd.v = bv;
+      cd.pos = bp;
+      cd.row = br < 0 ? -1 : (int)(r0 + br);
+      cand[(j & 1) * G + blockIdx.x] = cd;
+      s_wrow = br;  // local row of this CTA's candidate
+    }
+    __syncthreads();
+    {
+      const int lr = s_wrow;
+      T* dst = candrow + ((size_t)(j & 1) * G + blockIdx.x) * cols;
+      if (lr >= 0)
+        for (int c = j + tid; c < cols; c += NT) dst[c - j] = at(lr, c);
+    }
+    // 2. one grid barrier per step
+    if (!grid_barrier(bar, (unsigned)(j + 1), status)) return;
+    // 3. every CTA picks the same winner
+    bv = -1.0; bp = 0x7fffffff; int bc = -1;
+    for (int g = tid; g < G; g += NT) {
+      Cand cd = cand[(j & 1) * G + g];
+      if (cd.row >= 0 && cand_better(cd.v, cd.pos, bv, bp)) { bv = cd.v; bp = cd.pos; bc = g; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      int op = __shfl_down_sync(0xffffffffu, bp, o);
+      int oc = __shfl_down_sync(0xffffffffu, bc, o);
+      if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; bc = oc; }
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) { red_v[tid >> 5] = bv; red_p[tid >> 5] = bp; red_r[tid >> 5] = bc; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < NT / 32; ++w)
+        if (cand_better(red_v[w], red_p[w], bv, bp)) { bv = red_v[w]; bp = red_p[w]; bc = red_r[w]; }
+      s_wcta = bc;
+      s_wpos = bp;
+      s_wrow = bc >= 0 ? cand[(j & 1) * G + bc].row : -1;
+    }
+    __syncthreads();
+    const int wcta = s_wcta;
+    if (wcta < 0) {  // no row left (cannot happen with steps <= rows)
+      if (tid == 0) set_flag(status, FLAG_ZERO_PIVOT);
+      break;
+    }
+    {
+      const T* src = candrow + ((size_t)(j & 1) * G + wcta) * cols;
+      for (int c = j + tid; c < cols; c += NT) urow[c - j] = src[c - j];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const int w = s_wrow, wpos = s_wpos;
+      s_piv = (double)urow[0];
+      if (s_piv == 0.0 && blockIdx.x == 0) set_flag(status, FLAG_ZERO_PIVOT);
+      // getf2 swap of positions j and wpos
+      const int occ = pwin[j];
+      pwin[j] = w;
+      if (wpos < steps) pwin[wpos] = occ;
+      if (occ != w && occ >= r0 && occ < r0 + nr) lpos[occ - r0] = wpos;
+      if (w >= r0 && w < r0 + nr) {
+        lpos[w - r0] = j;
+        lstep[w - r0] = j;
+      }
+    }
+    __syncthreads();
+    // 4. scale column j below the pivot, then the rank-1 update
+    const T piv = (T)s_piv;
+    if (piv != T(0)) {
+      for (int r = tid; r < nr; r += NT) {
+        if (lstep[r] < 0) {
+          T lv = at(r, j) / piv;
+          at(r, j) = lv;
+          lval[r] = lv;
+        }
+      }
+      __syncthreads();
+      const int width = cols - j - 1;
+      if (width > 0) {
+        const int64_t tot = (int64_t)nr * width;
+        for (int64_t idx = tid; idx < tot; idx += NT) {
+          int r, c;
+          if (row_fast && !SMEM) { r = (int)(idx % nr); c = (int)(idx / nr); }
+          else { c = (int)(idx % width); r = (int)(idx / width); }
+          if (lstep[r] < 0) {
+            T& x = at(r, j + 1 + c);
+            x = x - lval[r] * urow[1 + c];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // write back
+  if (SMEM) {
+    const int64_t tot = (int64_t)nr * cols;
+    for (int64_t idx = tid; idx < tot; idx += NT) {
+      int r, c;
+      if (row_fast) { r = (int)(idx % nr); c = (int)(idx / nr); }
+      else { c = (int)(idx % cols); r = (int)(idx / cols); }
+      xref(X, rs, cs, r0 + r, c) = slab[(size_t)r * cols + c];
+    }
+  }
+  for (int r = tid; r < nr; r += NT) {
+    pos_out[r0 + r] = lpos[r];
+    pstep_out[r0 + r] = lstep[r];
+    perm_out[lpos[r]] = r0 + r;
+  }
+}
+
+template <typename T, bool SMEM>
+static size_t pivlu_smem(int64_t rpc, int cols, int steps) {
+  size_t b = (SMEM ? (size_t)rpc * cols * sizeof(T) : 0) + (size_t)cols * sizeof(T) + (size_t)rpc * sizeof(T) +
+             (size_t)rpc * 8 + (size_t)steps * 4;
+  return (b + 15) & ~(size_t)15;
+}
+
+template <typename T, bool SMEM>
+static int launch_cfg(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int steps, int G, PivLuWs& ws,
+                      unsigned int* status, cudaStream_t st) {
+  constexpr int NT = 256;
+  const int64_t rpc = cdiv(rows, G);
+  size_t smem = pivlu_smem<T, SMEM>(rpc, cols, steps);
+  auto kern = k_pivoted_lu<T, SMEM, NT>;
+  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+  if (per_sm < 1) return RLU_EINVAL;
+  RLU_CUDA_TRY(cudaMemsetAsync(ws.bar, 0, sizeof(unsigned int), st));
+  Cand* cand = reinterpret_cast<Cand*>(ws.cand);
+  T* candrow = reinterpret_cast<T*>(ws.candrow);
+  void* args[] = {&X, &rows, &cols, &rs, &cs, &steps, (void*)&rpc, &ws.pos, &ws.pstep, &ws.perm,
+                  &cand, &candrow, &ws.bar, &status};
+  RLU_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, G, NT, args, smem, st));
+  note_launch();
+  return RLU_OK;
+}
+
+size_t pivlu_cand_bytes(int max_ctas) { return (size_t)2 * max_ctas * sizeof(Cand); }
+
+template <typename T>
+int launch_pivoted_lu(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int steps, PivLuWs& ws,
+                      unsigned int* status, int num_sms, cudaStream_t st) {
+  if (steps > cols || steps > rows || cols > ws.max_cols) return RLU_EINVAL;
+  // one CTA per SM, or fewer for small inputs (at least 8 rows per CTA)
+  int G = (int)min64(num_sms, cdiv(rows, 8));
+  if (G > ws.max_ctas) G = ws.max_ctas;
+  const int64_t rpc = cdiv(rows, G);
+  size_t smem = pivlu_smem<T, true>(rpc, cols, steps);
+  if (smem <= 200 * 1024) return launch_cfg<T, true>(X, rows, cols, rs, cs, steps, G, ws, status, st);
+  return launch_cfg<T, false>(X, rows, cols, rs, cs, steps, G, ws, status, st);
+}
+
+template int launch_pivoted_lu<double>(double*, int64_t, int, int64_t, int64_t, int, PivLuWs&, unsigned int*, int,
+                                       cudaStream_t);
+template int launch_pivoted_lu<float>(float*, int64_t, int, int64_t, int64_t, int, PivLuWs&, unsigned int*, int,
+                                      cudaStream_t);
+
+}  // namespace rlu

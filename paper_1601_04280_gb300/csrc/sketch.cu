@@ -1,0 +1,452 @@
+// Step 1 and step 2 of Algorithm 1 (Sec. 3): the random structures and the
+// sketch Y = A S D H R / sqrt(l1).
+//
+//  * k_sketch_params / k_select_R: the hash h, signs s of the sparse embedding
+//    matrix (Sec. 2.2) and the signs d and subsample R of the real FFT-based
+//    projection (Sec. 2.1), all from Philox4x64-10 with key (seed, "RANDLU").
+//  * bucket lists: for each column chunk and bucket b, the columns j of the
+//    chunk with h(j) = b in ascending order, so the CountSketch is a
+//    deterministic gather-sum in ascending column order.
+//  * k_sketch_dense: one pass over dense row-major A.  Per group of R rows a
+//    CTA stages column chunks of A in shared memory, each thread sums the
+//    buckets it owns in registers, then every row pair goes through one
+//    complex mixed-radix Stockham FFT in shared memory (two real rows packed
+//    as real and imaginary parts), the Hartley outputs Re X - Im X of the l
+//    selected frequencies are scaled by 1/sqrt(l1) and written to Y.  Y1
+//    never reaches global memory.
+#include <cstdio>
+
+#include "common.cuh"
+#include "sketch.cuh"
+
+namespace rlu {
+
+// ---------------------------------------------------------------------------
+// Random structures
+// ---------------------------------------------------------------------------
+__global__ void k_sketch_params(int64_t n, int l1, uint64_t seed, uint32_t* hs, float* dsign, uint64_t* keys) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    Philox4 b = philox4x64_10((uint64_t)i, 0, 0, 0, seed, kKeyTag);
+    uint32_t h = (uint32_t)__umul64hi(b.w[0], (uint64_t)l1);
+    uint32_t neg = (uint32_t)(b.w[1] >> 63);
+    hs[i] = h | (neg << 31);
+  }
+  if (i < l1) {
+    Philox4 b1 = philox4x64_10((uint64_t)i, 1, 0, 0, seed, kKeyTag);
+    dsign[i] = (b1.w[0] >> 63) ? -1.0f : 1.0f;
+    Philox4 b2 = philox4x64_10((uint64_t)i, 2, 0, 0, seed, kKeyTag);
+    keys[i] = b2.w[0];
+  }
+}
+
+// R = the l indices b with the smallest (key[b], b), in increasing order:
+// each b counts the keys below its own and, if that rank is < l, lands at R[rank].
+__global__ void k_select_R(int l1, int l, const uint64_t* keys, int32_t* R) {
+  __shared__ uint64_t sk[1024];
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t kb = b < l1 ? keys[b] : 0;
+  int rank = 0;
+  for (int base = 0; base < l1; base += 1024) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < 1024 && base + t < l1; t += blockDim.x) sk[t] = keys[base + t];
+    __syncthreads();
+    int lim = min(1024, l1 - base);
+    if (b < l1) {
+      for (int t = 0; t < lim; ++t) {
+        uint64_t kt = sk[t];
+        rank += (kt < kb) || (kt == kb && base + t < b);
+      }
+    }
+  }
+  if (b < l1 && rank < l) R[rank] = b;
+}
+
+// ---------------------------------------------------------------------------
+// Bucket lists per column chunk: super-bucket sb = chunk * l1 + h(j)
+// ---------------------------------------------------------------------------
+__global__ void k_bucket_count(int64_t n, int l1, int chunk, const uint32_t* hs, int32_t* cnt) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) {
+    int64_t sb = (j / chunk) * l1 + (hs[j] & 0x7fffffffu);
+    atomicAdd(&cnt[sb], 1);
+  }
+}
+
+// Exclusive scan of cnt[0..count) into start[0..count], one CTA of 1024 threads.
+__global__ void k_scan_counts(int64_t count, const int32_t* cnt, int32_t* start) {
+  __shared__ int64_t part[1024];
+  const int T = blockDim.x;
+  int64_t per = cdiv(count, T);
+  int64_t a = threadIdx.x * per, b = min(count, a + per);
+  int64_t s = 0;
+  for (int64_t i = a; i < b; ++i) s += cnt[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t run = 0;
+    for (int t = 0; t < T; ++t) {
+      int64_t v = part[t];
+      part[t] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  int64_t run = part[threadIdx.x];
+  for (int64_t i = a; i < b; ++i) {
+    start[i] = (int32_t)run;
+    run += cnt[i];
+  }
+  if (threadIdx.x == T - 1) start[count] = (int32_t)run;
+}
+
+__global__ void k_bucket_fill(int64_t n, int l1, int chunk, const uint32_t* hs, const int32_t* start,
+                              int32_t* cursor, uint32_t* list) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) {
+    uint32_t e = hs[j];
+    int64_t c = j / chunk;
+    int64_t sb = c * l1 + (e & 0x7fffffffu);
+    int pos = start[sb] + atomicAdd(&cursor[sb], 1);
+    list[pos] = (uint32_t)(j - c * chunk) | (e & 0x80000000u);
+  }
+}
+
+// Sort each super-bucket's entries by column (insertion sort; buckets are short).
+__global__ void k_bucket_sort(int64_t count, const int32_t* start, uint32_t* list) {
+  int64_t sb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (sb >= count) return;
+  int a = start[sb], b = start[sb + 1];
+  for (int i = a + 1; i < b; ++i) {
+    uint32_t v = list[i];
+    uint32_t kv = v & 0x7fffffffu;
+    int t = i - 1;
+    while (t >= a && (list[t] & 0x7fffffffu) > kv) {
+      list[t + 1] = list[t];
+      --t;
+    }
+    list[t + 1] = v;
+  }
+}
+
+// Twiddles tw[e] = exp(-2 pi i e / N), computed in FP64 with sincospi.
+__global__ void k_twiddles(int N, double2* tw64, float2* tw32) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  double s, c;
+  sincospi(-2.0 * (double)e / (double)N, &s, &c);
+  tw64[e] = make_double2(c, s);
+  tw32[e] = make_float2((float)c, (float)s);
+}
+
+// ---------------------------------------------------------------------------
+// Complex arithmetic on float2 / double2
+// ---------------------------------------------------------------------------
+template <typename T> struct C2;
+template <> struct C2<float> { using t = float2; };
+template <> struct C2<double> { using t = double2; };
+
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// multiply by -i
+template <typename V> __device__ __forceinline__ V cmi(V a) { return V{a.y, -a.x}; }
+
+// One Stockham stage of radix r over N points: p = product of the radices
+// already applied.  Butterfly i < N/r reads in[i + t N/r] (t < r), applies
+// the twiddles exp(-2 pi i t (i mod p) / (p r)) and a length-r DFT, and
+// writes out[(i - i mod p) r + i mod p + u p] (u < r).  Output is in natural
+// order after the last stage.
+template <typename V, typename S>
+__device__ void stockham_stage(const V* __restrict__ in, V* __restrict__ out, int N, int r, int p, const V* tw) {
+  const int T = N / r;
+  const int step = N / (p * r);
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    const int k = i % p;
+    const int obase = (i - k) * r + k;
+    if (r == 4) {
+      V x0 = in[i], x1 = in[i + T], x2 = in[i + 2 * T], x3 = in[i + 3 * T];
+      if (k) {
+        x1 = cmul(x1, tw[k * step]);
+        x2 = cmul(x2, tw[2 * k * step]);
+        x3 = cmul(x3, tw[3 * k * step]);
+      }
+      V a0 = cadd(x0, x2), a1 = csub(x0, x2), b0 = cadd(x1, x3), b1 = cmi(csub(x1, x3));
+      out[obase] = cadd(a0, b0);
+      out[obase + p] = cadd(a1, b1);
+      out[obase + 2 * p] = csub(a0, b0);
+      out[obase + 3 * p] = csub(a1, b1);
+    } else if (r == 2) {
+      V x0 = in[i], x1 = in[i + T];
+      if (k) x1 = cmul(x1, tw[k * step]);
+      out[obase] = cadd(x0, x1);
+      out[obase + p] = csub(x0, x1);
+    } else if (r == 3) {
+      V x0 = in[i], x1 = in[i + T], x2 = in[i + 2 * T];
+      if (k) {
+        x1 = cmul(x1, tw[k * step]);
+        x2 = cmul(x2, tw[2 * k * step]);
+      }
+      // W3 = exp(-2 pi i / 3) = -1/2 - i sqrt(3)/2
+      const S h = S(0.86602540378443864676);
+      V s = cadd(x1, x2), d = csub(x1, x2);
+      V t = V{x0.x - S(0.5) * s.x, x0.y - S(0.5) * s.y};
+      V u = V{h * d.y, -h * d.x};  // -i * (sqrt(3)/2) * d
+      out[obase] = cadd(x0, s);
+      out[obase + p] = cadd(t, u);
+      out[obase + 2 * p] = csub(t, u);
+    } else if (r <= 16) {
+      V x[16];
+      for (int t = 0; t < r; ++t) {
+        V v = in[i + t * T];
+        x[t] = (k && t) ? cmul(v, tw[t * k * step]) : v;
+      }
+      const int wstep = N / r;
+      for (int u = 0; u < r; ++u) {
+        V y = x[0];
+        int e = 0;
+        for (int t = 1; t < r; ++t) {
+          e += u;
+          if (e >= r) e -= r;
+          y = cadd(y, cmul(x[t], tw[e * wstep]));
+        }
+        out[obase + u * p] = y;
+      }
+    } else {
+      // large prime radix: direct sums, operands re-read from shared memory
+      const int wstep = N / r;
+      for (int u = 0; u < r; ++u) {
+        V y = in[i];
+        int e = 0;
+        for (int t = 1; t < r; ++t) {
+          e += u;
+          if (e >= r) e -= r;
+          V v = in[i + t * T];
+          if (k) v = cmul(v, tw[t * k * step]);
+          y = cadd(y, cmul(v, tw[e * wstep]));
+        }
+        out[obase + u * p] = y;
+      }
+    }
+  }
+}
+
+template <typename TA> __device__ __forceinline__ float load_acc(const TA* p, float) { return to_float(*p); }
+template <typename TA> __device__ __forceinline__ double load_acc(const TA* p, double) { return to_double(*p); }
+
+// ---------------------------------------------------------------------------
+// Fused dense sketch: CountSketch + signs + Hartley FFT + subsample
+// ---------------------------------------------------------------------------
+template <typename TA, typename TACC, int NT, int NB, int R>
+__global__ void __launch_bounds__(NT) k_sketch_dense(const TA* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                                                     int l1, int l, int chunk, const int32_t* __restrict__ bstart,
+                                                     const uint32_t* __restrict__ blist,
+                                                     const float* __restrict__ dsign, const int32_t* __restrict__ Rsel,
+                                                     const typename C2<TACC>::t* __restrict__ tw, FftPlan plan,
+                                                     double* __restrict__ Y, unsigned int* status) {
+  using V = typename C2<TACC>::t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  TA* tile = reinterpret_cast<TA*>(smem);
+  V* buf0 = reinterpret_cast<V*>(smem);
+  V* buf1 = buf0 + l1;
+  const int tid = threadIdx.x;
+  const int64_t ngroups = cdiv(m, R);
+  const int nchunks = (int)cdiv(n, chunk);
+  const TACC scale = TACC(1) / sqrt(TACC(l1));
+  bool bad = false;
+  constexpr int VEC = 16 / sizeof(TA);
+  const bool vec_ok = ((lda * (int64_t)sizeof(TA)) % 16 == 0) && ((reinterpret_cast<uintptr_t>(A) % 16) == 0);
+
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const int64_t row0 = g * R;
+    TACC acc[NB][R];
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[t][r] = TACC(0);
+
+    for (int c = 0; c < nchunks; ++c) {
+      const int64_t col0 = (int64_t)c * chunk;
+      const int width = (int)min((int64_t)chunk, n - col0);
+      __syncthreads();
+      // stage R x width of A (rows past m read as zero; they are never written)
+      if (vec_ok && (width % VEC) == 0) {
+        const int nv = width / VEC;
+        for (int idx = tid; idx < R * nv; idx += NT) {
+          const int r = idx / nv, v = idx - r * nv;
+          uint4 val = make_uint4(0, 0, 0, 0);
+          if (row0 + r < m) val = __ldg(reinterpret_cast<const uint4*>(A + (row0 + r) * lda + col0) + v);
+          *reinterpret_cast<uint4*>(tile + r * chunk + v * VEC) = val;
+          const TA* e = reinterpret_cast<const TA*>(&val);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) bad |= !finite_(e[q]);
+        }
+      } else {
+        for (int idx = tid; idx < R * width; idx += NT) {
+          const int r = idx / width, cc = idx - r * width;
+          TA val = TA(0);
+          if (row0 + r < m) val = A[(row0 + r) * lda + col0 + cc];
+          tile[r * chunk + cc] = val;
+          bad |= !finite_(val);
+        }
+      }
+      __syncthreads();
+      const int32_t* bs = bstart + (int64_t)c * l1;
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        const int b = tid + t * NT;
+        if (b < l1) {
+          const int s0 = bs[b], s1 = bs[b + 1];
+          for (int e = s0; e < s1; ++e) {
+            const uint32_t ent = __ldg(blist + e);
+            const int off = (int)(ent & 0x7fffffffu);
+            const bool neg = (ent >> 31) != 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const TACC v = load_acc(tile + r * chunk + off, TACC(0));
+              acc[t][r] += neg ? -v : v;
+            }
+          }
+        }
+      }
+    }
+
+    // Hartley transform of each row pair: z = d (y1[2q] + i y1[2q+1])
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q) {
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        const int b = tid + t * NT;
+        if (b < l1) {
+          const TACC ds = (TACC)dsign[b];
+          buf0[b] = V{ds * acc[t][2 * q], ds * acc[t][2 * q + 1]};
+        }
+      }
+      __syncthreads();
+      V* src = buf0;
+      V* dst = buf1;
+      int p = 1;
+      for (int s = 0; s < plan.nstages; ++s) {
+        const int r = plan.radix[s];
+        stockham_stage<V, TACC>(src, dst, l1, r, p, tw);
+        p *= r;
+        __syncthreads();
+        V* tmp = src;
+        src = dst;
+        dst = tmp;
+      }
+      // src holds Z = FFT(z).  X1 = (Z[f] + conj Z[-f]) / 2, X2 = (Z[f] - conj Z[-f]) / 2i,
+      // Hartley H = Re X - Im X.
+      const int64_t ra = row0 + 2 * q, rb = ra + 1;
+      for (int cidx = tid; cidx < l; cidx += NT) {
+        const int f = Rsel[cidx];
+        const int fm = f == 0 ? 0 : l1 - f;
+        const V z = src[f], w = src[fm];
+        const TACC h1 = TACC(0.5) * ((z.x + w.x) - (z.y - w.y));
+        const TACC h2 = TACC(0.5) * ((z.x - w.x) + (z.y + w.y));
+        if (ra < m) Y[ra * l + cidx] = (double)(h1 * scale);
+        if (rb < m) Y[rb * l + cidx] = (double)(h2 * scale);
+      }
+    }
+  }
+  if (bad) set_flag(status, FLAG_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+FftPlan make_fft_plan(int N) {
+  FftPlan pl{};
+  int x = N;
+  auto push = [&](int r) { pl.radix[pl.nstages++] = r; };
+  while (x % 4 == 0) { push(4); x /= 4; }
+  while (x % 2 == 0) { push(2); x /= 2; }
+  for (int f = 3; x > 1; f += 2) {
+    while (x % f == 0) { push(f); x /= f; }
+  }
+  return pl;
+}
+
+int launch_sketch_params(const SketchWs& ws, int64_t n, int l1, int l, uint64_t seed, cudaStream_t st) {
+  int64_t cnt = n > l1 ? n : l1;
+  k_sketch_params<<<(unsigned)cdiv(cnt, 256), 256, 0, st>>>(n, l1, seed, ws.hs, ws.dsign, ws.keys);
+  k_select_R<<<(unsigned)cdiv(l1, 256), 256, 0, st>>>(l1, l, ws.keys, ws.R);
+  // bucket lists for the dense path
+  const int64_t nsb = ws.nchunks * (int64_t)l1;
+  RLU_CUDA_TRY(cudaMemsetAsync(ws.bcnt, 0, sizeof(int32_t) * (nsb + 1), st));
+  k_bucket_count<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, l1, ws.chunk, ws.hs, ws.bcnt);
+  k_scan_counts<<<1, 1024, 0, st>>>(nsb, ws.bcnt, ws.bstart);
+  RLU_CUDA_TRY(cudaMemsetAsync(ws.bcnt, 0, sizeof(int32_t) * (nsb + 1), st));
+  k_bucket_fill<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, l1, ws.chunk, ws.hs, ws.bstart, ws.bcnt, ws.blist);
+  k_bucket_sort<<<(unsigned)cdiv(nsb, 256), 256, 0, st>>>(nsb, ws.bstart, ws.blist);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch(6);
+  return RLU_OK;
+}
+
+int launch_twiddles(int N, double2* tw64, float2* tw32, cudaStream_t st) {
+  k_twiddles<<<(unsigned)cdiv(N, 256), 256, 0, st>>>(N, tw64, tw32);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return RLU_OK;
+}
+
+int sketch_chunk_cols(int dtype) {
+  // 64 KB of A per staged tile
+  if (dtype == RLU_F64) return 2048;  // 4 rows x 2048 x 8 B
+  if (dtype == RLU_F32) return 2048;  // 8 rows x 2048 x 4 B
+  return 4096;                        // 8 rows x 4096 x 2 B
+}
+
+template <typename TA, typename TACC, int NT, int NB, int R>
+static int launch_dense_cfg(const void* A, int64_t lda, int64_t m, int64_t n, int l1, int l, const SketchWs& ws,
+                            double* Y, unsigned int* status, int num_sms, cudaStream_t st) {
+  auto kern = k_sketch_dense<TA, TACC, NT, NB, R>;
+  size_t tile_bytes = (size_t)R * ws.chunk * sizeof(TA);
+  size_t fft_bytes = (size_t)2 * l1 * sizeof(typename C2<TACC>::t);
+  size_t smem = tile_bytes > fft_bytes ? tile_bytes : fft_bytes;
+  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+  if (per_sm < 1) return RLU_EINVAL;
+  int64_t groups = cdiv(m, R);
+  int64_t grid = (int64_t)per_sm * num_sms;
+  if (grid > groups) grid = groups;
+  const typename C2<TACC>::t* tw;
+  if constexpr (sizeof(TACC) == 8) tw = ws.tw64; else tw = ws.tw32;
+  kern<<<(unsigned)grid, NT, smem, st>>>(reinterpret_cast<const TA*>(A), lda, m, n, l1, l, ws.chunk, ws.bstart,
+                                         ws.blist, ws.dsign, ws.R, tw, ws.plan, Y, status);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return RLU_OK;
+}
+
+int launch_sketch_dense(const void* A, int64_t lda, int dtype, bool acc64, int64_t m, int64_t n, int l1, int l,
+                        const SketchWs& ws, double* Y, unsigned int* status, int num_sms, cudaStream_t st) {
+  if (dtype == RLU_F64) {
+    if (l1 <= 2048) return launch_dense_cfg<double, double, 256, 8, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 4096) return launch_dense_cfg<double, double, 512, 8, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 8192) return launch_dense_cfg<double, double, 1024, 8, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    return launch_dense_cfg<double, double, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+  }
+  if (acc64) return RLU_EINVAL;
+  if (dtype == RLU_F32) {
+    if (l1 <= 2048) return launch_dense_cfg<float, float, 256, 8, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 4096) return launch_dense_cfg<float, float, 512, 8, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 8192) return launch_dense_cfg<float, float, 1024, 8, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    return launch_dense_cfg<float, float, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+  }
+  if (dtype == RLU_BF16) {
+    using B = __nv_bfloat16;
+    if (l1 <= 2048) return launch_dense_cfg<B, float, 256, 8, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 4096) return launch_dense_cfg<B, float, 512, 8, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 8192) return launch_dense_cfg<B, float, 1024, 8, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    return launch_dense_cfg<B, float, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+  }
+  return RLU_EINVAL;
+}
+
+}  // namespace rlu

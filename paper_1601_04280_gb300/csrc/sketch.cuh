@@ -1,0 +1,39 @@
+// Declarations of the sketch step (step 1 and 2 of Algorithm 1).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rlu {
+
+constexpr int kMaxFftStages = 24;
+
+// Radices of the mixed-radix FFT of length l1, applied in order.
+struct FftPlan {
+  int nstages;
+  int radix[kMaxFftStages];
+};
+
+// Device buffers of the sketch step (owned by the handle).
+struct SketchWs {
+  uint32_t* hs;     // n: bucket h(j) in bits 0..30, sign s(j) < 0 in bit 31
+  float* dsign;     // l1: +-1
+  uint64_t* keys;   // l1: subsample selection keys
+  int32_t* R;       // l: selected frequencies
+  int chunk;        // columns per staged tile of the dense sketch
+  int64_t nchunks;  // ceil(n / chunk)
+  int32_t* bcnt;    // nchunks*l1 + 1: scratch counters
+  int32_t* bstart;  // nchunks*l1 + 1: start of each (chunk, bucket) list
+  uint32_t* blist;  // n: column offset within its chunk | sign bit, sorted by (chunk, bucket, column)
+  double2* tw64;    // l1 twiddles exp(-2 pi i e / l1)
+  float2* tw32;
+  FftPlan plan;
+};
+
+FftPlan make_fft_plan(int N);
+int sketch_chunk_cols(int dtype);
+int launch_sketch_params(const SketchWs& ws, int64_t n, int l1, int l, uint64_t seed, cudaStream_t st);
+int launch_twiddles(int N, double2* tw64, float2* tw32, cudaStream_t st);
+int launch_sketch_dense(const void* A, int64_t lda, int dtype, bool acc64, int64_t m, int64_t n, int l1, int l,
+                        const SketchWs& ws, double* Y, unsigned int* status, int num_sms, cudaStream_t st);
+
+}  // namespace rlu

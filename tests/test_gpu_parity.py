@@ -1,0 +1,263 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Tolerances
+  * sketch parameters h, s, d, R: bit-exact (integer work).
+  * FP64 precision: Y element-wise within 1e-12 * max|Y|; the relative error
+    e = ||LU - PAQ||_F / ||A||_F within 1e-12 (absolute difference of the two
+    e values); factors within 1e-9 relative to their max entry.
+  * FP32 precision: |e_gpu - e_oracle| <= 1e-5 (absolute difference of the two
+    relative errors), and where e_oracle >= 1e-4 also |e_gpu/e_oracle - 1| <=
+    1e-2.  Y element-wise within 5e-6 * max row norm: FP32 sums of n terms carry
+    a relative error of a few n*u_32 in the worst case and ~sqrt(n)*u_32
+    typically (u_32 = 6e-8).
+  * pivots: equal on every step before the first step whose two best
+    candidates, in the oracle, differ by less than 1e-4 of the largest entry
+    of the factored matrix (Y for the row pivots, B for the column pivots):
+    past that step the choice rests on rounding (for exactly rank-k inputs,
+    only the first k steps are compared).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import rlu_inputs as ri
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rg():
+    import paper_1601_04280_gb300 as rg
+    rg.build()
+    rg.load(reload=True)
+    return rg
+
+
+def to_dev(A, dtype):
+    return torch.from_numpy(np.ascontiguousarray(A)).to(device="cuda", dtype=dtype)
+
+
+def run(rg, A_np, k, l, l1, seed, prec, dtype, debug=False):
+    m, n = A_np.shape
+    h = rg.RandLU(m, n, k, l, l1, seed, prec=prec)
+    if debug:
+        h.debug_enable(True)
+    A = to_dev(A_np, dtype)
+    f = h.factor(A, check=False)
+    torch.cuda.synchronize()
+    out = dict(L=f.L.double().cpu().numpy(), U=f.U.double().cpu().numpy(), p=f.p.cpu().numpy(),
+               q=f.q.cpu().numpy(), status=f.status, handle=h)
+    if debug:
+        out["Y"] = h.debug_Y()
+        out["B"] = h.debug_B()
+    return out
+
+
+def separated_prefix(top, scale, thr):
+    """Number of leading steps whose two best candidates differ by more than
+    thr * scale (scale = the largest entry of the factored matrix): beyond the
+    first step that fails, the pivot is decided by rounding."""
+    sep = (top[:, 0] - top[:, 1]) > thr * scale
+    idx = np.nonzero(~sep)[0]
+    return int(idx[0]) if idx.size else len(sep)
+
+
+def check_pivots(g, o, k, exact_rank=False, thr=1e-4):
+    sy = separated_prefix(o.top_y, np.abs(o.Y).max(), thr)
+    if exact_rank:
+        sy = min(sy, k)
+    assert sy >= min(k, 1)
+    assert np.array_equal(g["p"][:sy], o.p[:sy]), "row pivots differ before step %d" % sy
+    if sy == len(o.top_y) or sy >= k:
+        sb = separated_prefix(o.top_b, np.abs(o.B).max(), thr)
+        assert np.array_equal(g["q"][:sb], o.q[:sb]), "column pivots differ before step %d" % sb
+    return sy
+
+
+def check_structure(g, m, n, k):
+    assert np.array_equal(np.sort(g["p"]), np.arange(m))
+    assert np.array_equal(np.sort(g["q"]), np.arange(n))
+    L, U = g["L"], g["U"]
+    assert np.all(np.triu(L[:k], 1) == 0)
+    assert np.all(np.tril(U, -1)[:, :k] == 0)
+    assert np.all(np.diag(U) == 1)
+    assert np.all(np.abs(U) <= 1.0 + 1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Sketch parameters: bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,l1,l,seed", [(1000, 240, 30, 1), (8192, 1600, 220, 2001), (300, 1024, 50, 2**63 + 5)])
+def test_sketch_params_bit_exact(rg, n, l1, l, seed):
+    m = max(l, 16)
+    A = np.random.default_rng(0).standard_normal((m, n)).astype(np.float32)
+    g = run(rg, A, min(l, 8), l, l1, seed, "f32", torch.float32)
+    hh, s, d, R = g["handle"].debug_sketch_params()
+    p = oracle.sketch_params(n, l1, l, seed)
+    assert np.array_equal(hh, p.h) and np.array_equal(s, p.s.astype(np.int8))
+    assert np.array_equal(d, p.d.astype(np.int8)) and np.array_equal(R, p.R)
+
+
+# ---------------------------------------------------------------------------
+# The sketch Y = A S D H R / sqrt(l1)
+# ---------------------------------------------------------------------------
+SKETCH_CASES = [
+    # m, n, l1, l : several row groups with a ragged tail, several column chunks with a ragged tail
+    (257, 5000, 240, 30),
+    (231, 2048, 1600, 220),
+    (150, 300, 960, 120),
+    (40, 4097, 251, 20),   # prime length: generic radix
+    (33, 1500, 22, 11),    # 2 x 11
+    (70, 100, 512, 64),    # l1 > n: empty buckets
+]
+
+
+@pytest.mark.parametrize("m,n,l1,l", SKETCH_CASES)
+def test_sketch_Y_f64(rg, m, n, l1, l):
+    A = np.random.default_rng(m + n).standard_normal((m, n))
+    g = run(rg, A, min(l, 10), l, l1, 77, "f64", torch.float64, debug=True)
+    pr = oracle.sketch_params(n, l1, l, 77)
+    Yo = oracle.fjl(oracle.countsketch(A, pr, l1), pr, l1)
+    assert np.abs(g["Y"] - Yo).max() <= 1e-12 * np.abs(Yo).max()
+
+
+@pytest.mark.parametrize("m,n,l1,l", SKETCH_CASES)
+def test_sketch_Y_f32(rg, m, n, l1, l):
+    A = np.random.default_rng(m * n).standard_normal((m, n)).astype(np.float32)
+    g = run(rg, A, min(l, 10), l, l1, 78, "f32", torch.float32, debug=True)
+    pr = oracle.sketch_params(n, l1, l, 78)
+    Yo = oracle.fjl(oracle.countsketch(A.astype(np.float64), pr, l1), pr, l1)
+    rown = np.linalg.norm(A.astype(np.float64), axis=1).max()
+    assert np.abs(g["Y"] - Yo).max() <= 5e-6 * rown
+
+
+def test_sketch_Y_bf16(rg):
+    m, n, l1, l = 100, 3000, 400, 40
+    A = ri.round_to_bf16(np.random.default_rng(5).standard_normal((m, n)))[0]
+    g = run(rg, A, 10, l, l1, 79, "f32", torch.bfloat16, debug=True)
+    pr = oracle.sketch_params(n, l1, l, 79)
+    Yo = oracle.fjl(oracle.countsketch(A.astype(np.float64), pr, l1), pr, l1)
+    rown = np.linalg.norm(A.astype(np.float64), axis=1).max()
+    assert np.abs(g["Y"] - Yo).max() <= 5e-6 * rown
+
+
+# ---------------------------------------------------------------------------
+# Whole factorizations
+# ---------------------------------------------------------------------------
+def test_dense_f64_1024_parity(rg):
+    w = ri.DENSE_F64_1K
+    A = ri.make_dense(w)
+    o = oracle.factor(A, w.k, w.l, w.l1, w.sketch_seed)
+    g = run(rg, A, w.k, w.l, w.l1, w.sketch_seed, "f64", torch.float64, debug=True)
+    assert g["status"] == 0
+    check_structure(g, w.m, w.n, w.k)
+    check_pivots(g, o, w.k)
+    assert np.abs(g["Y"] - o.Y).max() <= 1e-12 * np.abs(o.Y).max()
+    e_o = oracle.relative_residual(A, o.L, o.U, o.p, o.q)
+    e_g = oracle.relative_residual(A, g["L"], g["U"], g["p"], g["q"])
+    assert abs(e_g - e_o) <= 1e-12, (e_g, e_o)
+    assert np.abs(g["L"] - o.L).max() <= 1e-9 * np.abs(o.L).max()
+    assert np.abs(g["U"] - o.U).max() <= 1e-9
+    assert np.abs(g["B"] - o.B).max() <= 1e-9 * np.abs(o.B).max()
+
+
+F32_CASES = [
+    # m, n, k, l, l1, rank, noise
+    (1000, 1200, 20, 30, 240, 20, 1e-6),
+    (777, 2100, 40, 52, 400, 60, 1e-3),
+    (2500, 700, 64, 80, 640, 64, 1e-6),
+]
+
+
+@pytest.mark.parametrize("m,n,k,l,l1,rank,noise", F32_CASES)
+def test_dense_f32_parity(rg, m, n, k, l, l1, rank, noise):
+    A = ri.dense_low_rank_plus_noise(m, n, rank, noise, seed=m + n)
+    o = oracle.factor(A.astype(np.float64), k, l, l1, seed=91)
+    g = run(rg, A, k, l, l1, 91, "f32", torch.float32, debug=True)
+    assert g["status"] == 0
+    check_structure(g, m, n, k)
+    check_pivots(g, o, k)
+    e_o = oracle.relative_residual(A, o.L, o.U, o.p, o.q)
+    e_g = oracle.relative_residual(A, g["L"], g["U"], g["p"], g["q"])
+    assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
+    if e_o >= 1e-4:
+        assert abs(e_g / e_o - 1) <= 1e-2
+
+
+def test_dense_f32_8192_full_size(rg):
+    """The dense FP32 workload at full size, in the configuration the bench times."""
+    w = ri.DENSE_F32_8K
+    A = ri.make_dense(w)
+    o = oracle.factor(A.astype(np.float64), w.k, w.l, w.l1, w.sketch_seed)
+    g = run(rg, A, w.k, w.l, w.l1, w.sketch_seed, "f32", torch.float32)
+    assert g["status"] == 0
+    check_structure(g, w.m, w.n, w.k)
+    check_pivots(g, o, w.k)
+    e_o = oracle.relative_residual(A, o.L, o.U, o.p, o.q)
+    e_g = oracle.relative_residual(A, g["L"], g["U"], g["p"], g["q"])
+    assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
+
+
+def test_exact_rank_recovery_f64(rg):
+    A = ri.exact_rank(600, 500, 12, seed=3)
+    g = run(rg, A, 12, 16, 128, 5, "f64", torch.float64)
+    e = oracle.relative_residual(A, g["L"], g["U"], g["p"], g["q"])
+    assert e < 1e-12
+    o = oracle.factor(A, 12, 16, 128, 5)
+    check_pivots(g, o, 12, exact_rank=True)
+
+
+def test_k_equals_l_and_minimal_height(rg):
+    # k = l = m: the sketch is square, every row becomes a pivot row
+    A = np.random.default_rng(8).standard_normal((24, 300))
+    o = oracle.factor(A, 24, 24, 64, 4)
+    g = run(rg, A, 24, 24, 64, 4, "f64", torch.float64)
+    assert np.array_equal(g["p"], o.p) and np.array_equal(g["q"], o.q)
+    e_o = oracle.relative_residual(A, o.L, o.U, o.p, o.q)
+    e_g = oracle.relative_residual(A, g["L"], g["U"], g["p"], g["q"])
+    assert abs(e_g - e_o) <= 1e-12
+
+
+def test_zero_matrix_reports_rank_warning(rg):
+    m, n = 64, 80
+    A = np.zeros((m, n))
+    g = run(rg, A, 4, 6, 32, 1, "f64", torch.float64)
+    assert g["status"] == rg.RLU_WRANK
+    o = oracle.factor(A, 4, 6, 32, 1)
+    assert np.array_equal(g["p"], o.p) and np.array_equal(g["q"], o.q)
+    assert np.all(g["L"] == 0)
+
+
+def test_nonfinite_input_rejected(rg):
+    A = np.random.default_rng(1).standard_normal((100, 200)).astype(np.float32)
+    A[37, 150] = np.nan
+    g = run(rg, A, 5, 8, 64, 1, "f32", torch.float32)
+    assert g["status"] == rg.RLU_ENONFINITE
+
+
+def test_deterministic_bitwise(rg):
+    A = ri.dense_low_rank_plus_noise(900, 1100, 30, 1e-4, seed=4)
+    a = run(rg, A, 30, 40, 320, 12, "f32", torch.float32)
+    b = run(rg, A, 30, 40, 320, 12, "f32", torch.float32)
+    for key in ("L", "U", "p", "q"):
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_host_and_async_entry_points_match(rg):
+    m, n, k, l, l1 = 500, 700, 16, 24, 200
+    A = ri.dense_low_rank_plus_noise(m, n, 16, 1e-5, seed=6)
+    h = rg.RandLU(m, n, k, l, l1, 33, prec="f32")
+    Ad = to_dev(A, torch.float32)
+    ref = h.factor(Ad)
+    outs = h.alloc_outputs()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    h.factor_async(Ad, outs, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    Ah = torch.from_numpy(A).pin_memory()
+    oh = (torch.empty((m, k)).pin_memory(), torch.empty((k, n)).pin_memory(),
+          torch.empty(m, dtype=torch.int64).pin_memory(), torch.empty(n, dtype=torch.int64).pin_memory())
+    h.factor_host(Ah, oh)
+    for a, b, c in zip((ref.L, ref.U, ref.p, ref.q), outs, oh):
+        assert torch.equal(a.cpu(), b.cpu()) and torch.equal(a.cpu(), c)
