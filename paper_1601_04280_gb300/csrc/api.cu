@@ -35,7 +35,7 @@ struct rlu_ctx {
   PivLuWs pw{};
   int64_t* perm_y = nullptr;
   int64_t* perm_b = nullptr;
-  double* Lk = nullptr;
+  void* Lk = nullptr;
   double* gram_part = nullptr;
   int max_gram_splits = 0;
   double* G = nullptr;
@@ -209,15 +209,15 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   if ((rc = launch_bgemm_simt(h->W, f64 ? 1 : 0, A, lda, dtype, m, n, k, h->B, st))) return rc;
   if ((rc = mark(h, 7, st))) return rc;
   if (h->debug && h->Bdbg)
-    RLU_CUDA_TRY(cudaMemcpyAsync(h->Bdbg, h->B, (f64 ? 8 : 4) * (size_t)k * n, cudaMemcpyDeviceToDevice, st));
+    RLU_CUDA_TRY(cudaMemcpyAsync(h->Bdbg, h->B, 8 * (size_t)k * n, cudaMemcpyDeviceToDevice, st));
   // step 6: B Q = L_b U_b as partial pivoting of B^T
   h->pw.perm = h->perm_b;
   if (f64)
     rc = launch_pivoted_lu<double>(reinterpret_cast<double*>(h->B), n, k, 1, n, k, h->pw, h->status_dev,
                                    h->num_sms, st);
   else
-    rc = launch_pivoted_lu<float>(reinterpret_cast<float*>(h->B), n, k, 1, n, k, h->pw, h->status_dev, h->num_sms,
-                                  st);
+    rc = launch_pivoted_lu<df32>(reinterpret_cast<df32*>(h->B), n, k, 1, n, k, h->pw, h->status_dev, h->num_sms,
+                                 st);
   if (rc) return rc;
   if ((rc = mark(h, 8, st))) return rc;
   // step 7: L = L_y L_b, U = U_b, p, q
@@ -225,7 +225,7 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   aa.m = m; aa.n = n; aa.k = k;
   aa.Lk = h->Lk; aa.perm_y = h->perm_y; aa.perm_b = h->perm_b; aa.Bp = h->B;
   aa.LyP = h->LyP; aa.Lb = h->Lb; aa.L = L; aa.U = U; aa.p = p; aa.q = q;
-  rc = f64 ? launch_assemble<double>(aa, st) : launch_assemble<float>(aa, st);
+  rc = f64 ? launch_assemble<double, double>(aa, st) : launch_assemble<df32, float>(aa, st);
   if (rc) return rc;
   if ((rc = mark(h, 9, st))) return rc;
   h->last_prec = h->prec;
@@ -307,7 +307,7 @@ int rlu_create(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t 
   h->pw.bar = (unsigned int*)next();
   h->pw.max_ctas = kMaxPivCtas;
   h->pw.max_cols = l > k ? l : k;
-  h->Lk = (double*)next();
+  h->Lk = next();
   h->gram_part = (double*)next();
   h->max_gram_splits = max_gram_splits_for(k, sms);
   h->G = (double*)next();
@@ -488,9 +488,9 @@ int rlu_debug_B(rlu_t h, double* B_host) {
   if (h->last_prec == RLU_PREC_F64) {
     RLU_CUDA_TRY(cudaMemcpy(B_host, h->Bdbg, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
   } else {
-    std::vector<float> tmp(cnt);
-    RLU_CUDA_TRY(cudaMemcpy(tmp.data(), h->Bdbg, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < cnt; ++i) B_host[i] = tmp[i];
+    std::vector<float> tmp(2 * cnt);  // float-float pairs
+    RLU_CUDA_TRY(cudaMemcpy(tmp.data(), h->Bdbg, sizeof(float) * 2 * cnt, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < cnt; ++i) B_host[i] = (double)tmp[2 * i] + (double)tmp[2 * i + 1];
   }
   return RLU_OK;
 }

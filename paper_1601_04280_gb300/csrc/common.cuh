@@ -128,6 +128,84 @@ template <> __device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat
 template <typename T> __device__ __forceinline__ bool finite_(T x) { return isfinite(to_float(x)); }
 template <> __device__ __forceinline__ bool finite_<double>(double x) { return isfinite(x); }
 
+// ---------------------------------------------------------------------------
+// Float-float ("double-single") numbers: value = hi + lo with |lo| <= ulp(hi)/2,
+// about 48 significant bits on the FP32 pipes.  Built from the error-free
+// transformations of Knuth (TwoSum), Dekker/Fast2Sum and the FMA-based TwoProd
+// (Dekker 1971; Hida, Li and Bailey, "Algorithms for quad-double precision
+// floating point arithmetic", 2001).
+// ---------------------------------------------------------------------------
+struct __align__(8) df32 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df32 df_make(float hi, float lo) { df32 r; r.hi = hi; r.lo = lo; return r; }
+
+// s + e = a + b exactly (Knuth TwoSum)
+__device__ __forceinline__ df32 two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df_make(s, e);
+}
+// s + e = a + b exactly when |a| >= |b| (Fast2Sum)
+__device__ __forceinline__ df32 quick_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return df_make(s, e);
+}
+__device__ __forceinline__ df32 operator+(df32 a, df32 b) {
+  df32 s = two_sum(a.hi, b.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return quick_two_sum(s.hi, e);
+}
+__device__ __forceinline__ df32 operator-(df32 a) { return df_make(-a.hi, -a.lo); }
+__device__ __forceinline__ df32 operator-(df32 a, df32 b) { return a + (-b); }
+__device__ __forceinline__ df32 operator*(df32 a, df32 b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df32 operator/(df32 a, df32 b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  df32 r = a - b * df_make(q1, 0.f);
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  return quick_two_sum(q1, q2);
+}
+// c + a * b, one name for every arithmetic type of the templated kernels
+__device__ __forceinline__ df32 mad(df32 a, df32 b, df32 c) { return c + a * b; }
+__device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ bool operator!=(df32 a, df32 b) { return a.hi != b.hi || a.lo != b.lo; }
+__device__ __forceinline__ bool operator==(df32 a, df32 b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ df32 df_from_double(double x) {
+  float hi = __double2float_rn(x);
+  return df_make(hi, __double2float_rn(x - (double)hi));
+}
+__device__ __forceinline__ df32 abs_(df32 x) { return x.hi < 0.f ? -x : x; }
+template <> __device__ __forceinline__ double to_double<df32>(df32 x) { return (double)x.hi + (double)x.lo; }
+template <> __device__ __forceinline__ float to_float<df32>(df32 x) { return x.hi; }
+
+// Conversions used by templated kernels: cvt<To>(from)
+template <typename To> struct Cvt;
+template <> struct Cvt<double> {
+  template <typename F> __device__ static double f(F x) { return to_double(x); }
+};
+template <> struct Cvt<float> {
+  template <typename F> __device__ static float f(F x) { return to_float(x); }
+};
+template <> struct Cvt<df32> {
+  __device__ static df32 f(double x) { return df_from_double(x); }
+  __device__ static df32 f(float x) { return df_make(x, 0.f); }
+  __device__ static df32 f(__nv_bfloat16 x) { return df_make(__bfloat162float(x), 0.f); }
+  __device__ static df32 f(df32 x) { return x; }
+};
+template <typename To, typename F> __device__ __forceinline__ To cvt(F x) { return Cvt<To>::f(x); }
+template <typename T> __device__ __forceinline__ T zero_() { return cvt<T>(0.0); }
+template <typename T> __device__ __forceinline__ T one_() { return cvt<T>(1.0); }
+
 // Process-wide count of kernels this library has launched (a test hook).
 void note_launch(int count = 1);
 

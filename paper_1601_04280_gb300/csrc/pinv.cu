@@ -13,8 +13,9 @@ namespace rlu {
 
 // Lk[i, c] (c < k) from the packed panel LU of Y: row i pivoted at step s
 // holds L in columns < s and U from s on; unpivoted rows hold L everywhere.
+template <typename TL>
 __global__ void k_extract_Lk(int64_t m, int l, int k, const double* __restrict__ Y, const int32_t* __restrict__ pstep,
-                             double* __restrict__ Lk) {
+                             TL* __restrict__ Lk) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m * k) return;
   int64_t i = e / k;
@@ -23,30 +24,41 @@ __global__ void k_extract_Lk(int64_t m, int l, int k, const double* __restrict__
   double v;
   if (s < 0 || c < s) v = Y[i * l + c];
   else v = (c == s) ? 1.0 : 0.0;
-  Lk[e] = v;
+  Lk[e] = cvt<TL>(v);
 }
 
 // Blocked right-looking Cholesky G = R^T R (R upper, overwriting the upper
-// triangle of S), then R^{-1} column by column; one cooperative kernel with
-// three grid barriers per 32-wide panel.
+// triangle of S), then R^{-1}; one cooperative kernel, FP64, with three grid
+// barriers per 32-wide panel.
 constexpr int kNb = 32;
 
 __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S, double* __restrict__ Rinv,
                                                   unsigned int* bar, unsigned int* status) {
-  extern __shared__ __align__(16) double xs[];  // 8 warps x k
+  // FP64 on this part has long latency as well as low throughput, so every
+  // sequential chain below is spread over threads: one thread per element in
+  // the diagonal factor, one warp per column (lanes = rows) in the triangular
+  // solves, with reciprocals of the diagonal computed once per block.
   __shared__ double blk[kNb][kNb + 1];
+  __shared__ double rdiag[kNb];
+  __shared__ df32 tA[kNb][kNb + 1];
+  __shared__ df32 tB[kNb][kNb + 1];
   const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = 8;
   const int nt = (k + kNb - 1) / kNb;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid;
+  const int64_t gwarp = (int64_t)blockIdx.x * NW + warp;
+  const int64_t nwarps = (int64_t)gridDim.x * NW;
   unsigned int epoch = 0;
   for (int J = 0; J < nt; ++J) {
     const int c0 = J * kNb;
     const int jb = min(kNb, k - c0);
+    // (a) diagonal block by CTA 0, right-looking, all threads
     if (blockIdx.x == 0) {
-      for (int e = tid; e < jb * jb; e += blockDim.x) {
-        int r = e / jb, c = e % jb;
-        blk[r][c] = S[(int64_t)(c0 + r) * k + c0 + c];
+      for (int e = tid; e < kNb * kNb; e += blockDim.x) {
+        int r = e / kNb, c = e % kNb;
+        blk[r][c] = (r < jb && c < jb) ? S[(int64_t)(c0 + r) * k + c0 + c] : (r == c ? 1.0 : 0.0);
       }
       __syncthreads();
       for (int c = 0; c < jb; ++c) {
@@ -56,15 +68,16 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
             set_flag(status, FLAG_ZERO_PIVOT);
             d = 1.0;
           }
-          blk[c][c] = sqrt(d);
+          d = sqrt(d);
+          blk[c][c] = d;
+          rdiag[c] = 1.0 / d;
         }
         __syncthreads();
-        const double dc = blk[c][c];
-        for (int t = c + 1 + tid; t < jb; t += blockDim.x) blk[c][t] /= dc;
+        if (tid > c && tid < jb) blk[c][tid] *= rdiag[c];
         __syncthreads();
-        for (int e = tid; e < jb * jb; e += blockDim.x) {
-          int r = e / jb, t = e % jb;
-          if (r > c && t >= r) blk[r][t] -= blk[c][r] * blk[c][t];
+        for (int e = tid; e < kNb * kNb; e += blockDim.x) {
+          int r = e / kNb, t = e % kNb;
+          if (r > c && t >= r && t < jb) blk[r][t] -= blk[c][r] * blk[c][t];
         }
         __syncthreads();
       }
@@ -74,63 +87,146 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
       }
     }
     if (!grid_barrier(bar, ++epoch, status)) return;
-    // panel row: S[J, K] <- R_JJ^{-T} S[J, K] for all columns right of the block
     const int rest = k - (c0 + jb);
-    for (int64_t col = gtid; col < rest; col += gthreads) {
-      const int gc = c0 + jb + (int)col;
-      double x[kNb];
-      for (int r = 0; r < jb; ++r) {
-        double v = S[(int64_t)(c0 + r) * k + gc];
-        for (int t = 0; t < r; ++t) v -= S[(int64_t)(c0 + t) * k + c0 + r] * x[t];
-        x[r] = v / S[(int64_t)(c0 + r) * k + c0 + r];
-      }
-      for (int r = 0; r < jb; ++r) S[(int64_t)(c0 + r) * k + gc] = x[r];
-    }
-    if (!grid_barrier(bar, ++epoch, status)) return;
-    // trailing update of the upper triangle: S[r, c] -= sum_t S[t, r] S[t, c]
-    const int64_t tot = (int64_t)rest * rest;
-    for (int64_t e = gtid; e < tot; e += gthreads) {
-      const int r = c0 + jb + (int)(e / rest), c = c0 + jb + (int)(e % rest);
-      if (c < r) continue;
-      double s = 0.0;
-      for (int t = 0; t < jb; ++t) s += S[(int64_t)(c0 + t) * k + r] * S[(int64_t)(c0 + t) * k + c];
-      S[(int64_t)r * k + c] -= s;
-    }
-    if (!grid_barrier(bar, ++epoch, status)) return;
-  }
-  // R^{-1}: column c by back-substitution, one warp per column
-  const int warp = tid >> 5, lane = tid & 31;
-  double* x = xs + (int64_t)warp * k;
-  const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t c = gwarp; c < k; c += nwarps) {
-    if (lane == 0) x[c] = 1.0 / S[c * k + c];
-    __syncwarp();
-    for (int64_t i = c - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int64_t t = i + 1 + lane; t <= c; t += 32) s += S[i * k + t] * x[t];
+    if (rest > 0) {
+      // (b) panel row S[J, K] <- R_JJ^{-T} S[J, K]; warp per column, lane = row r:
+      // after lane t finalizes x_t, lanes r > t remove R[t][r] x_t.
+      double rcol[kNb];  // rcol[t] = R_JJ[t][lane]
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) x[i] = -s / S[i * k + i];
-      __syncwarp();
+      for (int t = 0; t < kNb; ++t) rcol[t] = (t < jb && lane < jb) ? S[(int64_t)(c0 + t) * k + c0 + lane] : 0.0;
+      const double rinv_l = (lane < jb) ? 1.0 / rcol[lane < kNb ? lane : 0] : 1.0;
+      for (int64_t col = gwarp; col < rest; col += nwarps) {
+        const int gc = c0 + jb + (int)col;
+        double b = (lane < jb) ? S[(int64_t)(c0 + lane) * k + gc] : 0.0;
+        double xl = 0.0;
+#pragma unroll
+        for (int t = 0; t < kNb; ++t) {
+          const double xt_local = (lane == t) ? b * rinv_l : 0.0;
+          const double xt = __shfl_sync(0xffffffffu, xt_local, t);
+          if (lane == t) xl = xt;
+          if (lane > t) b -= rcol[t] * xt;
+        }
+        if (lane < jb) S[(int64_t)(c0 + lane) * k + gc] = xl;
+      }
+      if (!grid_barrier(bar, ++epoch, status)) return;
+      // (c) trailing update of the upper triangle: S[r, c] -= sum_t S[t, r] S[t, c]
+      const int64_t tot = (int64_t)rest * rest;
+      for (int64_t e = gtid; e < tot; e += gthreads) {
+        const int rr = (int)(e / rest), cc = (int)(e - (int64_t)rr * rest);
+        if (cc < rr) continue;
+        const int r = c0 + jb + rr, c = c0 + jb + cc;
+        double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+        for (int t = 0; t < kNb; t += 2) {
+          if (t < jb) acc0 += S[(int64_t)(c0 + t) * k + r] * S[(int64_t)(c0 + t) * k + c];
+          if (t + 1 < jb) acc1 += S[(int64_t)(c0 + t + 1) * k + r] * S[(int64_t)(c0 + t + 1) * k + c];
+        }
+        S[(int64_t)r * k + c] -= acc0 + acc1;
+      }
+      if (!grid_barrier(bar, ++epoch, status)) return;
     }
-    for (int64_t i = lane; i < k; i += 32) Rinv[i * k + c] = (i <= c) ? x[i] : 0.0;
-    __syncwarp();
+  }
+  // R^{-1} (upper) by 32 x 32 blocks: the diagonal blocks X_JJ = R_JJ^{-1}
+  // (FP64, warp per column: lane t finalizes x_t from the bottom up), then
+  // block diagonal d = 1, 2, ... (one grid barrier each), in float-float:
+  //   X_{I,I+d} = -X_II * sum_{K=I+1}^{I+d} R_{I,K} X_{K,I+d}.
+  for (int J = blockIdx.x; J < nt; J += gridDim.x) {
+    const int c0 = J * kNb;
+    const int jb = min(kNb, k - c0);
+    double rrow[kNb];  // rrow[t] = R_JJ[lane][t]
+#pragma unroll
+    for (int t = 0; t < kNb; ++t) rrow[t] = (t < jb && lane < jb) ? S[(int64_t)(c0 + lane) * k + c0 + t] : 0.0;
+    const double rinv_l = (lane < jb) ? 1.0 / S[(int64_t)(c0 + lane) * k + c0 + lane] : 1.0;
+    for (int c = warp; c < jb; c += NW) {
+      double b = (lane == c) ? 1.0 : 0.0;
+      double xl = 0.0;
+#pragma unroll
+      for (int t = kNb - 1; t >= 0; --t) {
+        const double xt_local = (lane == t && t <= c) ? b * rinv_l : 0.0;
+        const double xt = __shfl_sync(0xffffffffu, xt_local, t);
+        if (lane == t) xl = xt;
+        if (lane < t) b -= rrow[t] * xt;
+      }
+      if (lane < jb) Rinv[(int64_t)(c0 + lane) * k + c0 + c] = (lane <= c) ? xl : 0.0;
+    }
+  }
+  // zero the strictly lower blocks of R^{-1}
+  for (int64_t e = gtid; e < (int64_t)k * k; e += gthreads) {
+    const int64_t r = e / k, c = e - r * k;
+    if (r / kNb > c / kNb) Rinv[e] = 0.0;
+  }
+  for (int d = 1; d < nt; ++d) {
+    if (!grid_barrier(bar, ++epoch, status)) return;
+    for (int I = blockIdx.x; I + d < nt; I += gridDim.x) {
+      const int r0 = I * kNb, cc0 = (I + d) * kNb;
+      const int rb = min(kNb, k - r0), cb = min(kNb, k - cc0);
+      df32 acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = df_make(0.f, 0.f);
+      for (int K = I + 1; K <= I + d; ++K) {
+        const int t0 = K * kNb, tb = min(kNb, k - t0);
+        __syncthreads();
+        for (int e = tid; e < kNb * kNb; e += blockDim.x) {
+          int r = e / kNb, c = e % kNb;
+          tA[r][c] = df_from_double((r < rb && c < tb) ? S[(int64_t)(r0 + r) * k + t0 + c] : 0.0);
+          tB[r][c] = df_from_double((r < tb && c < cb) ? Rinv[(int64_t)(t0 + r) * k + cc0 + c] : 0.0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = tid + q * 256, r = e / kNb, c = e % kNb;
+#pragma unroll 8
+          for (int t = 0; t < kNb; ++t) acc[q] = mad(tA[r][t], tB[t][c], acc[q]);
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < kNb * kNb; e += blockDim.x) {
+        int r = e / kNb, c = e % kNb;
+        tA[r][c] = df_from_double((r < rb && c < rb) ? Rinv[(int64_t)(r0 + r) * k + r0 + c] : 0.0);  // X_II
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + q * 256, r = e / kNb, c = e % kNb;
+        tB[r][c] = acc[q];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + q * 256, r = e / kNb, c = e % kNb;
+        df32 s2 = df_make(0.f, 0.f);
+#pragma unroll 8
+        for (int t = 0; t < kNb; ++t) s2 = mad(tA[r][t], tB[t][c], s2);
+        if (r < rb && c < cb) Rinv[(int64_t)(r0 + r) * k + cc0 + c] = -to_double(s2);
+      }
+      __syncthreads();
+    }
   }
 }
 
-// Lk and the Gram matrix G = Lk^T Lk (split over row ranges, summed in fixed order).
+// Lk and the Gram matrix G = Lk^T Lk (split over row ranges, summed in fixed
+// order).  FP64 in the FP64 mode; float-float (about 48 bits) otherwise.
 int launch_gram(const PinvArgs& a, cudaStream_t st) {
   const int64_t m = a.m;
   const int k = a.k, l = a.l;
-  k_extract_Lk<<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, l, k, a.Y, a.pstep, a.Lk);
-  RLU_CUDA_TRY(cudaGetLastError());
-  note_launch();
   const int64_t tiles = cdiv(k, 64) * cdiv(k, 64);
   int S = (int)min64(a.max_gram_splits, max64(1, cdiv(2 * a.num_sms, tiles)));
   S = (int)min64(S, max64(1, cdiv(m, 64)));
-  int rc = gemm_simt<double, double, double, double>(st, k, k, m, a.Lk, 1, k, a.Lk, k, 1, a.gram_part, k, 1, S,
-                                                     (int64_t)k * k);
+  int rc;
+  if (a.w64) {
+    double* Lk = reinterpret_cast<double*>(a.Lk);
+    k_extract_Lk<double><<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, l, k, a.Y, a.pstep, Lk);
+    RLU_CUDA_TRY(cudaGetLastError());
+    note_launch();
+    rc = gemm_simt<double, double, double, double>(st, k, k, m, Lk, 1, k, Lk, k, 1, a.gram_part, k, 1, S,
+                                                   (int64_t)k * k);
+  } else {
+    df32* Lk = reinterpret_cast<df32*>(a.Lk);
+    k_extract_Lk<df32><<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, l, k, a.Y, a.pstep, Lk);
+    RLU_CUDA_TRY(cudaGetLastError());
+    note_launch();
+    rc = gemm_simt<df32, df32, double, df32>(st, k, k, m, Lk, 1, k, Lk, k, 1, a.gram_part, k, 1, S,
+                                             (int64_t)k * k);
+  }
   if (rc) return rc;
   k_sum_slices<double><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>((int64_t)k * k, S, a.gram_part, a.G);
   RLU_CUDA_TRY(cudaGetLastError());
@@ -138,16 +234,15 @@ int launch_gram(const PinvArgs& a, cudaStream_t st) {
   return RLU_OK;
 }
 
-// Cholesky G = R^T R and R^{-1}.
+// Cholesky G = R^T R and R^{-1} (FP64).
 int launch_chol(const PinvArgs& a, cudaStream_t st) {
   const int k = a.k;
   RLU_CUDA_TRY(cudaMemsetAsync(a.bar, 0, sizeof(unsigned int), st));
-  int G = a.num_sms;
-  size_t smem = (size_t)8 * k * sizeof(double);
-  RLU_CUDA_TRY(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = 0;
   int per_sm = 0;
   RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_inv, 256, smem));
   if (per_sm < 1) return RLU_EINVAL;
+  int G = a.num_sms;
   double* Sm = a.G;
   double* Ri = a.Rinv;
   int kk = k;
@@ -159,20 +254,23 @@ int launch_chol(const PinvArgs& a, cudaStream_t st) {
   return RLU_OK;
 }
 
-// G^{-1} = R^{-1} R^{-T}, then W = G^{-1} Lk^T (k x m), FP64 accumulate,
-// stored in the B-product's type.
+// G^{-1} = R^{-1} R^{-T}, then W = G^{-1} Lk^T (k x m).  FP64 in the FP64
+// mode; float-float products otherwise, W stored as FP32.
 int launch_wform(const PinvArgs& a, cudaStream_t st) {
   const int64_t m = a.m;
   const int k = a.k;
-  int rc = gemm_simt<double, double, double, double>(st, k, k, k, a.Rinv, k, 1, a.Rinv, 1, k, a.Ginv, k, 1);
+  int rc;
+  if (a.w64) {
+    rc = gemm_simt<double, double, double, double>(st, k, k, k, a.Rinv, k, 1, a.Rinv, 1, k, a.Ginv, k, 1);
+    if (rc) return rc;
+    return gemm_simt<double, double, double, double>(st, k, m, k, a.Ginv, k, 1,
+                                                     reinterpret_cast<const double*>(a.Lk), 1, k,
+                                                     reinterpret_cast<double*>(a.W), m, 1);
+  }
+  rc = gemm_simt<double, double, double, df32>(st, k, k, k, a.Rinv, k, 1, a.Rinv, 1, k, a.Ginv, k, 1);
   if (rc) return rc;
-  if (a.w64)
-    rc = gemm_simt<double, double, double, double>(st, k, m, k, a.Ginv, k, 1, a.Lk, 1, k,
-                                                   reinterpret_cast<double*>(a.W), m, 1);
-  else
-    rc = gemm_simt<double, double, float, double>(st, k, m, k, a.Ginv, k, 1, a.Lk, 1, k,
-                                                  reinterpret_cast<float*>(a.W), m, 1);
-  return rc;
+  return gemm_simt<double, df32, float, df32>(st, k, m, k, a.Ginv, k, 1, reinterpret_cast<const df32*>(a.Lk), 1,
+                                              k, reinterpret_cast<float*>(a.W), m, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -180,13 +278,13 @@ int launch_wform(const PinvArgs& a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // L_y in P order: LyP[t, c] = Lk[perm[t], c]
 template <typename T>
-__global__ void k_build_LyP(int64_t m, int k, const double* __restrict__ Lk, const int64_t* __restrict__ perm,
+__global__ void k_build_LyP(int64_t m, int k, const T* __restrict__ Lk, const int64_t* __restrict__ perm,
                             T* __restrict__ LyP) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m * k) return;
   int64_t t = e / k;
   int c = (int)(e - t * k);
-  LyP[e] = (T)Lk[perm[t] * k + c];
+  LyP[e] = Lk[perm[t] * k + c];
 }
 
 // From the packed column-pivoted LU of B (k x n, row-major, columns never
@@ -198,42 +296,44 @@ __global__ void k_build_Lb(int k, int64_t n, const T* __restrict__ Bp, const int
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= k * k) return;
   int c = e / k, j = e % k;
-  Lb[e] = (c >= j) ? Bp[(int64_t)c * n + q[j]] : T(0);
+  Lb[e] = (c >= j) ? Bp[(int64_t)c * n + q[j]] : zero_<T>();
 }
 
-template <typename T>
+template <typename T, typename TO>
 __global__ void k_build_U(int k, int64_t n, const T* __restrict__ Bp, const int64_t* __restrict__ q,
-                          T* __restrict__ U) {
+                          TO* __restrict__ U) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)k * n) return;
   int64_t c = e / n, t = e - c * n;
-  T v;
-  if (t > c) v = Bp[c * n + q[t]];
-  else v = (t == c) ? T(1) : T(0);
+  TO v;
+  if (t > c) v = cvt<TO>(Bp[c * n + q[t]]);
+  else v = (t == c) ? TO(1) : TO(0);
   U[e] = v;
 }
 
-template <typename T>
+template <typename T, typename TO>
 int launch_assemble(const AssembleArgs& a, cudaStream_t st) {
   const int64_t m = a.m, n = a.n;
   const int k = a.k;
   T* LyP = reinterpret_cast<T*>(a.LyP);
   T* Lb = reinterpret_cast<T*>(a.Lb);
   const T* Bp = reinterpret_cast<const T*>(a.Bp);
-  k_build_LyP<T><<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, k, a.Lk, a.perm_y, LyP);
+  k_build_LyP<T><<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, k, reinterpret_cast<const T*>(a.Lk), a.perm_y,
+                                                              LyP);
   k_build_Lb<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(k, n, Bp, a.perm_b, Lb);
-  k_build_U<T><<<(unsigned)cdiv((int64_t)k * n, 256), 256, 0, st>>>(k, n, Bp, a.perm_b, reinterpret_cast<T*>(a.U));
+  k_build_U<T, TO><<<(unsigned)cdiv((int64_t)k * n, 256), 256, 0, st>>>(k, n, Bp, a.perm_b,
+                                                                          reinterpret_cast<TO*>(a.U));
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch(3);
-  int rc = gemm_simt<T, T, T, T>(st, m, k, k, LyP, k, 1, Lb, k, 1, reinterpret_cast<T*>(a.L), k, 1);
+  int rc = gemm_simt<T, T, TO, T>(st, m, k, k, LyP, k, 1, Lb, k, 1, reinterpret_cast<TO*>(a.L), k, 1);
   if (rc) return rc;
   RLU_CUDA_TRY(cudaMemcpyAsync(a.p, a.perm_y, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
   RLU_CUDA_TRY(cudaMemcpyAsync(a.q, a.perm_b, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, st));
   return RLU_OK;
 }
 
-template int launch_assemble<double>(const AssembleArgs&, cudaStream_t);
-template int launch_assemble<float>(const AssembleArgs&, cudaStream_t);
+template int launch_assemble<double, double>(const AssembleArgs&, cudaStream_t);
+template int launch_assemble<df32, float>(const AssembleArgs&, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // B = W A (first version: SIMT, FP32 or FP64 accumulate)
@@ -246,11 +346,10 @@ int launch_bgemm_simt(const void* W, int w64, const void* A, int64_t lda, int dt
                                                      (double*)B, n, 1);
   }
   if (dtype == RLU_F32)
-    return gemm_simt<float, float, float, float>(st, k, n, m, (const float*)W, m, 1, (const float*)A, lda, 1,
-                                                 (float*)B, n, 1);
+    return gemm_chunked<float, float>(st, k, n, m, (const float*)W, m, (const float*)A, lda, (df32*)B, n);
   if (dtype == RLU_BF16)
-    return gemm_simt<float, __nv_bfloat16, float, float>(st, k, n, m, (const float*)W, m, 1,
-                                                         (const __nv_bfloat16*)A, lda, 1, (float*)B, n, 1);
+    return gemm_chunked<float, __nv_bfloat16>(st, k, n, m, (const float*)W, m, (const __nv_bfloat16*)A, lda,
+                                              (df32*)B, n);
   return RLU_EINVAL;
 }
 

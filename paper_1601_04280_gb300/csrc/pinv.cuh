@@ -10,7 +10,7 @@ struct PinvArgs {
   int k, l;
   const double* Y;       // m x l packed panel LU (original row order)
   const int32_t* pstep;  // m
-  double* Lk;            // m x k
+  void* Lk;              // m x k, double if w64 else float-float
   double* gram_part;     // max_gram_splits x k x k
   int max_gram_splits;
   double* G;             // k x k (Cholesky overwrites its upper triangle)
@@ -26,7 +26,7 @@ struct PinvArgs {
 struct AssembleArgs {
   int64_t m, n;
   int k;
-  const double* Lk;
+  const void* Lk;         // m x k, same element type as the assembly
   const int64_t* perm_y;  // m
   const int64_t* perm_b;  // n
   const void* Bp;         // k x n packed LU of B
@@ -41,7 +41,7 @@ struct AssembleArgs {
 int launch_gram(const PinvArgs& a, cudaStream_t st);
 int launch_chol(const PinvArgs& a, cudaStream_t st);
 int launch_wform(const PinvArgs& a, cudaStream_t st);
-template <typename T>
+template <typename T, typename TO>
 int launch_assemble(const AssembleArgs& a, cudaStream_t st);
 int launch_bgemm_simt(const void* W, int w64, const void* A, int64_t lda, int dtype, int64_t m, int64_t n, int k,
                       void* B, cudaStream_t st);

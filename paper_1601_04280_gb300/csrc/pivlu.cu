@@ -44,24 +44,26 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
                                                    Cand* __restrict__ cand, T* __restrict__ candrow,
                                                    unsigned int* bar, unsigned int* status) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NW = NT / 32;
   const int G = gridDim.x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * rpc;
   const int nr = (int)max((int64_t)0, min(rpc, rows - r0));
+  const int rp = (int)rpc;
   // shared layout
   T* slab = reinterpret_cast<T*>(smem);                               // nr x cols (SMEM variant)
-  T* urow = slab + (SMEM ? (size_t)rpc * cols : 0);                   // cols
+  T* urow = slab + (SMEM ? (size_t)rp * cols : 0);                    // cols
   T* lval = urow + cols;                                              // rpc
-  int32_t* lpos = reinterpret_cast<int32_t*>(lval + rpc);             // rpc
-  int32_t* lstep = lpos + rpc;                                        // rpc
-  int32_t* pwin = lstep + rpc;                                        // steps
-  __shared__ double red_v[NT / 32];
-  __shared__ int red_p[NT / 32];
-  __shared__ int red_r[NT / 32];
-  __shared__ double s_piv;
+  int32_t* lpos = reinterpret_cast<int32_t*>(lval + rp);              // rpc
+  int32_t* lstep = lpos + rp;                                         // rpc
+  int32_t* pwin = lstep + rp;                                         // steps
+  __shared__ double red_v[NW];
+  __shared__ int red_p[NW];
+  __shared__ int red_r[NW];
+  __shared__ int s_zero;
   __shared__ int s_wrow, s_wpos, s_wcta;
 
-  const bool row_fast = (cs != 1);  // B^T: consecutive rows are contiguous
+  const bool row_fast = (cs == 1) ? false : true;  // B^T: consecutive rows are contiguous in memory
   auto at = [&](int r, int c) -> T& {
     if (SMEM) return slab[(size_t)r * cols + c];
     return xref(X, rs, cs, r0 + r, c);
@@ -69,15 +71,15 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
 
   // load slab, init bookkeeping
   if (SMEM) {
-    const int64_t tot = (int64_t)nr * cols;
-    for (int64_t idx = tid; idx < tot; idx += NT) {
-      int r, c;
-      if (row_fast) { r = (int)(idx % nr); c = (int)(idx / nr); }
-      else { c = (int)(idx % cols); r = (int)(idx / cols); }
-      slab[(size_t)r * cols + c] = xref(X, rs, cs, r0 + r, c);
+    if (row_fast) {
+      for (int c = warp; c < cols; c += NW)
+        for (int r = lane; r < nr; r += 32) slab[(size_t)r * cols + c] = xref(X, rs, cs, r0 + r, c);
+    } else {
+      for (int r = warp; r < nr; r += NW)
+        for (int c = lane; c < cols; c += 32) slab[(size_t)r * cols + c] = xref(X, rs, cs, r0 + r, c);
     }
   }
-  for (int r = tid; r < rpc; r += NT) {
+  for (int r = tid; r < rp; r += NT) {
     lpos[r] = (int32_t)(r0 + r);
     lstep[r] = -1;
   }
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
     int bp = 0x7fffffff, br = -1;
     for (int r = tid; r < nr; r += NT) {
       if (lstep[r] < 0) {
-        double v = (double)abs_(at(r, j));
+        double v = to_double(abs_(at(r, j)));
         int p = lpos[r];
         if (cand_better(v, p, bv, bp)) { bv = v; bp = p; br = r; }
       }
@@ -102,10 +104,10 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
       int orr = __shfl_down_sync(0xffffffffu, br, o);
       if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; br = orr; }
     }
-    if ((tid & 31) == 0) { red_v[tid >> 5] = bv; red_p[tid >> 5] = bp; red_r[tid >> 5] = br; }
+    if (lane == 0) { red_v[warp] = bv; red_p[warp] = bp; red_r[warp] = br; }
     __syncthreads();
     if (tid == 0) {
-      for (int w = 1; w < NT / 32; ++w)
+      for (int w = 1; w < NW; ++w)
         if (cand_better(red_v[w], red_p[w], bv, bp)) { bv = red_v[w]; bp = red_p[w]; br = red_r[w]; }
       Cand cd;
       cd.v = bv;
@@ -123,28 +125,25 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
     }
     // 2. one grid barrier per step
     if (!grid_barrier(bar, (unsigned)(j + 1), status)) return;
-    // 3. every CTA picks the same winner
-    bv = -1.0; bp = 0x7fffffff; int bc = -1;
-    for (int g = tid; g < G; g += NT) {
-      Cand cd = cand[(j & 1) * G + g];
-      if (cd.row >= 0 && cand_better(cd.v, cd.pos, bv, bp)) { bv = cd.v; bp = cd.pos; bc = g; }
-    }
+    // 3. every CTA picks the same winner (warp 0 scans the G candidates)
+    if (warp == 0) {
+      bv = -1.0; bp = 0x7fffffff; int bc = -1;
+      for (int g = lane; g < G; g += 32) {
+        Cand cd = cand[(j & 1) * G + g];
+        if (cd.row >= 0 && cand_better(cd.v, cd.pos, bv, bp)) { bv = cd.v; bp = cd.pos; bc = g; }
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, bv, o);
-      int op = __shfl_down_sync(0xffffffffu, bp, o);
-      int oc = __shfl_down_sync(0xffffffffu, bc, o);
-      if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; bc = oc; }
-    }
-    __syncthreads();
-    if ((tid & 31) == 0) { red_v[tid >> 5] = bv; red_p[tid >> 5] = bp; red_r[tid >> 5] = bc; }
-    __syncthreads();
-    if (tid == 0) {
-      for (int w = 1; w < NT / 32; ++w)
-        if (cand_better(red_v[w], red_p[w], bv, bp)) { bv = red_v[w]; bp = red_p[w]; bc = red_r[w]; }
-      s_wcta = bc;
-      s_wpos = bp;
-      s_wrow = bc >= 0 ? cand[(j & 1) * G + bc].row : -1;
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        int op = __shfl_down_sync(0xffffffffu, bp, o);
+        int oc = __shfl_down_sync(0xffffffffu, bc, o);
+        if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; bc = oc; }
+      }
+      if (lane == 0) {
+        s_wcta = bc;
+        s_wpos = bp;
+        s_wrow = bc >= 0 ? cand[(j & 1) * G + bc].row : -1;
+      }
     }
     __syncthreads();
     const int wcta = s_wcta;
@@ -159,8 +158,8 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
     __syncthreads();
     if (tid == 0) {
       const int w = s_wrow, wpos = s_wpos;
-      s_piv = (double)urow[0];
-      if (s_piv == 0.0 && blockIdx.x == 0) set_flag(status, FLAG_ZERO_PIVOT);
+      s_zero = (urow[0] == zero_<T>()) ? 1 : 0;
+      if (s_zero && blockIdx.x == 0) set_flag(status, FLAG_ZERO_PIVOT);
       // getf2 swap of positions j and wpos
       const int occ = pwin[j];
       pwin[j] = w;
@@ -173,8 +172,8 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
     }
     __syncthreads();
     // 4. scale column j below the pivot, then the rank-1 update
-    const T piv = (T)s_piv;
-    if (piv != T(0)) {
+    if (!s_zero) {
+      const T piv = urow[0];
       for (int r = tid; r < nr; r += NT) {
         if (lstep[r] < 0) {
           T lv = at(r, j) / piv;
@@ -183,16 +182,29 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
         }
       }
       __syncthreads();
-      const int width = cols - j - 1;
-      if (width > 0) {
-        const int64_t tot = (int64_t)nr * width;
-        for (int64_t idx = tid; idx < tot; idx += NT) {
-          int r, c;
-          if (row_fast && !SMEM) { r = (int)(idx % nr); c = (int)(idx / nr); }
-          else { c = (int)(idx % width); r = (int)(idx / width); }
-          if (lstep[r] < 0) {
-            T& x = at(r, j + 1 + c);
-            x = x - lval[r] * urow[1 + c];
+      const int c0 = j + 1;
+      if (c0 < cols) {
+        if (SMEM || !row_fast) {
+          // warps over rows, lanes over columns
+          for (int r = warp; r < nr; r += NW) {
+            if (lstep[r] < 0) {
+              const T lv = -lval[r];
+              for (int c = c0 + lane; c < cols; c += 32) {
+                T& x = at(r, c);
+                x = mad(lv, urow[c - j], x);
+              }
+            }
+          }
+        } else {
+          // warps over columns, lanes over rows (rows contiguous in memory)
+          for (int c = c0 + warp; c < cols; c += NW) {
+            const T u = urow[c - j];
+            for (int r = lane; r < nr; r += 32) {
+              if (lstep[r] < 0) {
+                T& x = at(r, c);
+                x = mad(-lval[r], u, x);
+              }
+            }
           }
         }
       }
@@ -202,12 +214,12 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
 
   // write back
   if (SMEM) {
-    const int64_t tot = (int64_t)nr * cols;
-    for (int64_t idx = tid; idx < tot; idx += NT) {
-      int r, c;
-      if (row_fast) { r = (int)(idx % nr); c = (int)(idx / nr); }
-      else { c = (int)(idx % cols); r = (int)(idx / cols); }
-      xref(X, rs, cs, r0 + r, c) = slab[(size_t)r * cols + c];
+    if (row_fast) {
+      for (int c = warp; c < cols; c += NW)
+        for (int r = lane; r < nr; r += 32) xref(X, rs, cs, r0 + r, c) = slab[(size_t)r * cols + c];
+    } else {
+      for (int r = warp; r < nr; r += NW)
+        for (int c = lane; c < cols; c += 32) xref(X, rs, cs, r0 + r, c) = slab[(size_t)r * cols + c];
     }
   }
   for (int r = tid; r < nr; r += NT) {
@@ -264,5 +276,7 @@ template int launch_pivoted_lu<double>(double*, int64_t, int, int64_t, int64_t, 
                                        cudaStream_t);
 template int launch_pivoted_lu<float>(float*, int64_t, int, int64_t, int64_t, int, PivLuWs&, unsigned int*, int,
                                       cudaStream_t);
+template int launch_pivoted_lu<df32>(df32*, int64_t, int, int64_t, int64_t, int, PivLuWs&, unsigned int*, int,
+                                     cudaStream_t);
 
 }  // namespace rlu
