@@ -8,6 +8,7 @@
 #include <new>
 #include <vector>
 
+#include "bgemm.cuh"
 #include "common.cuh"
 #include "pinv.cuh"
 #include "pivlu.cuh"
@@ -45,6 +46,7 @@ struct rlu_ctx {
   void* B = nullptr;
   void* LyP = nullptr;
   void* Lb = nullptr;
+  TcWs tcw{};
   unsigned int* status_dev = nullptr;
   unsigned int* bar2 = nullptr;
   unsigned int* status_host = nullptr;  // pinned
@@ -120,6 +122,7 @@ Sizes plan_sizes(int64_t m, int64_t n, int k, int l, int l1, int num_sms) {
   s.add(sizeof(double) * m * k);                     // LyP
   s.add(sizeof(double) * k * k);                     // Lb
   s.add(sizeof(unsigned int) * 4);                   // status, bar2
+  s.add(tc_workspace_bytes(m, n, k, num_sms));       // tensor-core GEMM: W planes, partials
   return s;
 }
 
@@ -205,8 +208,13 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   if ((rc = mark(h, 5, st))) return rc;
   if ((rc = launch_wform(pa, st))) return rc;
   if ((rc = mark(h, 6, st))) return rc;
-  // B = W A
-  if ((rc = launch_bgemm_simt(h->W, f64 ? 1 : 0, A, lda, dtype, m, n, k, h->B, st))) return rc;
+  // B = W A: tensor cores (BF16 splits) when available, else SIMT
+  if (!f64 && h->tcw.ready)
+    rc = launch_bgemm_tc(h->tcw, reinterpret_cast<const float*>(h->W), A, lda, dtype, h->prec, m, n, k,
+                         reinterpret_cast<df32*>(h->B), h->status_dev, st);
+  else
+    rc = launch_bgemm_simt(h->W, f64 ? 1 : 0, A, lda, dtype, m, n, k, h->B, st);
+  if (rc) return rc;
   if ((rc = mark(h, 7, st))) return rc;
   if (h->debug && h->Bdbg)
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Bdbg, h->B, 8 * (size_t)k * n, cudaMemcpyDeviceToDevice, st));
@@ -319,6 +327,11 @@ int rlu_create(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t 
   h->Lb = next();
   h->status_dev = (unsigned int*)next();
   h->bar2 = h->status_dev + 1;
+  if (tc_setup(h->tcw, next(), m, n, k, sms) != RLU_OK) {
+    rlu_destroy(h);
+    return RLU_ECUDA;
+  }
+
   if (cudaMallocHost(&h->status_host, sizeof(unsigned int)) != cudaSuccess) {
     cudaGetLastError();
     rlu_destroy(h);

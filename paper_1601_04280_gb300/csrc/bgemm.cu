@@ -1,0 +1,137 @@
+// Host side of B = W A on the tensor cores (step 6 of Algorithm 1, first
+// half): W split into BF16 planes, TMA descriptors of the planes, the split-K
+// tcgen05 kernel and the float-float reduction of its FP32 partials.
+#include <cuda.h>
+
+#include <type_traits>
+
+#include "bgemm.cuh"
+#include "gemm_tc.cuh"
+
+namespace rlu {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+void tc_plan(int64_t m, int64_t n, int k, int num_sms, TcPlan& p) {
+  p.nz = (k + 207) / 208;                 // N blocks of at most 208 rows of W (fits two stages in shared memory)
+  p.npad = (int)cdiv(cdiv(k, p.nz), 16) * 16;
+  p.ldw = cdiv(m, 8) * 8;                 // TMA row stride: multiple of 16 bytes
+  // Split-K: FP32 accumulation in tensor memory runs over at most kMaxKps rows
+  // of A (its rounding error grows with that depth); the split partials are
+  // summed in float-float.  Enough splits to fill the GPU twice over.
+  const int64_t xt = cdiv(n, tc::kBM);
+  const int64_t kMaxKps = 512;
+  int64_t S = max64(cdiv(m, kMaxKps), cdiv(2 * (int64_t)num_sms, xt * p.nz));
+  S = min64(S, max64(1, cdiv(m, tc::kBK)));
+  p.kps = cdiv(cdiv(m, S), tc::kBK) * tc::kBK;
+  p.splits = (int)cdiv(m, p.kps);
+}
+
+size_t tc_workspace_bytes(int64_t m, int64_t n, int k, int num_sms) {
+  TcPlan p;
+  tc_plan(m, n, k, num_sms, p);
+  return (size_t)3 * k * p.ldw * 2 + (size_t)p.splits * k * n * 4;
+}
+
+int tc_setup(TcWs& w, void* base, int64_t m, int64_t n, int k, int num_sms) {
+  tc_plan(m, n, k, num_sms, w.plan);
+  unsigned char* b = (unsigned char*)base;
+  const size_t plane = (size_t)k * w.plan.ldw * 2;
+  for (int q = 0; q < 3; ++q) w.wp[q] = (__nv_bfloat16*)(b + q * plane);
+  w.part = (float*)(b + 3 * plane);
+  w.ready = false;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return RLU_OK;  // no tensor-map support: the caller uses the SIMT path
+  for (int q = 0; q < 3; ++q) {
+    cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)k};
+    cuuint64_t strides[1] = {(cuuint64_t)(w.plan.ldw * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)tc::kBK, (cuuint32_t)w.plan.npad};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(reinterpret_cast<CUtensorMap*>(w.map[q]), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, w.wp[q], dims,
+                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return RLU_OK;
+  }
+  w.ready = true;
+  return RLU_OK;
+}
+
+// W (k x m, row-major f32) -> planes (k x ldw)
+__global__ void k_split_w_rows(int64_t m, int k, int64_t ldw, const float* __restrict__ W,
+                               __nv_bfloat16* __restrict__ W1, __nv_bfloat16* __restrict__ W2,
+                               __nv_bfloat16* __restrict__ W3) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = e / ldw, i = e - c * ldw;
+  if (c >= k) return;
+  const float w = i < m ? W[c * m + i] : 0.f;
+  const __nv_bfloat16 h1 = __float2bfloat16_rn(w);
+  const float r1 = w - __bfloat162float(h1);
+  const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(h2);
+  W1[e] = h1;
+  W2[e] = h2;
+  W3[e] = __float2bfloat16_rn(r2);
+}
+
+template <typename TA>
+static int launch_cfg(const TcWs& w, int wplanes, const TA* A, int64_t lda, int64_t m, int64_t n, int k,
+                      unsigned int* status, cudaStream_t st) {
+  constexpr int P = std::is_same<TA, float>::value ? 2 : 1;
+  const TcPlan& p = w.plan;
+  const size_t smem = tc::smem_bytes(P, wplanes, p.npad);
+  auto kern = tc::k_bgemm_tc<TA>;
+  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)cdiv(n, tc::kBM), (unsigned)p.splits, (unsigned)p.nz);
+  const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(w.map);
+  kern<<<grid, tc::kThreads, smem, st>>>(maps[0], maps[1], maps[2], wplanes, A, lda, m, n, k, p.npad, p.kps, w.part,
+                                         status);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return RLU_OK;
+}
+
+int launch_bgemm_tc(const TcWs& w, const float* W, const void* A, int64_t lda, int dtype, int prec, int64_t m,
+                    int64_t n, int k, df32* B, unsigned int* status, cudaStream_t st) {
+  if (!w.ready) return RLU_EINVAL;
+  const TcPlan& p = w.plan;
+  const int64_t tot = (int64_t)k * p.ldw;
+  k_split_w_rows<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(m, k, p.ldw, W, w.wp[0], w.wp[1], w.wp[2]);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  int wplanes = 3;
+  if (prec == RLU_PREC_BF16) wplanes = 1;
+  if (prec == RLU_PREC_BF16_REFINE) wplanes = 2;
+  int rc;
+  if (dtype == RLU_F32)
+    rc = launch_cfg<float>(w, wplanes, (const float*)A, lda, m, n, k, status, st);
+  else if (dtype == RLU_BF16)
+    rc = launch_cfg<__nv_bfloat16>(w, wplanes, (const __nv_bfloat16*)A, lda, m, n, k, status, st);
+  else
+    return RLU_EINVAL;
+  if (rc) return rc;
+  tc::k_sum_parts<<<(unsigned)cdiv((int64_t)k * n, 256), 256, 0, st>>>((int64_t)k * n, p.splits, w.part, B);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return RLU_OK;
+}
+
+}  // namespace rlu

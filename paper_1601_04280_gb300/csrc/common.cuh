@@ -66,6 +66,39 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int
   return s_ok != 0;
 }
 
+// Split form of the same barrier: grid_arrive publishes this block's arrival
+// (after every thread's prior writes); grid_wait(e) returns once all blocks
+// have arrived e times, or false after the bounded wait (FLAG_TIMEOUT).
+__device__ __forceinline__ void grid_arrive(unsigned int* counter) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    red_release_gpu_add(counter, 1u);
+  }
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned int* counter, unsigned int epoch, unsigned int* status) {
+  __shared__ int s_ok2;
+  if (threadIdx.x == 0) {
+    const unsigned int target = epoch * gridDim.x;
+    long long t0 = clock64();
+    int ok = 1;
+    while (true) {
+      unsigned int v = ld_acquire_gpu(counter);
+      if ((int)(v - target) >= 0) break;
+      if (ld_acquire_gpu(status) & FLAG_TIMEOUT) { ok = 0; break; }
+      if (clock64() - t0 > kSpinLimitCycles) {
+        set_flag(status, FLAG_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    s_ok2 = ok;
+  }
+  __syncthreads();
+  return s_ok2 != 0;
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from its
 // published definition: per round, two 64x64->128 products of counter words

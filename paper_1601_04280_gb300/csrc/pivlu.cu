@@ -7,9 +7,9 @@
 // Semantics follow LAPACK getf2: at step j the pivot is the row with the
 // largest |X[., j]| among the rows not yet pivoted, ties going to the row
 // with the smallest current position (positions change by the getf2 swap
-// of position j with the pivot's position); a nonzero pivot divides the
-// column below it; the rank-1 update runs on the trailing block.  An exactly
-// zero pivot skips the division and raises FLAG_ZERO_PIVOT.
+// of position j with the pivot's position); a nonzero pivot scales the
+// column below it by its reciprocal; the rank-1 update runs on the trailing
+// block.  An exactly zero pivot skips the scaling and raises FLAG_ZERO_PIVOT.
 //
 // Rows are never moved.  Each CTA owns a contiguous slab of rows (kept in
 // shared memory when it fits) and tracks their current positions; every CTA
@@ -23,14 +23,35 @@
 namespace rlu {
 
 struct __align__(16) Cand {
-  double v;     // |pivot candidate|, -1 if the CTA has no candidate
-  int pos;      // current position of the candidate row
-  int row;      // original row index
+  unsigned long long key;  // order-preserving bits of |pivot candidate|; 0 if the CTA has no candidate
+  int pos;                 // current position of the candidate row
+  int row;                 // original row index, -1 if none
 };
 
-__device__ __forceinline__ bool cand_better(double va, int pa, double vb, int pb) {
-  return va > vb || (va == vb && pa < pb);
+// |x| as an unsigned key whose integer order is the numeric order of |x|
+// (IEEE bit patterns of non-negative numbers sort as integers), so the pivot
+// search needs no floating-point compares.  Any finite |x| maps above the
+// "no candidate" key 0 except +0, which maps to 1.
+__device__ __forceinline__ unsigned long long mag_key(double x) {
+  return (unsigned long long)(__double_as_longlong(x) & 0x7fffffffffffffffll) + 1ull;
 }
+__device__ __forceinline__ unsigned long long mag_key(float x) {
+  return ((unsigned long long)(__float_as_uint(x) & 0x7fffffffu) << 32) + 1ull;
+}
+__device__ __forceinline__ unsigned long long mag_key(df32 x) {
+  // |x| = |hi| + lo * sign(hi): order by |hi|, then by the signed low part
+  const unsigned int h = __float_as_uint(x.hi) & 0x7fffffffu;
+  const float l = (x.hi < 0.f) ? -x.lo : x.lo;
+  unsigned int lb = __float_as_uint(l);
+  lb = (lb & 0x80000000u) ? ~lb : (lb | 0x80000000u);  // order-preserving map of a signed float
+  return (((unsigned long long)h << 32) | lb) + 1ull;
+}
+
+__device__ __forceinline__ bool cand_better(unsigned long long ka, int pa, unsigned long long kb, int pb) {
+  return ka > kb || (ka == kb && pa < pb);
+}
+
+template <typename T> __device__ __forceinline__ T recip(T x) { return one_<T>() / x; }
 
 template <typename T>
 __device__ __forceinline__ T& xref(T* X, int64_t rs, int64_t cs, int64_t i, int c) {
@@ -57,10 +78,10 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
   int32_t* lpos = reinterpret_cast<int32_t*>(lval + rp);              // rpc
   int32_t* lstep = lpos + rp;                                         // rpc
   int32_t* pwin = lstep + rp;                                         // steps
-  __shared__ double red_v[NW];
+  __shared__ unsigned long long red_v[NW];
   __shared__ int red_p[NW];
   __shared__ int red_r[NW];
-  __shared__ int s_zero;
+  __shared__ int s_zero, s_cand;
   __shared__ int s_wrow, s_wpos, s_wcta;
 
   const bool row_fast = (cs == 1) ? false : true;  // B^T: consecutive rows are contiguous in memory
@@ -86,20 +107,21 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
   for (int t = tid; t < steps; t += NT) pwin[t] = t;
   __syncthreads();
 
-  for (int j = 0; j < steps; ++j) {
-    // 1. local candidate for column j
-    double bv = -1.0;
+  // Publish this CTA's best candidate for column jc (rows not yet pivoted):
+  // its |value|, current position and row, and the row's values jc..cols-1.
+  auto publish = [&](int jc) {
+    unsigned long long bv = 0ull;
     int bp = 0x7fffffff, br = -1;
     for (int r = tid; r < nr; r += NT) {
       if (lstep[r] < 0) {
-        double v = to_double(abs_(at(r, j)));
-        int p = lpos[r];
+        const unsigned long long v = mag_key(at(r, jc));
+        const int p = lpos[r];
         if (cand_better(v, p, bv, bp)) { bv = v; bp = p; br = r; }
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      unsigned long long ov = __shfl_down_sync(0xffffffffu, bv, o);
       int op = __shfl_down_sync(0xffffffffu, bp, o);
       int orr = __shfl_down_sync(0xffffffffu, br, o);
       if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; br = orr; }
@@ -109,40 +131,53 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
     if (tid == 0) {
       for (int w = 1; w < NW; ++w)
         if (cand_better(red_v[w], red_p[w], bv, bp)) { bv = red_v[w]; bp = red_p[w]; br = red_r[w]; }
-      Cand cd;
-      cd.v = bv;
-      cd.pos = bp;
-      cd.row = br < 0 ? -1 : (int)(r0 + br);
-      cand[(j & 1) * G + blockIdx.x] = cd;
-      s_wrow = br;  // local row of this CTA's candidate
+      s_cand = br;
     }
     __syncthreads();
-    {
-      const int lr = s_wrow;
-      T* dst = candrow + ((size_t)(j & 1) * G + blockIdx.x) * cols;
-      if (lr >= 0)
-        for (int c = j + tid; c < cols; c += NT) dst[c - j] = at(lr, c);
+    return s_cand;  // local row, or -1
+  };
+  auto write_cand = [&](int jc, int lr) {
+    if (tid == 0) {
+      Cand cd;
+      cd.key = lr >= 0 ? mag_key(at(lr, jc)) : 0ull;
+      cd.pos = lr >= 0 ? lpos[lr] : 0x7fffffff;
+      cd.row = lr < 0 ? -1 : (int)(r0 + lr);
+      cand[(jc & 1) * G + blockIdx.x] = cd;
     }
-    // 2. one grid barrier per step
-    if (!grid_barrier(bar, (unsigned)(j + 1), status)) return;
-    // 3. every CTA picks the same winner (warp 0 scans the G candidates)
+    T* dst = candrow + ((size_t)(jc & 1) * G + blockIdx.x) * cols;
+    if (lr >= 0)
+      for (int c = jc + tid; c < cols; c += NT) dst[c - jc] = at(lr, c);
+  };
+
+  // step 0 candidate
+  {
+    const int lr = publish(0);
+    write_cand(0, lr);
+    grid_arrive(bar);
+  }
+  for (int j = 0; j < steps; ++j) {
+    // 1. wait for every CTA's candidate of step j
+    if (!grid_wait(bar, (unsigned)(j + 1), status)) return;
+    // 2. every CTA picks the same winner (warp 0 scans the G candidates)
     if (warp == 0) {
-      bv = -1.0; bp = 0x7fffffff; int bc = -1;
+      unsigned long long bv = 0ull;
+      int bp = 0x7fffffff, bc = -1, bw = -1;
       for (int g = lane; g < G; g += 32) {
-        Cand cd = cand[(j & 1) * G + g];
-        if (cd.row >= 0 && cand_better(cd.v, cd.pos, bv, bp)) { bv = cd.v; bp = cd.pos; bc = g; }
+        const Cand cd = cand[(j & 1) * G + g];
+        if (cd.row >= 0 && cand_better(cd.key, cd.pos, bv, bp)) { bv = cd.key; bp = cd.pos; bc = g; bw = cd.row; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        unsigned long long ov = __shfl_down_sync(0xffffffffu, bv, o);
         int op = __shfl_down_sync(0xffffffffu, bp, o);
         int oc = __shfl_down_sync(0xffffffffu, bc, o);
-        if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; bc = oc; }
+        int ow = __shfl_down_sync(0xffffffffu, bw, o);
+        if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; bc = oc; bw = ow; }
       }
       if (lane == 0) {
         s_wcta = bc;
         s_wpos = bp;
-        s_wrow = bc >= 0 ? cand[(j & 1) * G + bc].row : -1;
+        s_wrow = bw;
       }
     }
     __syncthreads();
@@ -171,39 +206,57 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
       }
     }
     __syncthreads();
-    // 4. scale column j below the pivot, then the rank-1 update
-    if (!s_zero) {
-      const T piv = urow[0];
+    const bool zero = s_zero != 0;
+    // 3. column j below the pivot: l = x / pivot; then column j+1 (look-ahead)
+    if (!zero) {
+      const T rpiv = recip(urow[0]);
+      const T u1 = (j + 1 < cols) ? urow[1] : zero_<T>();
       for (int r = tid; r < nr; r += NT) {
         if (lstep[r] < 0) {
-          T lv = at(r, j) / piv;
+          T lv = at(r, j) * rpiv;
           at(r, j) = lv;
           lval[r] = lv;
+          if (j + 1 < cols) {
+            T& x = at(r, j + 1);
+            x = mad(-lv, u1, x);
+          }
         }
       }
+    }
+    __syncthreads();
+    int rstar = -1;
+    if (j + 1 < steps) {
+      // 4. next candidate: its row is brought fully up to date before publishing
+      rstar = publish(j + 1);
+      if (!zero && rstar >= 0)
+        for (int c = j + 2 + tid; c < cols; c += NT) {
+          T& x = at(rstar, c);
+          x = mad(-lval[rstar], urow[c - j], x);
+        }
       __syncthreads();
-      const int c0 = j + 1;
-      if (c0 < cols) {
-        if (SMEM || !row_fast) {
-          // warps over rows, lanes over columns
-          for (int r = warp; r < nr; r += NW) {
-            if (lstep[r] < 0) {
-              const T lv = -lval[r];
-              for (int c = c0 + lane; c < cols; c += 32) {
-                T& x = at(r, c);
-                x = mad(lv, urow[c - j], x);
-              }
+      write_cand(j + 1, rstar);
+      grid_arrive(bar);
+    }
+    // 5. the rest of the rank-1 update (columns j+2.., rows other than rstar)
+    const int c0 = j + 2;
+    if (!zero && c0 < cols) {
+      if (SMEM || !row_fast) {
+        for (int r = warp; r < nr; r += NW) {
+          if (lstep[r] < 0 && r != rstar) {
+            const T lv = -lval[r];
+            for (int c = c0 + lane; c < cols; c += 32) {
+              T& x = at(r, c);
+              x = mad(lv, urow[c - j], x);
             }
           }
-        } else {
-          // warps over columns, lanes over rows (rows contiguous in memory)
-          for (int c = c0 + warp; c < cols; c += NW) {
-            const T u = urow[c - j];
-            for (int r = lane; r < nr; r += 32) {
-              if (lstep[r] < 0) {
-                T& x = at(r, c);
-                x = mad(-lval[r], u, x);
-              }
+        }
+      } else {
+        for (int c = c0 + warp; c < cols; c += NW) {
+          const T u = urow[c - j];
+          for (int r = lane; r < nr; r += 32) {
+            if (lstep[r] < 0 && r != rstar) {
+              T& x = at(r, c);
+              x = mad(-lval[r], u, x);
             }
           }
         }
