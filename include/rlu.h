@@ -52,6 +52,7 @@ typedef enum {
   RLU_ETIMEOUT = 4,   /* a bounded device wait gave up (co-residency lost); outputs undefined */
   RLU_ENONFINITE = 5, /* A holds NaN or Inf; outputs undefined */
   RLU_EBADCSR = 6,    /* CSR structure invalid (found on the device); outputs undefined */
+  RLU_ETOOLARGE = 7,  /* sizes exceed the fixed scratch of rlu_sketch_dense_noalloc; nothing was launched */
   RLU_WRANK = 100     /* warning: an exactly zero pivot was met (rank deficiency); outputs valid */
 } rlu_status;
 
@@ -162,6 +163,40 @@ int rlu_debug_stage_ms(rlu_t h, float* ms, int max_stages, int* count);
 
 /* Number of CUDA kernels this library has launched in this process so far. */
 int rlu_debug_launch_count(int64_t* out);
+
+/* ---- sketch without allocation ----
+ * No counterpart in the paper: this entry point exists for callers that
+ * cannot allocate device memory on their call path — a serving loop that
+ * must not call cudaMalloc (it synchronizes the whole device and stalls other
+ * streams), a host process whose device memory is already reserved by another
+ * framework's pool, or an embedded caller with a fixed memory map.
+ *
+ * rlu_sketch_dense_noalloc computes the sketch of step 2 of Algorithm 1,
+ *   Y = A S D H R / sqrt(l1)   (m x l, row-major f64, device, written by the call),
+ * with S, D, R drawn from `seed` exactly as rlu_create(m, n, k, l, l1, seed)
+ * draws them (so Y equals the sketch a handle computes for the same inputs).
+ * A: device, m x n row-major of `dtype` (RLU_F64 sums in FP64, RLU_F32 and
+ * RLU_BF16 in FP32), leading dimension lda >= n.
+ * It allocates nothing: its scratch (hash and sign arrays, per-chunk bucket
+ * lists, twiddles, a status word) is one fixed file-scope device array of
+ * RLU_NOALLOC_SCRATCH_BYTES bytes, present on every device that loads the
+ * library until the process exits.  Sizes are limited accordingly:
+ * n <= RLU_NOALLOC_MAX_N, l1 <= RLU_NOALLOC_MAX_L1, l <= RLU_NOALLOC_MAX_L;
+ * larger sizes return RLU_ETOOLARGE before anything is launched.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls on one device share the array and it keeps the last
+ * call's contents (each call re-initializes what it needs); calls on the same
+ * device whose GPU work overlaps race on it and must be serialized.
+ * Asynchronous on `stream`: `status_dev` (device, one int32) receives RLU_OK
+ * or RLU_ENONFINITE when the work completes.
+ * Errors at call time: RLU_EINVAL, RLU_ETOOLARGE, RLU_ECUDA. */
+#define RLU_NOALLOC_MAX_N 65536
+#define RLU_NOALLOC_MAX_L1 4096
+#define RLU_NOALLOC_MAX_L 1024
+#define RLU_NOALLOC_SCRATCH_BYTES 1725184
+int rlu_sketch_dense_noalloc(const void* A, int64_t lda, int dtype, int64_t m, int64_t n, int32_t l, int32_t l1,
+                             uint64_t seed, double* Y, int32_t* status_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -16,6 +16,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "librlu.so")
 
 RLU_OK, RLU_EINVAL, RLU_ENOMEM, RLU_ECUDA, RLU_ETIMEOUT, RLU_ENONFINITE, RLU_EBADCSR = 0, 1, 2, 3, 4, 5, 6
+RLU_ETOOLARGE = 7
+RLU_NOALLOC_MAX_N, RLU_NOALLOC_MAX_L1, RLU_NOALLOC_MAX_L = 65536, 4096, 1024
 RLU_WRANK = 100
 RLU_F64, RLU_F32, RLU_BF16 = 0, 1, 2
 RLU_PREC_F64, RLU_PREC_F32, RLU_PREC_BF16, RLU_PREC_BF16_REFINE = 0, 1, 2, 3
@@ -25,7 +27,7 @@ PREC = {"f64": RLU_PREC_F64, "f32": RLU_PREC_F32, "bf16": RLU_PREC_BF16, "bf16_r
 C_SYMBOLS = ("rlu_create", "rlu_set_precision", "rlu_workspace_bytes", "rlu_factor_dense",
              "rlu_factor_dense_async", "rlu_factor_csr", "rlu_factor_dense_host", "rlu_destroy",
              "rlu_strerror", "rlu_debug_sketch_params", "rlu_debug_Y", "rlu_debug_B", "rlu_debug_enable",
-             "rlu_debug_timing", "rlu_debug_stage_ms", "rlu_debug_launch_count")
+             "rlu_debug_timing", "rlu_debug_stage_ms", "rlu_debug_launch_count", "rlu_sketch_dense_noalloc")
 
 #: stage names reported by rlu_debug_stage_ms, in order
 STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
@@ -66,6 +68,7 @@ def load(reload=False):
         "rlu_debug_timing": ([vp, c.c_int], c.c_int),
         "rlu_debug_stage_ms": ([vp, vp, c.c_int, c.POINTER(c.c_int)], c.c_int),
         "rlu_debug_launch_count": ([c.POINTER(i64)], c.c_int),
+        "rlu_sketch_dense_noalloc": ([vp, i64, c.c_int, i64, i64, i32, i32, u64, vp, vp, vp], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -127,6 +130,12 @@ def rlu_factor_dense_host(h, A_ptr, dtype, L_ptr, U_ptr, p_ptr, q_ptr, stream_pt
 
 def rlu_destroy(h):
     return load().rlu_destroy(h)
+
+
+def rlu_sketch_dense_noalloc(A_ptr, lda, dtype, m, n, l, l1, seed, Y_ptr, status_ptr, stream_ptr):
+    """Sketch Y = A S D H R / sqrt(l1) without any allocation (see include/rlu.h)."""
+    return load().rlu_sketch_dense_noalloc(A_ptr, lda, dtype, m, n, l, l1, ctypes.c_uint64(seed & (2**64 - 1)),
+                                           Y_ptr, status_ptr, stream_ptr)
 
 
 def rlu_debug_launch_count():

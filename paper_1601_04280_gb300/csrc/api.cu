@@ -259,6 +259,7 @@ const char* rlu_strerror(int code) {
     case RLU_ETIMEOUT: return "a bounded device wait timed out";
     case RLU_ENONFINITE: return "input holds NaN or Inf";
     case RLU_EBADCSR: return "invalid CSR structure";
+    case RLU_ETOOLARGE: return "sizes exceed the fixed scratch of the allocation-free sketch";
     case RLU_WRANK: return "warning: exactly zero pivot met (rank deficient input)";
     default: return "unknown status";
   }
