@@ -194,7 +194,7 @@ int rlu_debug_launch_count(int64_t* out);
 #define RLU_NOALLOC_MAX_N 65536
 #define RLU_NOALLOC_MAX_L1 4096
 #define RLU_NOALLOC_MAX_L 1024
-#define RLU_NOALLOC_SCRATCH_BYTES 1725184
+#define RLU_NOALLOC_SCRATCH_BYTES 2773760
 int rlu_sketch_dense_noalloc(const void* A, int64_t lda, int dtype, int64_t m, int64_t n, int32_t l, int32_t l1,
                              uint64_t seed, double* Y, int32_t* status_dev, void* stream);
 

@@ -93,7 +93,7 @@ int max_gram_splits_for(int k, int num_sms) {
 // The order of `add` calls is the allocation order in rlu_create.
 Sizes plan_sizes(int64_t m, int64_t n, int k, int l, int l1, int num_sms) {
   Sizes s;
-  const int64_t nch = cdiv(n, 2048);  // smallest chunk of the dense sketch
+  const int64_t nch = cdiv(n, 1024);  // smallest chunk of the dense sketch
   s.add(sizeof(uint32_t) * n);                       // hs
   s.add(sizeof(float) * l1);                         // dsign
   s.add(sizeof(uint64_t) * l1);                      // keys

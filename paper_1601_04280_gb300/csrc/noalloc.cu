@@ -26,7 +26,7 @@ namespace {
 constexpr int64_t kMaxN = RLU_NOALLOC_MAX_N;
 constexpr int64_t kMaxL1 = RLU_NOALLOC_MAX_L1;
 constexpr int64_t kMaxL = RLU_NOALLOC_MAX_L;
-constexpr int64_t kMinChunk = 2048;  // smallest column chunk of the dense sketch
+constexpr int64_t kMinChunk = 1024;  // smallest column chunk of the dense sketch
 constexpr int64_t kMaxChunks = (kMaxN + kMinChunk - 1) / kMinChunk;
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }

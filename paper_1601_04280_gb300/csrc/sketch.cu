@@ -159,6 +159,85 @@ template <typename V> __device__ __forceinline__ V cmi(V a) { return V{a.y, -a.x
 // the twiddles exp(-2 pi i t (i mod p) / (p r)) and a length-r DFT, and
 // writes out[(i - i mod p) r + i mod p + u p] (u < r).  Output is in natural
 // order after the last stage.
+// The same stage applied to `nb` independent transforms at once: transform t
+// reads in + t * stride and writes out + t * stride (one barrier per stage
+// for the whole batch instead of one per transform).
+template <typename V, typename S>
+__device__ void stockham_stage_batch(const V* __restrict__ in, V* __restrict__ out, int stride, int nb, int N, int r,
+                                     int p, const V* tw) {
+  const int T = N / r;
+  const int step = N / (p * r);
+  const int total = nb * T;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int tb = idx / T, i = idx - tb * T;
+    const V* src = in + (size_t)tb * stride;
+    V* dst = out + (size_t)tb * stride;
+    const int k = i % p;
+    const int obase = (i - k) * r + k;
+    if (r == 4) {
+      V x0 = src[i], x1 = src[i + T], x2 = src[i + 2 * T], x3 = src[i + 3 * T];
+      if (k) {
+        x1 = cmul(x1, tw[k * step]);
+        x2 = cmul(x2, tw[2 * k * step]);
+        x3 = cmul(x3, tw[3 * k * step]);
+      }
+      V a0 = cadd(x0, x2), a1 = csub(x0, x2), b0 = cadd(x1, x3), b1 = cmi(csub(x1, x3));
+      dst[obase] = cadd(a0, b0);
+      dst[obase + p] = cadd(a1, b1);
+      dst[obase + 2 * p] = csub(a0, b0);
+      dst[obase + 3 * p] = csub(a1, b1);
+    } else if (r == 2) {
+      V x0 = src[i], x1 = src[i + T];
+      if (k) x1 = cmul(x1, tw[k * step]);
+      dst[obase] = cadd(x0, x1);
+      dst[obase + p] = csub(x0, x1);
+    } else if (r == 3) {
+      V x0 = src[i], x1 = src[i + T], x2 = src[i + 2 * T];
+      if (k) {
+        x1 = cmul(x1, tw[k * step]);
+        x2 = cmul(x2, tw[2 * k * step]);
+      }
+      const S h = S(0.86602540378443864676);
+      V sm = cadd(x1, x2), d = csub(x1, x2);
+      V t = V{x0.x - S(0.5) * sm.x, x0.y - S(0.5) * sm.y};
+      V u = V{h * d.y, -h * d.x};
+      dst[obase] = cadd(x0, sm);
+      dst[obase + p] = cadd(t, u);
+      dst[obase + 2 * p] = csub(t, u);
+    } else if (r == 5) {
+      V x[5];
+      x[0] = src[i];
+#pragma unroll
+      for (int q = 1; q < 5; ++q) {
+        V v = src[i + q * T];
+        x[q] = k ? cmul(v, tw[q * k * step]) : v;
+      }
+      const int wstep = N / 5;
+#pragma unroll
+      for (int u = 0; u < 5; ++u) {
+        V y = x[0];
+#pragma unroll
+        for (int q = 1; q < 5; ++q) y = cadd(y, cmul(x[q], tw[((u * q) % 5) * wstep]));
+        dst[obase + u * p] = y;
+      }
+    } else {
+      const int wstep = N / r;
+      for (int u = 0; u < r; ++u) {
+        V y = src[i];
+        int e = 0;
+        for (int q = 1; q < r; ++q) {
+          e += u;
+          if (e >= r) e -= r;
+          V v = src[i + q * T];
+          if (k) v = cmul(v, tw[q * k * step]);
+          y = cadd(y, cmul(v, tw[e * wstep]));
+        }
+        dst[obase + u * p] = y;
+      }
+    }
+  }
+}
+
 template <typename V, typename S>
 __device__ void stockham_stage(const V* __restrict__ in, V* __restrict__ out, int N, int r, int p, const V* tw) {
   const int T = N / r;
@@ -356,6 +435,204 @@ __global__ void __launch_bounds__(NT) k_sketch_dense(const TA* __restrict__ A, i
 }
 
 // ---------------------------------------------------------------------------
+// Fused dense sketch, TMA-fed: the (row group, column chunk) tiles of A stream
+// through a two-stage shared-memory ring with 1D bulk copies (one per row
+// segment, completion on an mbarrier), so the next tile is in flight while
+// the current one is summed and while a finished group runs its FFTs (whose
+// buffers are separate from the ring).  Same arithmetic and order as
+// k_sketch_dense.  Needs 16-byte aligned rows (lda * sizeof(TA) and the base
+// address multiples of 16, and the chunk widths multiples of 16 bytes).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void sk_mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void sk_mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool sk_mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kSpinLimitCycles) return false;
+  }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+template <typename TA, typename TACC, int NT, int NB, int R>
+__global__ void __launch_bounds__(NT, 1) k_sketch_dense_tma(const TA* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                                                         int l1, int l, int chunk,
+                                                         const int32_t* __restrict__ bstart,
+                                                         const uint32_t* __restrict__ blist,
+                                                         const float* __restrict__ dsign,
+                                                         const int32_t* __restrict__ Rsel,
+                                                         const typename C2<TACC>::t* __restrict__ tw, FftPlan plan,
+                                                         int pb, int lists_in_smem, double* __restrict__ Y,
+                                                         unsigned int* status) {
+  using V = typename C2<TACC>::t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ int s_fail;
+  TA* ring = reinterpret_cast<TA*>(smem);                       // [2][R][chunk]
+  V* twsm = reinterpret_cast<V*>(smem + (size_t)2 * R * chunk * sizeof(TA));  // l1 twiddles
+  V* fbuf = twsm + l1;                                          // [pb][2][l1] FFT ping-pong buffers
+  // optional copy of the bucket lists (start offsets, then entries) after the FFT buffers
+  int32_t* bs_sm = reinterpret_cast<int32_t*>(fbuf + (size_t)pb * 2 * l1);
+  const int tid = threadIdx.x;
+  const int64_t ngroups = cdiv(m, R);
+  const int nchunks = (int)cdiv(n, chunk);
+  const TACC scale = TACC(1) / sqrt(TACC(l1));
+  // tiles of this CTA: t -> group blockIdx.x + (t / nchunks) * gridDim.x, chunk t % nchunks
+  const int64_t my_groups = blockIdx.x < ngroups ? cdiv(ngroups - blockIdx.x, gridDim.x) : 0;
+  const int64_t ntiles = my_groups * nchunks;
+  bool bad = false;
+
+  auto issue = [&](int64_t t) {  // thread 0 only
+    const int s = (int)(t & 1);
+    const int64_t g = blockIdx.x + (t / nchunks) * (int64_t)gridDim.x;
+    const int c = (int)(t % nchunks);
+    const int64_t row0 = g * R, col0 = (int64_t)c * chunk;
+    const int width = (int)min64(chunk, n - col0);
+    const int rows = (int)min64(R, m - row0);
+    const uint32_t bytes = (uint32_t)width * sizeof(TA);
+    sk_mbar_expect_tx(&full[s], bytes * rows);
+    for (int r = 0; r < rows; ++r)
+      bulk_g2s(ring + ((size_t)s * R + r) * chunk, A + (row0 + r) * lda + col0, bytes, &full[s]);
+  };
+
+  if (tid == 0) {
+    sk_mbar_init(&full[0], 1);
+    sk_mbar_init(&full[1], 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int e = tid; e < l1; e += NT) twsm[e] = tw[e];
+  const int64_t nstart = (int64_t)nchunks * l1 + 1;
+  uint32_t* bl_sm = reinterpret_cast<uint32_t*>(bs_sm + nstart);
+  if (lists_in_smem) {
+    for (int64_t e = tid; e < nstart; e += NT) bs_sm[e] = bstart[e];
+    for (int64_t e = tid; e < n; e += NT) bl_sm[e] = blist[e];
+  }
+  const int32_t* bsrc = lists_in_smem ? bs_sm : bstart;
+  const uint32_t* lsrc = lists_in_smem ? bl_sm : blist;
+  __syncthreads();
+  if (tid == 0 && ntiles > 0) issue(0);
+
+  TACC acc[NB][R];
+#pragma unroll
+  for (int t = 0; t < NB; ++t)
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[t][r] = TACC(0);
+
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const int s = (int)(t & 1);
+    const int64_t g = blockIdx.x + (t / nchunks) * (int64_t)gridDim.x;
+    const int c = (int)(t % nchunks);
+    const int64_t row0 = g * R;
+    const int rows = (int)min64(R, m - row0);
+    // the other stage was released by the __syncthreads that ended tile t-1
+    if (tid == 0 && t + 1 < ntiles) issue(t + 1);
+    if (!sk_mbar_wait(&full[s], (uint32_t)((t >> 1) & 1))) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+      // drain the copy issued for tile t+1 (bounded) before leaving
+      if (tid == 0 && t + 1 < ntiles) sk_mbar_wait(&full[(t + 1) & 1], (uint32_t)(((t + 1) >> 1) & 1));
+      break;
+    }
+    const TA* tile = ring + (size_t)s * R * chunk;
+    const int32_t* bs = bsrc + (int64_t)c * l1;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int b = tid + q * NT;
+      if (b < l1) {
+        const int s0 = bs[b], s1 = bs[b + 1];
+        for (int e = s0; e < s1; ++e) {
+          const uint32_t ent = lsrc[e];
+          const int off = (int)(ent & 0x7fffffffu);
+          const bool neg = (ent >> 31) != 0;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const TACC v = load_acc(tile + r * chunk + off, TACC(0));
+            if (r < rows) bad |= !isfinite(v);
+            acc[q][r] += neg ? -v : v;
+          }
+        }
+      }
+    }
+    if (c == nchunks - 1) {
+      // Hartley transforms of the finished group's row pairs, pb pairs per batch
+      for (int q0 = 0; q0 < R / 2; q0 += pb) {
+        const int nbat = min(pb, R / 2 - q0);
+        __syncthreads();
+#pragma unroll
+        for (int q2 = 0; q2 < R / 2; ++q2) {
+          if (q2 >= q0 && q2 < q0 + nbat) {
+            const bool va = 2 * q2 < rows, vb = 2 * q2 + 1 < rows;
+            V* z = fbuf + (size_t)(q2 - q0) * 2 * l1;
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+              const int b = tid + q * NT;
+              if (b < l1) {
+                const TACC ds = (TACC)dsign[b];
+                z[b] = V{va ? ds * acc[q][2 * q2] : TACC(0), vb ? ds * acc[q][2 * q2 + 1] : TACC(0)};
+              }
+            }
+          }
+        }
+        __syncthreads();
+        V* src = fbuf;
+        V* dst = fbuf + l1;
+        int p = 1;
+        for (int st = 0; st < plan.nstages; ++st) {
+          const int r = plan.radix[st];
+          stockham_stage_batch<V, TACC>(src, dst, 2 * l1, nbat, l1, r, p, twsm);
+          p *= r;
+          __syncthreads();
+          V* tmp = src;
+          src = dst;
+          dst = tmp;
+        }
+        for (int idx = tid; idx < nbat * l; idx += NT) {
+          const int qb = idx / l, cidx = idx - qb * l;
+          const V* zz = src + (size_t)qb * 2 * l1;
+          const int q2 = q0 + qb;
+          const int64_t ra = row0 + 2 * q2, rb = ra + 1;
+          const int f = Rsel[cidx];
+          const int fm = f == 0 ? 0 : l1 - f;
+          const V z = zz[f], w = zz[fm];
+          const TACC h1 = TACC(0.5) * ((z.x + w.x) - (z.y - w.y));
+          const TACC h2 = TACC(0.5) * ((z.x - w.x) + (z.y + w.y));
+          if (2 * q2 < rows) Y[ra * l + cidx] = (double)(h1 * scale);
+          if (2 * q2 + 1 < rows) Y[rb * l + cidx] = (double)(h2 * scale);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[q][r] = TACC(0);
+    }
+    __syncthreads();  // every thread is done with stage s before it is refilled
+  }
+  if (bad) set_flag(status, FLAG_NONFINITE);
+  if (tid == 0 && s_fail) set_flag(status, FLAG_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
 FftPlan make_fft_plan(int N) {
@@ -395,15 +672,60 @@ int launch_twiddles(int N, double2* tw64, float2* tw32, cudaStream_t st) {
 }
 
 int sketch_chunk_cols(int dtype) {
-  // 64 KB of A per staged tile
-  if (dtype == RLU_F64) return 2048;  // 4 rows x 2048 x 8 B
-  if (dtype == RLU_F32) return 2048;  // 8 rows x 2048 x 4 B
-  return 4096;                        // 8 rows x 4096 x 2 B
+  // 32 KB of A per staged tile (a two-stage ring leaves room for batched FFT buffers)
+  if (dtype == RLU_F64) return 1024;  // 4 rows x 1024 x 8 B
+  if (dtype == RLU_F32) return 1024;  // 8 rows x 1024 x 4 B
+  return 2048;                        // 8 rows x 2048 x 2 B
+}
+
+template <typename TA, typename TACC, int NT, int NB, int R>
+static int launch_dense_tma_cfg(const void* A, int64_t lda, int64_t m, int64_t n, int l1, int l, const SketchWs& ws,
+                                double* Y, unsigned int* status, int num_sms, cudaStream_t st) {
+  auto kern = k_sketch_dense_tma<TA, TACC, NT, NB, R>;
+  using V = typename C2<TACC>::t;
+  const size_t ring = (size_t)2 * R * ws.chunk * sizeof(TA);
+  const size_t budget = 220 * 1024;
+  const size_t per_pair = (size_t)2 * l1 * sizeof(V);
+  const size_t fixed = ring + (size_t)l1 * sizeof(V);
+  const size_t lists = (size_t)4 * (ws.nchunks * l1 + 1) + (size_t)4 * n;
+  if (fixed + per_pair > budget) return RLU_EINVAL;
+  // prefer the bucket lists in shared memory with at least two FFT pairs per batch
+  int lists_in_smem = 0;
+  int pb;
+  if (fixed + lists + 2 * per_pair <= budget || (R / 2 < 2 && fixed + lists + per_pair <= budget)) {
+    lists_in_smem = 1;
+    pb = (int)((budget - fixed - lists) / per_pair);
+  } else {
+    pb = (int)((budget - fixed) / per_pair);
+  }
+  if (pb > R / 2) pb = R / 2;
+  const size_t smem = fixed + (size_t)pb * per_pair + (lists_in_smem ? lists : 0);
+  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+  if (per_sm < 1) return RLU_EINVAL;
+  const int64_t groups = cdiv(m, R);
+  int64_t grid = (int64_t)per_sm * num_sms;
+  if (grid > groups) grid = groups;
+  const typename C2<TACC>::t* tw;
+  if constexpr (sizeof(TACC) == 8) tw = ws.tw64; else tw = ws.tw32;
+  kern<<<(unsigned)grid, NT, smem, st>>>(reinterpret_cast<const TA*>(A), lda, m, n, l1, l, ws.chunk, ws.bstart,
+                                         ws.blist, ws.dsign, ws.R, tw, ws.plan, pb, lists_in_smem, Y, status);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return RLU_OK;
 }
 
 template <typename TA, typename TACC, int NT, int NB, int R>
 static int launch_dense_cfg(const void* A, int64_t lda, int64_t m, int64_t n, int l1, int l, const SketchWs& ws,
                             double* Y, unsigned int* status, int num_sms, cudaStream_t st) {
+  // TMA-fed kernel when every row segment is a 16-byte-aligned run of 16-byte multiples
+  // and the ring plus FFT buffers fit in shared memory
+  const bool aligned = ((uintptr_t)A % 16 == 0) && ((lda * (int64_t)sizeof(TA)) % 16 == 0) &&
+                       ((n * (int64_t)sizeof(TA)) % 16 == 0) && ((ws.chunk * (int64_t)sizeof(TA)) % 16 == 0);
+  const size_t tma_smem = (size_t)2 * R * ws.chunk * sizeof(TA) + (size_t)3 * l1 * sizeof(typename C2<TACC>::t);
+  if (aligned && tma_smem <= 220 * 1024)
+    return launch_dense_tma_cfg<TA, TACC, NT, NB, R>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
   auto kern = k_sketch_dense<TA, TACC, NT, NB, R>;
   size_t tile_bytes = (size_t)R * ws.chunk * sizeof(TA);
   size_t fft_bytes = (size_t)2 * l1 * sizeof(typename C2<TACC>::t);
@@ -426,23 +748,24 @@ static int launch_dense_cfg(const void* A, int64_t lda, int64_t m, int64_t n, in
 
 int launch_sketch_dense(const void* A, int64_t lda, int dtype, bool acc64, int64_t m, int64_t n, int l1, int l,
                         const SketchWs& ws, double* Y, unsigned int* status, int num_sms, cudaStream_t st) {
+  // 1024 threads per CTA; each thread owns NB buckets of R rows in registers
   if (dtype == RLU_F64) {
-    if (l1 <= 2048) return launch_dense_cfg<double, double, 256, 8, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    if (l1 <= 4096) return launch_dense_cfg<double, double, 512, 8, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 2048) return launch_dense_cfg<double, double, 1024, 2, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 4096) return launch_dense_cfg<double, double, 1024, 4, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
     if (l1 <= 8192) return launch_dense_cfg<double, double, 1024, 8, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
     return launch_dense_cfg<double, double, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
   }
   if (acc64) return RLU_EINVAL;
   if (dtype == RLU_F32) {
-    if (l1 <= 2048) return launch_dense_cfg<float, float, 256, 8, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    if (l1 <= 4096) return launch_dense_cfg<float, float, 512, 8, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 2048) return launch_dense_cfg<float, float, 1024, 2, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 4096) return launch_dense_cfg<float, float, 1024, 4, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
     if (l1 <= 8192) return launch_dense_cfg<float, float, 1024, 8, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
     return launch_dense_cfg<float, float, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
   }
   if (dtype == RLU_BF16) {
     using B = __nv_bfloat16;
-    if (l1 <= 2048) return launch_dense_cfg<B, float, 256, 8, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    if (l1 <= 4096) return launch_dense_cfg<B, float, 512, 8, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 2048) return launch_dense_cfg<B, float, 1024, 2, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 4096) return launch_dense_cfg<B, float, 1024, 4, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
     if (l1 <= 8192) return launch_dense_cfg<B, float, 1024, 8, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
     return launch_dense_cfg<B, float, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
   }
