@@ -109,12 +109,16 @@ int rlu_factor_dense(rlu_t h, const void* A, int64_t lda, int dtype, void* L, vo
 int rlu_factor_dense_async(rlu_t h, const void* A, int64_t lda, int dtype, void* L, void* U, int64_t* p,
                            int64_t* q, int32_t* status_dev, void* stream);
 
-/* Factor CSR A (m x n, nnz entries).
+/* Factor CSR A (m x n, nnz entries, nnz < 2^31).
  *   rowptr: device, m+1 int64, rowptr[0] = 0, non-decreasing, rowptr[m] = nnz.
- *   colind: device, nnz int32 in [0, n).  Order within a row is free.
- *   val:    device, nnz values of type `dtype` (RLU_F32 or RLU_F64).
- * Outputs as rlu_factor_dense.  The structure is validated on the device
- * (RLU_EBADCSR).  Errors as rlu_factor_dense. */
+ *   colind: device, nnz int32 in [0, n).  Order within a row is free;
+ *           repeated coordinates are summed.
+ *   val:    device, nnz values: RLU_F32 with RLU_PREC_F32, RLU_F64 with RLU_PREC_F64.
+ * Outputs as rlu_factor_dense.  Rows with at least n/4 entries are copied to a
+ * dense block for the tensor-core product; the handle allocates that block and
+ * the per-entry scratch on first use (and grows them), and reads the number of
+ * such rows back to the host once per call.  The structure is validated on the
+ * device (RLU_EBADCSR).  Errors as rlu_factor_dense. */
 int rlu_factor_csr(rlu_t h, const int64_t* rowptr, const int32_t* colind, const void* val, int64_t nnz, int dtype,
                    void* L, void* U, int64_t* p, int64_t* q, void* stream);
 

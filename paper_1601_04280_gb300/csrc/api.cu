@@ -10,6 +10,7 @@
 
 #include "bgemm.cuh"
 #include "common.cuh"
+#include "csr.cuh"
 #include "pinv.cuh"
 #include "pivlu.cuh"
 #include "sketch.cuh"
@@ -61,6 +62,13 @@ struct rlu_ctx {
   void* U_stage = nullptr;
   int64_t* p_stage = nullptr;
   int64_t* q_stage = nullptr;
+  // CSR path workspace, sized on first use (rows) and grown with nnz / heavy rows
+  CsrWs csr{};
+  bool csr_rows_ready = false;
+  int64_t csr_cap_nnz = -1, csr_cap_heavy = -1;
+  void* csr_nnz_buf = nullptr;
+  void* csr_heavy_buf = nullptr;
+  void* csr_rows_buf = nullptr;
   // per-stage device timing (test hook)
   int timing = 0;
   cudaEvent_t ev[kNumStages + 1] = {};
@@ -162,6 +170,68 @@ bool prec_dtype_ok(int prec, int dtype) {
   }
 }
 
+int csr_rows_alloc(rlu_ctx* h) {
+  if (h->csr_rows_ready) return RLU_OK;
+  const int64_t m = h->m, n = h->n;
+  Sizes sz;
+  for (int i = 0; i < 4; ++i) sz.add(sizeof(int32_t) * (m + 1));  // hflag, lflag, hpos, lpos
+  sz.add(sizeof(int32_t) * m);                                     // heavy
+  sz.add(sizeof(int32_t) * m);                                     // light
+  sz.add(sizeof(int32_t) * 2);                                     // count
+  sz.add(sizeof(int32_t) * (n + 1));                               // ccnt
+  sz.add(sizeof(int32_t) * (n + 1));                               // cstart
+  sz.add((size_t)8 * m * h->k);                                    // W^T
+  char* b = nullptr;
+  if (cudaMalloc(&b, sz.total) != cudaSuccess) { cudaGetLastError(); return RLU_ENOMEM; }
+  h->csr_rows_buf = b;
+  size_t off = 0;
+  int idx = 0;
+  auto next = [&]() -> void* { void* p = b + off; off += sz.parts[idx++]; return p; };
+  CsrWs& w = h->csr;
+  w.hflag = (int32_t*)next(); w.lflag = (int32_t*)next(); w.hpos = (int32_t*)next(); w.lpos = (int32_t*)next();
+  w.heavy = (int32_t*)next(); w.light = (int32_t*)next(); w.count = (int32_t*)next();
+  w.ccnt = (int32_t*)next(); w.cstart = (int32_t*)next(); w.Wt = next();
+  h->csr_rows_ready = true;
+  return RLU_OK;
+}
+
+int csr_grow(rlu_ctx* h, int64_t nnz, int64_t nheavy) {
+  if (nnz > h->csr_cap_nnz) {
+    if (h->csr_nnz_buf) cudaFree(h->csr_nnz_buf);
+    h->csr_nnz_buf = nullptr;
+    h->csr_cap_nnz = -1;
+    const size_t rb = ((sizeof(int32_t) * (size_t)max64(nnz, 1)) + 255) & ~(size_t)255;
+    char* b = nullptr;
+    if (cudaMalloc(&b, rb + (size_t)8 * max64(nnz, 1)) != cudaSuccess) { cudaGetLastError(); return RLU_ENOMEM; }
+    h->csr_nnz_buf = b;
+    h->csr.crow = (int32_t*)b;
+    h->csr.cval = b + rb;
+    h->csr_cap_nnz = nnz;
+  }
+  if (nheavy > h->csr_cap_heavy) {
+    if (h->csr_heavy_buf) cudaFree(h->csr_heavy_buf);
+    h->csr_heavy_buf = nullptr;
+    h->csr_cap_heavy = -1;
+    const int64_t nh = max64(nheavy, 1);
+    const size_t dbytes = (((size_t)8 * nh * h->n) + 1023) & ~(size_t)1023;
+    const size_t wbytes = (((size_t)8 * h->k * nh) + 1023) & ~(size_t)1023;
+    const size_t tbytes = tc_workspace_bytes(nh, h->n, h->k, h->num_sms);
+    char* b = nullptr;
+    if (cudaMalloc(&b, dbytes + wbytes + tbytes) != cudaSuccess) { cudaGetLastError(); return RLU_ENOMEM; }
+    h->csr_heavy_buf = b;
+    h->csr.D = b;
+    h->csr.Wh = b + dbytes;
+    h->csr_cap_heavy = nheavy;
+  }
+  if (nheavy > 0) {
+    const size_t dbytes = (((size_t)8 * max64(h->csr_cap_heavy, 1) * h->n) + 1023) & ~(size_t)1023;
+    const size_t wbytes = (((size_t)8 * h->k * max64(h->csr_cap_heavy, 1)) + 1023) & ~(size_t)1023;
+    int rc = tc_setup(h->csr.tc, (char*)h->csr_heavy_buf + dbytes + wbytes, nheavy, h->n, h->k, h->num_sms);
+    if (rc) return rc;
+  }
+  return RLU_OK;
+}
+
 int mark(rlu_ctx* h, int i, cudaStream_t st) {
   if (!h->timing) return RLU_OK;
   RLU_CUDA_TRY(cudaEventRecord(h->ev[i], st));
@@ -229,6 +299,75 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   if (rc) return rc;
   if ((rc = mark(h, 8, st))) return rc;
   // step 7: L = L_y L_b, U = U_b, p, q
+  AssembleArgs aa{};
+  aa.m = m; aa.n = n; aa.k = k;
+  aa.Lk = h->Lk; aa.perm_y = h->perm_y; aa.perm_b = h->perm_b; aa.Bp = h->B;
+  aa.LyP = h->LyP; aa.Lb = h->Lb; aa.L = L; aa.U = U; aa.p = p; aa.q = q;
+  rc = f64 ? launch_assemble<double, double>(aa, st) : launch_assemble<df32, float>(aa, st);
+  if (rc) return rc;
+  if ((rc = mark(h, 9, st))) return rc;
+  h->last_prec = h->prec;
+  return RLU_OK;
+}
+
+// The CSR path: the same stages as enqueue_dense with the CSR sketch and the
+// sparse B = W A; one host read-back of the heavy-row count after the row
+// classification (it sizes the dense copy of the heavy rows).
+int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const void* val, int64_t nnz, int dtype,
+                void* L, void* U, int64_t* p, int64_t* q, cudaStream_t st) {
+  const int64_t m = h->m, n = h->n;
+  const int k = h->k, l = h->l, l1 = h->l1;
+  const bool f64 = (h->prec == RLU_PREC_F64);
+  int rc;
+  if ((rc = csr_rows_alloc(h))) return rc;
+  RLU_CUDA_TRY(cudaMemsetAsync(h->status_dev, 0, sizeof(unsigned int), st));
+  h->ev_recorded = 0;
+  if ((rc = mark(h, 0, st))) return rc;
+  h->sk.chunk = sketch_chunk_cols(dtype);
+  h->sk.nchunks = cdiv(n, h->sk.chunk);
+  if ((rc = launch_sketch_params(h->sk, n, l1, l, h->seed, st))) return rc;
+  CsrRows cr{};
+  if ((rc = csr_classify(h->csr, rowptr, m, n, nnz, h->status_dev, cr, st))) return rc;
+  if ((rc = csr_grow(h, nnz, cr.n_heavy))) return rc;
+  if ((rc = mark(h, 1, st))) return rc;
+  RLU_CUDA_TRY(cudaMemsetAsync(h->Y, 0, sizeof(double) * m * l, st));
+  if ((rc = launch_sketch_csr(rowptr, colind, val, dtype, n, cr, l1, l, h->sk, h->csr.D, h->Y, h->status_dev,
+                              h->num_sms, st)))
+    return rc;
+  if ((rc = mark(h, 2, st))) return rc;
+  if (h->debug && h->Ydbg)
+    RLU_CUDA_TRY(cudaMemcpyAsync(h->Ydbg, h->Y, sizeof(double) * m * l, cudaMemcpyDeviceToDevice, st));
+  h->pw.perm = h->perm_y;
+  if ((rc = launch_pivoted_lu<double>(h->Y, m, l, l, 1, l, h->pw, h->status_dev, h->num_sms, st))) return rc;
+  if ((rc = mark(h, 3, st))) return rc;
+  PinvArgs pa{};
+  pa.m = m; pa.k = k; pa.l = l;
+  pa.Y = h->Y; pa.pstep = h->pw.pstep; pa.Lk = h->Lk;
+  pa.gram_part = h->gram_part; pa.max_gram_splits = h->max_gram_splits;
+  pa.G = h->G; pa.Rinv = h->Rinv; pa.Ginv = h->Ginv;
+  pa.W = h->W; pa.w64 = f64 ? 1 : 0;
+  pa.bar = h->bar2; pa.status = h->status_dev; pa.num_sms = h->num_sms;
+  if ((rc = launch_gram(pa, st))) return rc;
+  if ((rc = mark(h, 4, st))) return rc;
+  if ((rc = launch_chol(pa, st))) return rc;
+  if ((rc = mark(h, 5, st))) return rc;
+  if ((rc = launch_wform(pa, st))) return rc;
+  if ((rc = mark(h, 6, st))) return rc;
+  if ((rc = csr_bgemm(h->csr, rowptr, colind, val, dtype, h->prec, m, n, k, cr, h->W, h->B, h->status_dev,
+                      h->num_sms, st)))
+    return rc;
+  if ((rc = mark(h, 7, st))) return rc;
+  if (h->debug && h->Bdbg)
+    RLU_CUDA_TRY(cudaMemcpyAsync(h->Bdbg, h->B, 8 * (size_t)k * n, cudaMemcpyDeviceToDevice, st));
+  h->pw.perm = h->perm_b;
+  if (f64)
+    rc = launch_pivoted_lu<double>(reinterpret_cast<double*>(h->B), n, k, 1, n, k, h->pw, h->status_dev,
+                                   h->num_sms, st);
+  else
+    rc = launch_pivoted_lu<df32>(reinterpret_cast<df32*>(h->B), n, k, 1, n, k, h->pw, h->status_dev, h->num_sms,
+                                 st);
+  if (rc) return rc;
+  if ((rc = mark(h, 8, st))) return rc;
   AssembleArgs aa{};
   aa.m = m; aa.n = n; aa.k = k;
   aa.Lk = h->Lk; aa.perm_y = h->perm_y; aa.perm_b = h->perm_b; aa.Bp = h->B;
@@ -363,6 +502,9 @@ int rlu_destroy(rlu_t h) {
   if (h->U_stage) cudaFree(h->U_stage);
   if (h->p_stage) cudaFree(h->p_stage);
   if (h->q_stage) cudaFree(h->q_stage);
+  if (h->csr_rows_buf) cudaFree(h->csr_rows_buf);
+  if (h->csr_nnz_buf) cudaFree(h->csr_nnz_buf);
+  if (h->csr_heavy_buf) cudaFree(h->csr_heavy_buf);
   for (int i = 0; i <= kNumStages; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   delete h;
@@ -394,9 +536,14 @@ int rlu_factor_dense(rlu_t h, const void* A, int64_t lda, int dtype, void* L, vo
 
 int rlu_factor_csr(rlu_t h, const int64_t* rowptr, const int32_t* colind, const void* val, int64_t nnz, int dtype,
                    void* L, void* U, int64_t* p, int64_t* q, void* stream) {
-  (void)h; (void)rowptr; (void)colind; (void)val; (void)nnz; (void)dtype;
-  (void)L; (void)U; (void)p; (void)q; (void)stream;
-  return RLU_EINVAL;  // the CSR path is added in a later change
+  if (!h || !rowptr || !L || !U || !p || !q || nnz < 0 || nnz >= (1ll << 31)) return RLU_EINVAL;
+  if (nnz > 0 && (!colind || !val)) return RLU_EINVAL;
+  if (!((dtype == RLU_F64 && h->prec == RLU_PREC_F64) || (dtype == RLU_F32 && h->prec == RLU_PREC_F32)))
+    return RLU_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = enqueue_csr(h, rowptr, colind, val, nnz, dtype, L, U, p, q, st);
+  if (rc) return rc;
+  return finish_sync(h, st);
 }
 
 int rlu_factor_dense_host(rlu_t h, const void* A_host, int dtype, void* L_host, void* U_host, int64_t* p_host,

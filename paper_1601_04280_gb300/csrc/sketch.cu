@@ -633,6 +633,286 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_dense_tma(const TA* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// CSR sketch.  Rows are split by the host side into light rows (a warp per
+// row) and heavy rows (a whole CTA per row): a warp scatters 32 entries at a
+// time into its row's buckets in shared memory; lanes whose bucket no other
+// lane of the round hits add directly, colliding lanes add one after another
+// in lane order, so every bucket sums its entries in a fixed order.  Heavy
+// rows give each warp a contiguous part of the row and a private bucket
+// array, summed over the warps in warp order, and are also written densely
+// (row-major, n columns) for the tensor-core product.  Then the Hartley
+// transforms of row pairs run as in the dense sketch.
+// ---------------------------------------------------------------------------
+template <typename TV, typename TACC>
+__device__ __forceinline__ void csr_scatter_warp(const int32_t* __restrict__ colind, const TV* __restrict__ val,
+                                                 int64_t e0, int64_t e1, int64_t n, const uint32_t* __restrict__ hs,
+                                                 TACC* __restrict__ y1, TV* __restrict__ drow, bool& bad_csr,
+                                                 bool& bad_val, bool* increasing = nullptr) {
+  const int lane = threadIdx.x & 31;
+  int prev_last = -1;  // last column of the previous round (for the strict-increase check)
+  bool inc = true;
+  for (int64_t base = e0; base < e1; base += 32) {
+    const int64_t e = base + lane;
+    bool valid = e < e1;
+    int col = 0;
+    TACC x = TACC(0);
+    int b = -1 - lane;  // unique key for lanes without an entry
+    if (valid) {
+      col = colind[e];
+      const TV v = val[e];
+      if (col < 0 || (int64_t)col >= n) {
+        bad_csr = true;
+        valid = false;
+      } else {
+        bad_val |= !finite_(v);
+        const uint32_t h = hs[col];
+        b = (int)(h & 0x7fffffffu);
+        x = (h >> 31) ? -(TACC)v : (TACC)v;
+        if (drow) drow[col] = v;
+      }
+    }
+    if (increasing) {
+      const int c_prev = __shfl_up_sync(0xffffffffu, col, 1);
+      const int before = lane == 0 ? prev_last : c_prev;
+      if (e < e1 && col <= before) inc = false;
+      const int64_t last = min64(31, e1 - 1 - base);
+      prev_last = __shfl_sync(0xffffffffu, col, (int)last);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const bool collide = valid && __popc(peers) > 1;
+    if (valid && !collide) y1[b] += x;
+    if (__any_sync(0xffffffffu, collide)) {
+      for (int src = 0; src < 32; ++src) {
+        if (lane == src && collide) y1[b] += x;
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+  }
+  if (increasing) *increasing = __all_sync(0xffffffffu, inc);
+}
+
+// Hartley transforms of `np` row pairs stored in yrows[2*np][l1] (TACC), rows
+// out of range zero; writes Y[row[q] * l + c].
+template <typename TACC>
+__device__ void csr_pairs_fft(const TACC* __restrict__ yrows, int np, const int32_t* rows, int l1, int l,
+                              const float* __restrict__ dsign, const int32_t* __restrict__ Rsel,
+                              const typename C2<TACC>::t* twsm, typename C2<TACC>::t* fbuf, int pb, FftPlan plan,
+                              double* __restrict__ Y) {
+  using V = typename C2<TACC>::t;
+  const TACC scale = TACC(1) / sqrt(TACC(l1));
+  for (int q0 = 0; q0 < np; q0 += pb) {
+    const int nbat = min(pb, np - q0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nbat * l1; idx += blockDim.x) {
+      const int qb = idx / l1, b = idx - qb * l1;
+      const int q2 = q0 + qb;
+      const TACC ds = (TACC)dsign[b];
+      fbuf[(size_t)qb * 2 * l1 + b] = V{ds * yrows[(size_t)(2 * q2) * l1 + b], ds * yrows[(size_t)(2 * q2 + 1) * l1 + b]};
+    }
+    __syncthreads();
+    V* src = fbuf;
+    V* dst = fbuf + l1;
+    int p = 1;
+    for (int st = 0; st < plan.nstages; ++st) {
+      const int r = plan.radix[st];
+      stockham_stage_batch<V, TACC>(src, dst, 2 * l1, nbat, l1, r, p, twsm);
+      p *= r;
+      __syncthreads();
+      V* tmp = src;
+      src = dst;
+      dst = tmp;
+    }
+    for (int idx = threadIdx.x; idx < nbat * l; idx += blockDim.x) {
+      const int qb = idx / l, cidx = idx - qb * l;
+      const V* zz = src + (size_t)qb * 2 * l1;
+      const int q2 = q0 + qb;
+      const int f = Rsel[cidx];
+      const int fm = f == 0 ? 0 : l1 - f;
+      const V z = zz[f], w = zz[fm];
+      const TACC h1 = TACC(0.5) * ((z.x + w.x) - (z.y - w.y));
+      const TACC h2 = TACC(0.5) * ((z.x - w.x) + (z.y + w.y));
+      const int ra = rows[2 * q2], rb = rows[2 * q2 + 1];
+      if (ra >= 0) Y[(int64_t)ra * l + cidx] = (double)(h1 * scale);
+      if (rb >= 0) Y[(int64_t)rb * l + cidx] = (double)(h2 * scale);
+    }
+  }
+  __syncthreads();
+}
+
+constexpr int kCsrWarps = 16;
+
+// Light rows: warp w of a group takes row list[g * kCsrWarps + w].
+template <typename TV, typename TACC>
+__global__ void __launch_bounds__(kCsrWarps * 32, 1)
+    k_sketch_csr_light(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                       const TV* __restrict__ val, int64_t n, const int32_t* __restrict__ list, const int32_t* count,
+                       int l1, int l, const uint32_t* __restrict__ hs, const float* __restrict__ dsign,
+                       const int32_t* __restrict__ Rsel, const typename C2<TACC>::t* __restrict__ tw, FftPlan plan,
+                       int pb, double* __restrict__ Y, unsigned int* status) {
+  using V = typename C2<TACC>::t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  V* twsm = reinterpret_cast<V*>(smem);
+  V* fbuf = twsm + l1;
+  TACC* y1 = reinterpret_cast<TACC*>(fbuf + (size_t)pb * 2 * l1);  // [kCsrWarps][l1]
+  __shared__ int32_t rows[kCsrWarps];
+  const int warp = threadIdx.x >> 5;
+  const int nrows = *count;
+  const int ngroups = (nrows + kCsrWarps - 1) / kCsrWarps;
+  for (int e = threadIdx.x; e < l1; e += blockDim.x) twsm[e] = tw[e];
+  bool bad_csr = false, bad_val = false;
+  for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    __syncthreads();
+    const int li = g * kCsrWarps + warp;
+    const int row = li < nrows ? list[li] : -1;
+    if ((threadIdx.x & 31) == 0) rows[warp] = row;
+    TACC* my = y1 + (size_t)warp * l1;
+    for (int b = threadIdx.x & 31; b < l1; b += 32) my[b] = TACC(0);
+    __syncwarp();
+    if (row >= 0) {
+      const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
+      csr_scatter_warp<TV, TACC>(colind, val, e0, e1, n, hs, my, (TV*)nullptr, bad_csr, bad_val);
+    }
+    __syncthreads();
+    csr_pairs_fft<TACC>(y1, kCsrWarps / 2, rows, l1, l, dsign, Rsel, twsm, fbuf, pb, plan, Y);
+  }
+  if (bad_csr) set_flag(status, FLAG_BAD_CSR);
+  if (bad_val) set_flag(status, FLAG_NONFINITE);
+}
+
+// Heavy rows: a CTA per pair of rows (list[2p], list[2p+1]); the dense copy of
+// heavy row r of the list goes to D[r * n ...].
+template <typename TV, typename TACC>
+__global__ void __launch_bounds__(kCsrWarps * 32, 1)
+    k_sketch_csr_heavy(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                       const TV* __restrict__ val, int64_t n, const int32_t* __restrict__ list, const int32_t* count,
+                       int l1, int l, const uint32_t* __restrict__ hs, const float* __restrict__ dsign,
+                       const int32_t* __restrict__ Rsel, const typename C2<TACC>::t* __restrict__ tw, FftPlan plan,
+                       TV* __restrict__ D, double* __restrict__ Y, unsigned int* status) {
+  using V = typename C2<TACC>::t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  V* twsm = reinterpret_cast<V*>(smem);
+  V* fbuf = twsm + l1;                                               // [1][2][l1]
+  TACC* yrows = reinterpret_cast<TACC*>(fbuf + (size_t)2 * l1);     // [2][l1]
+  TACC* part = yrows + (size_t)2 * l1;                               // [kCsrWarps][l1]
+  __shared__ int32_t rows[2];
+  __shared__ int first_col[kCsrWarps], last_col[kCsrWarps], warp_inc[kCsrWarps];
+  __shared__ int s_redo;
+  const int warp = threadIdx.x >> 5;
+  const int nrows = *count;
+  const int npairs = (nrows + 1) / 2;
+  for (int e = threadIdx.x; e < l1; e += blockDim.x) twsm[e] = tw[e];
+  bool bad_csr = false, bad_val = false;
+  for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
+    for (int rr = 0; rr < 2; ++rr) {
+      __syncthreads();
+      const int li = 2 * p + rr;
+      const int row = li < nrows ? list[li] : -1;
+      if (threadIdx.x == 0) rows[rr] = row;
+      for (int e = threadIdx.x; e < kCsrWarps * l1; e += blockDim.x) part[e] = TACC(0);
+      if (row >= 0) {
+        TV* drow = D + (int64_t)li * n;
+        const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
+        if (e1 - e0 != n)  // not a full row: its dense copy starts from zeros
+          for (int64_t c = threadIdx.x; c < n; c += blockDim.x) drow[c] = TV(0);
+        __syncthreads();
+        const int64_t len = e1 - e0, per = (len + kCsrWarps - 1) / kCsrWarps;
+        const int64_t a = e0 + min64(len, (int64_t)warp * per), b = e0 + min64(len, (int64_t)(warp + 1) * per);
+        bool inc = true;
+        csr_scatter_warp<TV, TACC>(colind, val, a, b, n, hs, part + (size_t)warp * l1, drow, bad_csr, bad_val, &inc);
+        if ((threadIdx.x & 31) == 0) {
+          warp_inc[warp] = inc ? 1 : 0;
+          first_col[warp] = a < b ? colind[a] : -1;
+          last_col[warp] = a < b ? colind[b - 1] : -1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          // plain stores are right only for strictly increasing columns (no duplicates); a full
+          // row (n entries, no zero-fill) with strictly increasing columns holds exactly 0..n-1
+          int ok = 1;
+          int last = -1;
+          for (int w = 0; w < kCsrWarps; ++w) {
+            if (first_col[w] < 0) continue;
+            ok &= warp_inc[w] && first_col[w] > last;
+            last = last_col[w];
+          }
+          s_redo = ok ? 0 : 1;
+        }
+        __syncthreads();
+        if (s_redo) {  // rebuild the dense copy: zeros, then every entry added (duplicates summed)
+          for (int64_t c = threadIdx.x; c < n; c += blockDim.x) drow[c] = TV(0);
+          __syncthreads();
+          for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int c = colind[e];
+            if (c >= 0 && (int64_t)c < n) atomicAdd(drow + c, val[e]);
+          }
+        }
+      }
+      __syncthreads();
+      for (int b = threadIdx.x; b < l1; b += blockDim.x) {
+        TACC s = TACC(0);
+        for (int w = 0; w < kCsrWarps; ++w) s += part[(size_t)w * l1 + b];
+        yrows[(size_t)rr * l1 + b] = s;
+      }
+    }
+    csr_pairs_fft<TACC>(yrows, 1, rows, l1, l, dsign, Rsel, twsm, fbuf, 1, plan, Y);
+  }
+  if (bad_csr) set_flag(status, FLAG_BAD_CSR);
+  if (bad_val) set_flag(status, FLAG_NONFINITE);
+}
+
+template <typename TV, typename TACC>
+static int launch_csr_cfg(const int64_t* rowptr, const int32_t* colind, const TV* val, int64_t n, const CsrRows& cr,
+                          int l1, int l, const SketchWs& ws, TV* D, double* Y, unsigned int* status, int num_sms,
+                          cudaStream_t st) {
+  using V = typename C2<TACC>::t;
+  const typename C2<TACC>::t* tw;
+  if constexpr (sizeof(TACC) == 8) tw = ws.tw64; else tw = ws.tw32;
+  const size_t budget = 220 * 1024;
+  if (cr.n_light > 0) {
+    auto kern = k_sketch_csr_light<TV, TACC>;
+    const size_t fixed = (size_t)l1 * sizeof(V) + (size_t)kCsrWarps * l1 * sizeof(TACC);
+    const size_t per_pair = (size_t)2 * l1 * sizeof(V);
+    if (fixed + per_pair > budget) return RLU_EINVAL;
+    int pb = (int)((budget - fixed) / per_pair);
+    if (pb > kCsrWarps / 2) pb = kCsrWarps / 2;
+    const size_t smem = fixed + (size_t)pb * per_pair;
+    RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t groups = cdiv(cr.n_light, kCsrWarps);
+    const unsigned grid = (unsigned)min64(groups, (int64_t)num_sms);
+    kern<<<grid, kCsrWarps * 32, smem, st>>>(rowptr, colind, val, n, cr.light, cr.d_count, l1, l, ws.hs, ws.dsign,
+                                             ws.R, tw, ws.plan, pb, Y, status);
+    RLU_CUDA_TRY(cudaGetLastError());
+    note_launch();
+  }
+  if (cr.n_heavy > 0) {
+    auto kern = k_sketch_csr_heavy<TV, TACC>;
+    const size_t smem = (size_t)3 * l1 * sizeof(V) + (size_t)(2 + kCsrWarps) * l1 * sizeof(TACC);
+    if (smem > budget) return RLU_EINVAL;
+    RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t pairs = cdiv(cr.n_heavy, 2);
+    const unsigned grid = (unsigned)min64(pairs, (int64_t)num_sms);
+    kern<<<grid, kCsrWarps * 32, smem, st>>>(rowptr, colind, val, n, cr.heavy, cr.d_count + 1, l1, l, ws.hs,
+                                             ws.dsign, ws.R, tw, ws.plan, D, Y, status);
+    RLU_CUDA_TRY(cudaGetLastError());
+    note_launch();
+  }
+  return RLU_OK;
+}
+
+int launch_sketch_csr(const int64_t* rowptr, const int32_t* colind, const void* val, int dtype, int64_t n,
+                      const CsrRows& cr, int l1, int l, const SketchWs& ws, void* D, double* Y, unsigned int* status,
+                      int num_sms, cudaStream_t st) {
+  if (dtype == RLU_F64)
+    return launch_csr_cfg<double, double>(rowptr, colind, (const double*)val, n, cr, l1, l, ws, (double*)D, Y,
+                                          status, num_sms, st);
+  if (dtype == RLU_F32)
+    return launch_csr_cfg<float, float>(rowptr, colind, (const float*)val, n, cr, l1, l, ws, (float*)D, Y, status,
+                                        num_sms, st);
+  return RLU_EINVAL;
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
 FftPlan make_fft_plan(int N) {
@@ -661,6 +941,13 @@ int launch_sketch_params(const SketchWs& ws, int64_t n, int l1, int l, uint64_t 
   k_bucket_sort<<<(unsigned)cdiv(nsb, 256), 256, 0, st>>>(nsb, ws.bstart, ws.blist);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch(6);
+  return RLU_OK;
+}
+
+int launch_scan_i32(int64_t count, const int32_t* cnt, int32_t* start, cudaStream_t st) {
+  k_scan_counts<<<1, 1024, 0, st>>>(count, cnt, start);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
   return RLU_OK;
 }
 
