@@ -104,11 +104,16 @@ def sem_matrix(params, l1):
 # Step 2: the sketch Y = A * Omega_1^T
 # ---------------------------------------------------------------------------
 def countsketch(A, params, l1):
-    """Y1 = A S, i.e. Y1[i, h(j)] += s(j) A[i, j] (Sec. 2.2, Lemma 2.6 cost)."""
+    """Y1 = A S, i.e. Y1[i, h(j)] += s(j) A[i, j] (Sec. 2.2, Lemma 2.6 cost).
+
+    Computed as the product with the sparse S (one term per entry of A), so
+    the cost is that of reading A once, as the paper states for the SEM.
+    """
     S = sem_matrix(params, l1)
     if scipy.sparse.issparse(A):
         return np.asarray((A.tocsr().astype(np.float64) @ S).todense())
-    return np.asarray(A, dtype=np.float64) @ S.toarray()
+    A = np.asarray(A, dtype=np.float64)
+    return np.asarray((S.T.tocsr() @ A.T).T)
 
 
 def hartley_columns(l1, freqs):

@@ -47,6 +47,7 @@ struct rlu_ctx {
   void* B = nullptr;
   void* LyP = nullptr;
   void* Lb = nullptr;
+  double* bpart = nullptr;  // split-K partials of the FP64 SIMT B = W A
   TcWs tcw{};
   unsigned int* status_dev = nullptr;
   unsigned int* bar2 = nullptr;
@@ -131,6 +132,7 @@ Sizes plan_sizes(int64_t m, int64_t n, int k, int l, int l1, int num_sms) {
   s.add(sizeof(double) * k * k);                     // Lb
   s.add(sizeof(unsigned int) * 4);                   // status, bar2
   s.add(tc_workspace_bytes(m, n, k, num_sms));       // tensor-core GEMM: W planes, partials
+  s.add(sizeof(double) * bgemm_simt_splits(m, n, k, num_sms) * k * n);  // FP64 B = W A partials
   return s;
 }
 
@@ -283,7 +285,7 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
     rc = launch_bgemm_tc(h->tcw, reinterpret_cast<const float*>(h->W), A, lda, dtype, h->prec, m, n, k,
                          reinterpret_cast<df32*>(h->B), h->status_dev, st);
   else
-    rc = launch_bgemm_simt(h->W, f64 ? 1 : 0, A, lda, dtype, m, n, k, h->B, st);
+    rc = launch_bgemm_simt(h->W, f64 ? 1 : 0, A, lda, dtype, m, n, k, h->B, h->bpart, h->num_sms, st);
   if (rc) return rc;
   if ((rc = mark(h, 7, st))) return rc;
   if (h->debug && h->Bdbg)
@@ -467,7 +469,9 @@ int rlu_create(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t 
   h->Lb = next();
   h->status_dev = (unsigned int*)next();
   h->bar2 = h->status_dev + 1;
-  if (tc_setup(h->tcw, next(), m, n, k, sms) != RLU_OK) {
+  void* tcbase = next();
+  h->bpart = (double*)next();
+  if (tc_setup(h->tcw, tcbase, m, n, k, sms) != RLU_OK) {
     rlu_destroy(h);
     return RLU_ECUDA;
   }

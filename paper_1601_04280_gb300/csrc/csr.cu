@@ -305,7 +305,7 @@ int csr_bgemm(CsrWs& w, const int64_t* rowptr, const int32_t* colind, const void
       k_gather_cols<double><<<g, 256, 0, st>>>(k, m, nh, (const double*)W, cr.heavy, (double*)w.Wh);
       RLU_CUDA_TRY(cudaGetLastError());
       note_launch();
-      rc = launch_bgemm_simt(w.Wh, 1, w.D, n, RLU_F64, nh, n, k, B, st);
+      rc = launch_bgemm_simt(w.Wh, 1, w.D, n, RLU_F64, nh, n, k, B, nullptr, num_sms, st);
     } else {
       k_gather_cols<float><<<g, 256, 0, st>>>(k, m, nh, (const float*)W, cr.heavy, (float*)w.Wh);
       RLU_CUDA_TRY(cudaGetLastError());
@@ -313,7 +313,7 @@ int csr_bgemm(CsrWs& w, const int64_t* rowptr, const int32_t* colind, const void
       if (w.tc.ready)
         rc = launch_bgemm_tc(w.tc, (const float*)w.Wh, w.D, n, RLU_F32, prec, nh, n, k, (df32*)B, status, st);
       else
-        rc = launch_bgemm_simt(w.Wh, 0, w.D, n, RLU_F32, nh, n, k, B, st);
+        rc = launch_bgemm_simt(w.Wh, 0, w.D, n, RLU_F32, nh, n, k, B, nullptr, num_sms, st);
     }
     if (rc) return rc;
   } else {

@@ -338,10 +338,29 @@ template int launch_assemble<df32, float>(const AssembleArgs&, cudaStream_t);
 // ---------------------------------------------------------------------------
 // B = W A (first version: SIMT, FP32 or FP64 accumulate)
 // ---------------------------------------------------------------------------
+int bgemm_simt_splits(int64_t m, int64_t n, int k, int num_sms) {
+  const int64_t tiles = cdiv(k, 64) * cdiv(n, 64);
+  int64_t S = cdiv(2 * (int64_t)num_sms, tiles);
+  S = min64(S, max64(1, m / 256));
+  return (int)max64(1, S);
+}
+
 int launch_bgemm_simt(const void* W, int w64, const void* A, int64_t lda, int dtype, int64_t m, int64_t n, int k,
-                      void* B, cudaStream_t st) {
+                      void* B, double* part, int num_sms, cudaStream_t st) {
   if (w64) {
     if (dtype != RLU_F64) return RLU_EINVAL;
+    // small k x n: split the m-long contraction (partials summed in fixed order)
+    const int S = part ? bgemm_simt_splits(m, n, k, num_sms) : 1;
+    if (S > 1) {
+      int rc = gemm_simt<double, double, double, double>(st, k, n, m, (const double*)W, m, 1, (const double*)A, lda,
+                                                         1, part, n, 1, S, (int64_t)k * n);
+      if (rc) return rc;
+      k_sum_slices<double><<<(unsigned)cdiv((int64_t)k * n, 256), 256, 0, st>>>((int64_t)k * n, S, part,
+                                                                                (double*)B);
+      RLU_CUDA_TRY(cudaGetLastError());
+      note_launch();
+      return RLU_OK;
+    }
     return gemm_simt<double, double, double, double>(st, k, n, m, (const double*)W, m, 1, (const double*)A, lda, 1,
                                                      (double*)B, n, 1);
   }

@@ -43,7 +43,10 @@ int launch_chol(const PinvArgs& a, cudaStream_t st);
 int launch_wform(const PinvArgs& a, cudaStream_t st);
 template <typename T, typename TO>
 int launch_assemble(const AssembleArgs& a, cudaStream_t st);
+// B = W A on the SIMT pipes; `part` (bgemm_simt_splits * k * n doubles, or
+// null) lets the FP64 product split its contraction when k x n is small.
+int bgemm_simt_splits(int64_t m, int64_t n, int k, int num_sms);
 int launch_bgemm_simt(const void* W, int w64, const void* A, int64_t lda, int dtype, int64_t m, int64_t n, int k,
-                      void* B, cudaStream_t st);
+                      void* B, double* part, int num_sms, cudaStream_t st);
 
 }  // namespace rlu

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
     // 5. the rest of the rank-1 update (columns j+2.., rows other than rstar)
     const int c0 = j + 2;
     if (!zero && c0 < cols) {
-      if (SMEM || !row_fast) {
+      if (SMEM) {
         for (int r = warp; r < nr; r += NW) {
           if (lstep[r] < 0 && r != rstar) {
             const T lv = -lval[r];
@@ -251,14 +251,28 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
           }
         }
       } else {
-        for (int c = c0 + warp; c < cols; c += NW) {
-          const T u = urow[c - j];
-          for (int r = lane; r < nr; r += 32) {
-            if (lstep[r] < 0 && r != rstar) {
-              T& x = at(r, c);
-              x = mad(-lval[r], u, x);
-            }
+        // global memory: a flat loop over (row, column) with several independent
+        // elements per thread in flight; the fast index follows the memory layout
+        const int width = cols - c0;
+        const int tot = nr * width;
+        constexpr int U = 4;
+        for (int base = tid; base < tot; base += NT * U) {
+          T xv[U];
+          int rr[U], cc[U];
+          bool act[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int idx = base + u * NT;
+            int r, c;
+            if (row_fast) { r = idx % nr; c = idx / nr; } else { c = idx % width; r = idx / width; }
+            rr[u] = r;
+            cc[u] = c0 + c;
+            act[u] = idx < tot && lstep[r < nr ? r : 0] < 0 && r != rstar;
+            if (act[u]) xv[u] = at(r, c0 + c);
           }
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (act[u]) at(rr[u], cc[u]) = mad(-lval[rr[u]], urow[cc[u] - j], xv[u]);
         }
       }
     }
@@ -292,7 +306,7 @@ static size_t pivlu_smem(int64_t rpc, int cols, int steps) {
 template <typename T, bool SMEM>
 static int launch_cfg(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int steps, int G, PivLuWs& ws,
                       unsigned int* status, cudaStream_t st) {
-  constexpr int NT = 256;
+  constexpr int NT = SMEM ? 256 : 1024;
   const int64_t rpc = cdiv(rows, G);
   size_t smem = pivlu_smem<T, SMEM>(rpc, cols, steps);
   auto kern = k_pivoted_lu<T, SMEM, NT>;
