@@ -79,6 +79,18 @@ typedef enum { RLU_PREC_F64 = 0, RLU_PREC_F32 = 1, RLU_PREC_BF16 = 2, RLU_PREC_B
  * Errors: RLU_EINVAL for bad sizes or a null `out`, RLU_ENOMEM, RLU_ECUDA. */
 int rlu_create(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t seed, rlu_t* out);
 
+/* As rlu_create, but the handle's workspace is the caller's device memory
+ * `workspace` (256-byte aligned, at least rlu_workspace_bytes(...) bytes, kept
+ * alive and unused by others until rlu_destroy): nothing is allocated on the
+ * device, nothing waits for the device, and the one set-up kernel (the FFT
+ * twiddles) is enqueued on `stream`.  For callers that manage device memory
+ * themselves (a serving loop that admits requests by HBM footprint from its
+ * own pool).  The CSR entry point still allocates its per-entry scratch on
+ * first use.  Errors: RLU_EINVAL (sizes, null, misaligned or too small
+ * workspace), RLU_ENOMEM (host), RLU_ECUDA. */
+int rlu_create_in(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t seed, void* workspace,
+                  size_t workspace_bytes, void* stream, rlu_t* out);
+
 /* Select the arithmetic (rlu_prec).  Valid at any time between calls. */
 int rlu_set_precision(rlu_t h, int prec);
 

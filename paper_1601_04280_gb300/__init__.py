@@ -24,7 +24,7 @@ RLU_PREC_F64, RLU_PREC_F32, RLU_PREC_BF16, RLU_PREC_BF16_REFINE = 0, 1, 2, 3
 PREC = {"f64": RLU_PREC_F64, "f32": RLU_PREC_F32, "bf16": RLU_PREC_BF16, "bf16_refine": RLU_PREC_BF16_REFINE}
 
 #: every entry point declared in include/rlu.h
-C_SYMBOLS = ("rlu_create", "rlu_set_precision", "rlu_workspace_bytes", "rlu_factor_dense",
+C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_bytes", "rlu_factor_dense",
              "rlu_factor_dense_async", "rlu_factor_csr", "rlu_factor_dense_host", "rlu_destroy",
              "rlu_strerror", "rlu_debug_sketch_params", "rlu_debug_Y", "rlu_debug_B", "rlu_debug_enable",
              "rlu_debug_timing", "rlu_debug_stage_ms", "rlu_debug_launch_count", "rlu_sketch_dense_noalloc")
@@ -53,6 +53,7 @@ def load(reload=False):
     vp, i64, i32, u64 = c.c_void_p, c.c_int64, c.c_int32, c.c_uint64
     sig = {
         "rlu_create": ([i64, i64, i32, i32, i32, u64, c.POINTER(vp)], c.c_int),
+        "rlu_create_in": ([i64, i64, i32, i32, i32, u64, vp, c.c_size_t, vp, c.POINTER(vp)], c.c_int),
         "rlu_set_precision": ([vp, c.c_int], c.c_int),
         "rlu_workspace_bytes": ([i64, i64, i32, i32, i32, c.c_int, c.POINTER(c.c_size_t)], c.c_int),
         "rlu_factor_dense": ([vp, vp, i64, c.c_int, vp, vp, vp, vp, vp], c.c_int),
@@ -98,6 +99,13 @@ def _check(code, where, allow_warn=True):
 def rlu_create(m, n, k, l, l1, seed):
     h = ctypes.c_void_p()
     _check(load().rlu_create(m, n, k, l, l1, ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(h)), "rlu_create")
+    return h
+
+
+def rlu_create_in(m, n, k, l, l1, seed, workspace_ptr, workspace_bytes, stream_ptr):
+    h = ctypes.c_void_p()
+    _check(load().rlu_create_in(m, n, k, l, l1, ctypes.c_uint64(seed & (2**64 - 1)), workspace_ptr,
+                                workspace_bytes, stream_ptr, ctypes.byref(h)), "rlu_create_in")
     return h
 
 
@@ -168,9 +176,15 @@ def _stream_ptr(stream):
 class RandLU:
     """One handle: fixed sizes, seed and precision; reusable across calls."""
 
-    def __init__(self, m, n, k, l, l1, seed, prec="f32"):
+    def __init__(self, m, n, k, l, l1, seed, prec="f32", workspace=None, stream=None):
+        """workspace: optional device tensor (uint8, >= rlu_workspace_bytes) the handle
+        uses instead of allocating; the caller keeps it alive until close()."""
         self.m, self.n, self.k, self.l, self.l1, self.seed = m, n, k, l, l1, seed
-        self.h = rlu_create(m, n, k, l, l1, seed)
+        if workspace is None:
+            self.h = rlu_create(m, n, k, l, l1, seed)
+        else:
+            self.h = rlu_create_in(m, n, k, l, l1, seed, ctypes.c_void_p(workspace.data_ptr()),
+                                   workspace.numel() * workspace.element_size(), _stream_ptr(stream))
         self.prec = prec
         rlu_set_precision(self.h, prec)
 

@@ -17,9 +17,34 @@
 
 using namespace rlu;
 
+#include <mutex>
+
 namespace rlu {
 static std::atomic<long long> g_launches{0};
 void note_launch(int count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+
+static std::mutex g_coop_mu;
+static cudaEvent_t g_coop_evt[64] = {};
+static bool g_coop_any[64] = {};
+
+cudaError_t launch_cooperative(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
+  int dev = 0;
+  if (cap != cudaStreamCaptureStatusNone || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return cudaLaunchCooperativeKernel(func, grid, block, args, smem, st);
+  std::lock_guard<std::mutex> lock(g_coop_mu);
+  if (!g_coop_evt[dev]) {
+    cudaError_t e = cudaEventCreateWithFlags(&g_coop_evt[dev], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e;
+  if (g_coop_any[dev] && (e = cudaStreamWaitEvent(st, g_coop_evt[dev], 0)) != cudaSuccess) return e;
+  if ((e = cudaLaunchCooperativeKernel(func, grid, block, args, smem, st)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(g_coop_evt[dev], st)) != cudaSuccess) return e;
+  g_coop_any[dev] = true;
+  return cudaSuccess;
+}
 }  // namespace rlu
 
 // Stages whose device time the timing hook reports, in order.
@@ -51,7 +76,8 @@ struct rlu_ctx {
   TcWs tcw{};
   unsigned int* status_dev = nullptr;
   unsigned int* bar2 = nullptr;
-  unsigned int* status_host = nullptr;  // pinned
+  unsigned int* status_host = nullptr;  // pinned when status_pinned, else ordinary host memory
+  bool status_pinned = false;
   int debug = 0;
   double* Ydbg = nullptr;
   void* Bdbg = nullptr;
@@ -414,10 +440,11 @@ int rlu_workspace_bytes(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, 
   return RLU_OK;
 }
 
-int rlu_create(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t seed, rlu_t* out) {
-  if (!out) return RLU_EINVAL;
-  *out = nullptr;
-  if (!sizes_ok(m, n, k, l, l1)) return RLU_EINVAL;
+// Build a handle on workspace `base` (plan_sizes(...).total bytes).  With
+// own_base the handle frees it; the caller's stream receives the twiddle
+// launch.  `pinned` chooses page-locked memory for the status read-back.
+static int create_common(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t seed, char* base,
+                         bool own_base, bool pinned, cudaStream_t st, rlu_t* out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return RLU_ECUDA;
   int sms = 0;
@@ -427,13 +454,7 @@ int rlu_create(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t 
   h->m = m; h->n = n; h->k = k; h->l = l; h->l1 = l1; h->seed = seed;
   h->device = dev; h->num_sms = sms;
   Sizes sz = plan_sizes(m, n, k, l, l1, sms);
-  char* base = nullptr;
-  if (cudaMalloc(&base, sz.total) != cudaSuccess) {
-    cudaGetLastError();
-    delete h;
-    return RLU_ENOMEM;
-  }
-  h->allocs.push_back(base);
+  if (own_base) h->allocs.push_back(base);
   size_t off = 0;
   int idx = 0;
   auto next = [&](void) -> void* { void* p = base + off; off += sz.parts[idx++]; return p; };
@@ -475,18 +496,65 @@ int rlu_create(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t 
     rlu_destroy(h);
     return RLU_ECUDA;
   }
-
-  if (cudaMallocHost(&h->status_host, sizeof(unsigned int)) != cudaSuccess) {
-    cudaGetLastError();
-    rlu_destroy(h);
-    return RLU_ENOMEM;
+  if (pinned) {
+    if (cudaMallocHost(&h->status_host, sizeof(unsigned int)) != cudaSuccess) {
+      cudaGetLastError();
+      rlu_destroy(h);
+      return RLU_ENOMEM;
+    }
+    h->status_pinned = true;
+  } else {
+    h->status_host = new (std::nothrow) unsigned int(0);
+    if (!h->status_host) {
+      rlu_destroy(h);
+      return RLU_ENOMEM;
+    }
   }
-  if (launch_twiddles(l1, h->sk.tw64, h->sk.tw32, 0) != RLU_OK || cudaDeviceSynchronize() != cudaSuccess) {
+  if (launch_twiddles(l1, h->sk.tw64, h->sk.tw32, st) != RLU_OK) {
     rlu_destroy(h);
     return RLU_ECUDA;
   }
   *out = h;
   return RLU_OK;
+}
+
+int rlu_create(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t seed, rlu_t* out) {
+  if (!out) return RLU_EINVAL;
+  *out = nullptr;
+  if (!sizes_ok(m, n, k, l, l1)) return RLU_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return RLU_ECUDA;
+  char* base = nullptr;
+  if (cudaMalloc(&base, plan_sizes(m, n, k, l, l1, sms).total) != cudaSuccess) {
+    cudaGetLastError();
+    return RLU_ENOMEM;
+  }
+  int rc = create_common(m, n, k, l, l1, seed, base, true, true, 0, out);
+  if (rc) {
+    if (!*out) cudaFree(base);
+    return rc;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    rlu_destroy(*out);
+    *out = nullptr;
+    return RLU_ECUDA;
+  }
+  return RLU_OK;
+}
+
+int rlu_create_in(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t seed, void* workspace,
+                  size_t workspace_bytes, void* stream, rlu_t* out) {
+  if (!out) return RLU_EINVAL;
+  *out = nullptr;
+  if (!sizes_ok(m, n, k, l, l1) || !workspace || ((uintptr_t)workspace % 256) != 0) return RLU_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return RLU_ECUDA;
+  if (workspace_bytes < plan_sizes(m, n, k, l, l1, sms).total) return RLU_EINVAL;
+  return create_common(m, n, k, l, l1, seed, (char*)workspace, false, false, (cudaStream_t)stream, out);
 }
 
 int rlu_set_precision(rlu_t h, int prec) {
@@ -498,7 +566,10 @@ int rlu_set_precision(rlu_t h, int prec) {
 int rlu_destroy(rlu_t h) {
   if (!h) return RLU_OK;
   for (void* p : h->allocs) cudaFree(p);
-  if (h->status_host) cudaFreeHost(h->status_host);
+  if (h->status_host) {
+    if (h->status_pinned) cudaFreeHost(h->status_host);
+    else delete h->status_host;
+  }
   if (h->Ydbg) cudaFree(h->Ydbg);
   if (h->Bdbg) cudaFree(h->Bdbg);
   if (h->A_stage) cudaFree(h->A_stage);

@@ -242,6 +242,12 @@ template <typename T> __device__ __forceinline__ T one_() { return cvt<T>(1.0); 
 // Process-wide count of kernels this library has launched (a test hook).
 void note_launch(int count = 1);
 
+// Cooperative launch of a kernel with grid barriers.  Such kernels from
+// different streams are chained on the GPU (each waits for the previous one
+// to finish, through an event), so two of them are never partly resident at
+// once and waiting on each other; all other kernels still overlap freely.
+cudaError_t launch_cooperative(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st);
+
 __host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }

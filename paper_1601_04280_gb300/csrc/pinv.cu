@@ -249,7 +249,7 @@ int launch_chol(const PinvArgs& a, cudaStream_t st) {
   unsigned int* bar = a.bar;
   unsigned int* status = a.status;
   void* args[] = {&kk, &Sm, &Ri, &bar, &status};
-  RLU_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_chol_inv, G, 256, args, smem, st));
+  RLU_CUDA_TRY(launch_cooperative((void*)k_chol_inv, G, 256, args, smem, st));
   note_launch();
   return RLU_OK;
 }

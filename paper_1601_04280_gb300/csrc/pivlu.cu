@@ -319,7 +319,7 @@ static int launch_cfg(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int 
   T* candrow = reinterpret_cast<T*>(ws.candrow);
   void* args[] = {&X, &rows, &cols, &rs, &cs, &steps, (void*)&rpc, &ws.pos, &ws.pstep, &ws.perm,
                   &cand, &candrow, &ws.bar, &status};
-  RLU_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, G, NT, args, smem, st));
+  RLU_CUDA_TRY(launch_cooperative((void*)kern, G, NT, args, smem, st));
   note_launch();
   return RLU_OK;
 }
