@@ -40,6 +40,8 @@ WORKLOADS = {
     "dense_bf16_32768x16384_k500": ("DENSE_BF16_32K", "bf16_refine", "dense"),
 }
 DEFAULT_WORKLOAD = "dense_f32_8192x8192_k200"
+#: the serving form: a trace of independent requests of uneven sizes
+SERVING_WORKLOAD = "serving_4096req_mixed_dense_f32_csr"
 
 
 def measured_peaks():
@@ -175,7 +177,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + [SERVING_WORKLOAD])
+    ap.add_argument("--requests", type=int, default=4096, help="serving: requests in the trace")
+    ap.add_argument("--slots", type=int, default=8, help="serving: concurrent slots")
+    ap.add_argument("--pool-gb", type=float, default=48.0, help="serving: device pool for admission (GiB)")
+    ap.add_argument("--e2e-requests", type=int, default=256, help="serving: requests of the host-arrival run")
     ap.add_argument("--prec", default=None, help="override the workload's precision (f64, f32, bf16, bf16_refine)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -184,7 +190,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
+        if args.workload == SERVING_WORKLOAD:
+            return run_serving_reference(args, rank)
         return run_reference(args, rank)
+    if args.workload == SERVING_WORKLOAD:
+        return run_serving(args, rank, world, local)
 
     import torch
     import torch.distributed as dist
@@ -249,6 +259,34 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * args.steps / (total_ms / 1e3)
+
+    # the same steps replayed from one captured launch graph (dense inputs)
+    graph = None
+    if kind == "dense":
+        import ctypes
+        st_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+        gstream = torch.cuda.Stream(dev)
+        gstream.wait_stream(stream)
+        sp = ctypes.c_void_p(gstream.cuda_stream)
+        ptrs = [ctypes.c_void_p(x.data_ptr()) for x in (dev_in[0],) + tuple(outs)]
+        g = rg.rlu_graph_capture_dense(h.h, ptrs[0], dev_in[0].stride(0), rg._dtype_code(dev_in[0]), *ptrs[1:],
+                                       ctypes.c_void_p(st_dev.data_ptr()), sp)
+        for _ in range(args.warmup):
+            rg.rlu_graph_launch(g, sp)
+        gev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        gstream.synchronize()
+        gev[0].record(gstream)
+        for i in range(args.steps):
+            rg.rlu_graph_launch(g, sp)
+            gev[i + 1].record(gstream)
+        gstream.synchronize()
+        gms = [gev[i].elapsed_time(gev[i + 1]) for i in range(args.steps)]
+        gtot = gev[0].elapsed_time(gev[-1])
+        graph = {"value": args.steps / (gtot / 1e3), "unit": UNIT, "ms_per_step": gtot / args.steps,
+                 "latency_ms": {"p50": statistics.median(gms), "p99": float(np.percentile(gms, 99))},
+                 "status": int(st_dev.item())}
+        rg.rlu_graph_destroy(g)
+        stream.wait_stream(gstream)
 
     # per-stage device times (events on the same stream between the stages)
     h.debug_timing(True)
@@ -346,6 +384,7 @@ def main():
                        if a_bytes > 135e6 else "inputs smaller than L2 (latency-bound workload)",
                        "parallelism": "independent problems per GPU" if world > 1 else "single GPU"},
             "latency_ms": {"p50": statistics.median(step_ms), "p99": float(np.percentile(step_ms, 99))},
+            "graph_replay": graph,
             "a_read_gbs": 2.0 * a_bytes / (total_ms / args.steps / 1e3) / 1e9,
             "a_read_frac_of_hbm": 2.0 * a_bytes / (total_ms / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"],
             "stage_ms": stage_acc,
@@ -360,6 +399,234 @@ def main():
     h.close()
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def serving_requests(specs, device, base_count=8, base_size=16384):
+    """Requests of the trace with inputs made on `device` (see rlu_inputs.serving)."""
+    from paper_1601_04280_gb300 import serving
+    from rlu_inputs import serving as rs
+    used = sorted({s.data_seed % base_count for s in specs if s.kind == "dense"})
+    base = [None] * base_count
+    for b in used:
+        base[b] = rs.dense_base_pool(1, base_size, device, seed=3000 + b)[0]
+    out = []
+    for s in specs:
+        r = serving.Request(s.rid, s.m, s.n, s.k, s.l, s.l1, rs.SKETCH_SEED)
+        if s.kind == "dense":
+            r.A = base[s.data_seed % base_count][: s.m, : s.n]
+        else:
+            r.csr = rs.csr_request(s, device)
+        out.append(r)
+    return out
+
+
+def request_input_bytes(r):
+    if r.csr is not None:
+        return 8 * (r.m + 1) + sum(t.element_size() * t.numel() for t in r.csr[1:])
+    return r.A.element_size() * r.m * r.n
+
+
+def oracle_request_seconds(r):
+    import scipy.sparse
+
+    import oracle
+    if r.csr is not None:
+        rowptr, colind, val = (t.cpu().numpy() for t in r.csr)
+        A = scipy.sparse.csr_matrix((val.astype(np.float64), colind, rowptr), shape=(r.m, r.n))
+    else:
+        A = r.A.cpu().double().numpy()
+    t0 = time.perf_counter()
+    oracle.factor(A, r.k, r.l, r.l1, r.seed)
+    return time.perf_counter() - t0
+
+
+def oracle_sample(reqs, budget_s):
+    """Oracle factorizations of the trace's requests in order until budget_s of CPU time."""
+    done, tot = 0, 0.0
+    for r in reqs:
+        tot += oracle_request_seconds(r)
+        done += 1
+        if tot >= budget_s:
+            break
+    return done, tot
+
+
+def run_serving(args, rank, world, local):
+    """Serving form: slots x streams over one device pool, a 4096-request trace.
+
+    value = requests / makespan with every request waiting at time 0 (the
+    saturation throughput); then the same trace with Poisson arrivals at 0.5x
+    and 0.9x of that rate (p50/p99 latency from arrival to factors ready), and
+    one request at a time (a single slot) as the baseline.  Times are host
+    wall-clock around the run: a request is done when its status is back.
+    """
+    import torch
+    import torch.distributed as dist
+
+    import paper_1601_04280_gb300 as rg
+    from paper_1601_04280_gb300 import serving
+    from rlu_inputs import serving as rs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    rg.load()
+    specs = rs.make_trace(args.requests, seed=rs.SKETCH_SEED + rank)
+    reqs = serving_requests(specs, dev)
+    torch.cuda.synchronize()
+    pool_bytes = int(args.pool_gb * 2 ** 30)
+    nwarm = max(3, args.warmup) * args.slots
+    warm = [serving.Request(10 ** 6 + i, r.m, r.n, r.k, r.l, r.l1, r.seed, A=r.A, csr=r.csr)
+            for i, r in enumerate(reqs[:nwarm])]
+    a_read = sum(2.0 * request_input_bytes(r) for r in reqs)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def set_arrivals(rate):
+        t = 0.0
+        for r, s in zip(reqs, specs):
+            t += s.gap / rate
+            r.t_arrive = t
+
+    with serving.Server(pool_bytes, slots=args.slots) as srv:
+        srv.run(warm, open_loop=False)
+        torch.cuda.synchronize()
+        l0 = rg.rlu_debug_launch_count()
+        barrier()
+        with ClockSampler(local) as clk:
+            res_sat, span_sat = srv.run(reqs, open_loop=False)
+        barrier()
+        launches = rg.rlu_debug_launch_count() - l0
+        span_max = span_sat
+        if world > 1:
+            t = torch.tensor([span_sat], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            span_max = float(t.item())
+        sat = len(reqs) / span_sat
+        runs = {"saturation": serving.summarize(res_sat, span_sat)}
+        for frac in (0.5, 0.9):
+            set_arrivals(frac * sat)
+            res, span = srv.run(reqs, open_loop=True)
+            runs["open_loop_%.1fx" % frac] = dict(serving.summarize(res, span), arrival_rate=frac * sat)
+    with serving.Server(pool_bytes, slots=1) as one:
+        one.run(warm[:3], open_loop=False)
+        res_one, span_one = one.run(reqs, open_loop=False)
+        s1 = serving.summarize(res_one, span_one)
+        svc = np.array([r.t_done - r.t_admit for r in res_one]) * 1e3
+        s1.update(service_p50_ms=float(np.percentile(svc, 50)), service_p99_ms=float(np.percentile(svc, 99)))
+        runs["one_at_a_time"] = s1
+    failed = [r.rid for r in res_sat if r.status not in (rg.RLU_OK, rg.RLU_WRANK)]
+
+    # end to end: the first requests arrive from page-locked host memory and
+    # their L, U, p, q and status go back to page-locked host memory
+    sub = reqs[: args.e2e_requests]
+    host_base = {}
+    hreqs = []
+    for r in sub:
+        q = serving.Request(r.rid, r.m, r.n, r.k, r.l, r.l1, r.seed)
+        if r.csr is not None:
+            q.csr = tuple(t.cpu().pin_memory() for t in r.csr)
+        else:
+            b = r.A.data_ptr()
+            if b not in host_base:
+                host_base[b] = r.A.as_strided((16384, 16384), (16384, 1)).cpu().pin_memory()
+            q.A = host_base[b][: r.m, : r.n]
+        hreqs.append(q)
+    with serving.Server(pool_bytes, slots=args.slots, return_host=(16384, 16384, 256, "f32")) as srv:
+        srv.run(hreqs[: args.slots], open_loop=False)
+        barrier()
+        res_e2e, span_e2e = srv.run(hreqs, open_loop=False)
+        barrier()
+    h2d = sum(request_input_bytes(r) for r in sub) / len(sub)
+    d2h = sum(4 * (r.m * r.k + r.k * r.n) + 8 * (r.m + r.n) + 4 for r in sub) / len(sub)
+    e2e_value = len(hreqs) / span_e2e
+    if world > 1:
+        t = torch.tensor([span_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_value = world * len(hreqs) / float(t.item())
+
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        ach = a_read / span_sat / 1e9
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            done, secs = oracle_sample(reqs, 20.0)
+            cpu = {"value": done / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": "the first %d requests of the trace, one after another, by the FP64 oracle" % done}
+        line = {
+            "metric": METRIC, "value": world * len(reqs) / span_max, "unit": UNIT, "n_gpus": world,
+            "steps": len(reqs), "warmup": len(warm), "ms_per_step": 1e3 * span_sat / len(reqs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": SERVING_WORKLOAD, "requests": len(reqs), "slots": args.slots,
+                       "pool_gib": args.pool_gb, "m_n": "log-uniform [512, 16384]", "k": "uniform [16, 256]",
+                       "l": "k + 20", "l1": "8 k", "dense_share": rs.DENSE_SHARE, "csr_density": rs.CSR_DENSITY,
+                       "dense_inputs": "leading blocks of 8 rank-96 16384^2 FP32 matrices, geometric spectrum",
+                       "l2": "inputs larger than L2 for most requests (mean dense A %.0f MB)" % (
+                           np.mean([request_input_bytes(r) for r in reqs if r.csr is None]) / 1e6),
+                       "parallelism": "replicas (independent traces per GPU)" if world > 1 else "single GPU"},
+            "timing": "host wall clock around each run; a request is done when its status is on the host",
+            "serving": runs,
+            "speedup_vs_one_at_a_time": sat / runs["one_at_a_time"]["factorizations_per_s"],
+            "latency_ms": {"p50": runs["open_loop_0.9x"]["p50_ms"], "p99": runs["open_loop_0.9x"]["p99_ms"],
+                           "at": "Poisson arrivals at 0.9x the saturation throughput"},
+            "failed_requests": failed,
+            "a_read_gbs": ach,
+            "roofline": {"kernel": "whole serving run (all kernels)", "bound": "hbm", "achieved": ach,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                         "peak_kind": peak_kind,
+                         "note": "achieved = two algorithmic reads of every request's A / makespan"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "requests": len(hreqs),
+                    "mode": "host arrival: A (or CSR arrays) from page-locked host memory, factors back to it"},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_serving_reference(args, rank):
+    """The oracle on the serving trace's requests, one after another (host cores)."""
+    if rank != 0:
+        return 0
+    from rlu_inputs import serving as rs
+    specs = rs.make_trace(args.requests, seed=rs.SKETCH_SEED)
+    budget = 30.0
+    # inputs made on the host with torch's CPU generator (same recipe as the GPU arm)
+    sample = []
+    tot, done = 0.0, 0
+    for i in range(0, len(specs), 8):
+        reqs = serving_requests(specs[i:i + 8], "cpu", base_count=8)
+        for r in reqs:
+            if done >= args.warmup + args.steps or tot >= budget:
+                break
+            secs = oracle_request_seconds(r)
+            if done >= args.warmup:
+                sample.append(secs)
+                tot += secs
+            done += 1
+        if done >= args.warmup + args.steps or tot >= budget:
+            break
+    value = len(sample) / sum(sample)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": len(sample), "warmup": args.warmup, "ms_per_step": 1e3 * sum(sample) / len(sample),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": SERVING_WORKLOAD, "requests": args.requests},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "%d requests of the trace in order, after %d warm-up, by the FP64 oracle"
+                                   % (len(sample), args.warmup)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 

@@ -85,11 +85,33 @@ int rlu_create(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t 
  * device, nothing waits for the device, and the one set-up kernel (the FFT
  * twiddles) is enqueued on `stream`.  For callers that manage device memory
  * themselves (a serving loop that admits requests by HBM footprint from its
- * own pool).  The CSR entry point still allocates its per-entry scratch on
- * first use.  Errors: RLU_EINVAL (sizes, null, misaligned or too small
- * workspace), RLU_ENOMEM (host), RLU_ECUDA. */
+ * own pool).  The handle's host words for the status read-back come from one
+ * process-wide page-locked slab (allocated on the first call, 4096 handles at
+ * a time).  The CSR entry point allocates its scratch on first use unless
+ * rlu_set_csr_workspace gave it caller memory.  Errors: RLU_EINVAL (sizes,
+ * null, misaligned or too small workspace), RLU_ENOMEM (host, or more than
+ * 4096 such handles alive), RLU_ECUDA. */
 int rlu_create_in(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t seed, void* workspace,
                   size_t workspace_bytes, void* stream, rlu_t* out);
+
+/* Device bytes of caller-owned CSR scratch for a handle of sizes m, n, k that
+ * will factor CSR inputs of at most max_nnz entries (the per-row lists, the
+ * column-major copy of the light entries, and the dense copy of at most
+ * min(m, max_nnz / ceil(n/4)) heavy rows with its tensor-core workspace).
+ * The library's own extension; the paper has no counterpart.
+ * Errors: RLU_EINVAL. */
+int rlu_csr_workspace_bytes(int64_t m, int64_t n, int32_t k, int64_t max_nnz, size_t* bytes);
+
+/* Give handle h caller-owned CSR scratch (device, 256-byte aligned, at least
+ * rlu_csr_workspace_bytes(h's m, n, k, max_nnz) bytes).  The handle then never
+ * allocates for rlu_factor_csr, and a later call with more than max_nnz
+ * entries returns RLU_EINVAL.  The memory stays the caller's: rlu_destroy does
+ * not free it, and it must outlive the handle's last factorization.  Must come
+ * before the handle's first CSR factorization.
+ * The library's own extension; the paper has no counterpart.
+ * Errors: RLU_EINVAL (null, misaligned, too small, or CSR scratch already
+ * allocated). */
+int rlu_set_csr_workspace(rlu_t h, int64_t max_nnz, void* workspace, size_t workspace_bytes);
 
 /* Select the arithmetic (rlu_prec).  Valid at any time between calls. */
 int rlu_set_precision(rlu_t h, int prec);
@@ -120,6 +142,34 @@ int rlu_factor_dense(rlu_t h, const void* A, int64_t lda, int dtype, void* L, vo
  * capture once the handle has run one factorization of the same dtype. */
 int rlu_factor_dense_async(rlu_t h, const void* A, int64_t lda, int dtype, void* L, void* U, int64_t* p,
                            int64_t* q, int32_t* status_dev, void* stream);
+
+/* Copy `rows` rows of `width_bytes` bytes from src (row pitch src_pitch
+ * bytes) to dst (row pitch dst_pitch bytes), asynchronously on `stream`;
+ * either side may be host (page-locked for an asynchronous copy) or device
+ * memory.  Used to bring a request's matrix, or a block of a larger one, into
+ * a caller-owned workspace before rlu_factor_dense.
+ * The library's own extension; the paper has no counterpart.
+ * Errors: RLU_EINVAL (null pointer, pitch below the width, negative size),
+ * RLU_ECUDA. */
+int rlu_copy_block_async(void* dst, int64_t dst_pitch, const void* src, int64_t src_pitch, int64_t width_bytes,
+                         int64_t rows, void* stream);
+
+/* Captured launch graphs (CUDA graphs) of one dense factorization.
+ * rlu_graph_capture_dense records, without running it, the whole path of
+ * rlu_factor_dense_async for these exact pointers on `stream` (not the legacy
+ * default stream) and instantiates it.  The handle must have run one
+ * factorization of the same dtype before (setup that allocates or reads back
+ * happens then), and timing and debug copies must be off.  Each
+ * rlu_graph_launch replays it on `stream`: the same A, L, U, p, q and status
+ * addresses, new contents.  The handle and every captured buffer must outlive
+ * the graph; one graph runs at a time per handle.
+ * The library's own extension; the paper has no counterpart.
+ * Errors: RLU_EINVAL, RLU_ENOMEM, RLU_ECUDA. */
+typedef struct rlu_graph* rlu_graph_t;
+int rlu_graph_capture_dense(rlu_t h, const void* A, int64_t lda, int dtype, void* L, void* U, int64_t* p,
+                            int64_t* q, int32_t* status_dev, void* stream, rlu_graph_t* out);
+int rlu_graph_launch(rlu_graph_t g, void* stream);
+int rlu_graph_destroy(rlu_graph_t g);
 
 /* Factor CSR A (m x n, nnz entries, nnz < 2^31).
  *   rowptr: device, m+1 int64, rowptr[0] = 0, non-decreasing, rowptr[m] = nnz.

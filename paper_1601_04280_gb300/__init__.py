@@ -27,7 +27,9 @@ PREC = {"f64": RLU_PREC_F64, "f32": RLU_PREC_F32, "bf16": RLU_PREC_BF16, "bf16_r
 C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_bytes", "rlu_factor_dense",
              "rlu_factor_dense_async", "rlu_factor_csr", "rlu_factor_dense_host", "rlu_destroy",
              "rlu_strerror", "rlu_debug_sketch_params", "rlu_debug_Y", "rlu_debug_B", "rlu_debug_enable",
-             "rlu_debug_timing", "rlu_debug_stage_ms", "rlu_debug_launch_count", "rlu_sketch_dense_noalloc")
+             "rlu_debug_timing", "rlu_debug_stage_ms", "rlu_debug_launch_count", "rlu_sketch_dense_noalloc",
+             "rlu_csr_workspace_bytes", "rlu_set_csr_workspace", "rlu_graph_capture_dense", "rlu_graph_launch",
+             "rlu_graph_destroy", "rlu_copy_block_async")
 
 #: stage names reported by rlu_debug_stage_ms, in order
 STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
@@ -70,6 +72,12 @@ def load(reload=False):
         "rlu_debug_stage_ms": ([vp, vp, c.c_int, c.POINTER(c.c_int)], c.c_int),
         "rlu_debug_launch_count": ([c.POINTER(i64)], c.c_int),
         "rlu_sketch_dense_noalloc": ([vp, i64, c.c_int, i64, i64, i32, i32, u64, vp, vp, vp], c.c_int),
+        "rlu_csr_workspace_bytes": ([i64, i64, i32, i64, c.POINTER(c.c_size_t)], c.c_int),
+        "rlu_set_csr_workspace": ([vp, i64, vp, c.c_size_t], c.c_int),
+        "rlu_graph_capture_dense": ([vp, vp, i64, c.c_int, vp, vp, vp, vp, vp, vp, c.POINTER(vp)], c.c_int),
+        "rlu_graph_launch": ([vp, vp], c.c_int),
+        "rlu_graph_destroy": ([vp], c.c_int),
+        "rlu_copy_block_async": ([vp, i64, vp, i64, i64, i64, vp], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -119,12 +127,42 @@ def rlu_workspace_bytes(m, n, k, l, l1, prec):
     return out.value
 
 
+def rlu_csr_workspace_bytes(m, n, k, max_nnz):
+    out = ctypes.c_size_t()
+    _check(load().rlu_csr_workspace_bytes(m, n, k, max_nnz, ctypes.byref(out)), "rlu_csr_workspace_bytes")
+    return out.value
+
+
+def rlu_set_csr_workspace(h, max_nnz, workspace_ptr, workspace_bytes):
+    return _check(load().rlu_set_csr_workspace(h, max_nnz, workspace_ptr, workspace_bytes), "rlu_set_csr_workspace")
+
+
 def rlu_factor_dense(h, A_ptr, lda, dtype, L_ptr, U_ptr, p_ptr, q_ptr, stream_ptr):
     return load().rlu_factor_dense(h, A_ptr, lda, dtype, L_ptr, U_ptr, p_ptr, q_ptr, stream_ptr)
 
 
 def rlu_factor_dense_async(h, A_ptr, lda, dtype, L_ptr, U_ptr, p_ptr, q_ptr, status_ptr, stream_ptr):
     return load().rlu_factor_dense_async(h, A_ptr, lda, dtype, L_ptr, U_ptr, p_ptr, q_ptr, status_ptr, stream_ptr)
+
+
+def rlu_graph_capture_dense(h, A_ptr, lda, dtype, L_ptr, U_ptr, p_ptr, q_ptr, status_ptr, stream_ptr):
+    g = ctypes.c_void_p()
+    _check(load().rlu_graph_capture_dense(h, A_ptr, lda, dtype, L_ptr, U_ptr, p_ptr, q_ptr, status_ptr, stream_ptr,
+                                          ctypes.byref(g)), "rlu_graph_capture_dense", allow_warn=False)
+    return g
+
+
+def rlu_copy_block_async(dst_ptr, dst_pitch, src_ptr, src_pitch, width_bytes, rows, stream_ptr):
+    return _check(load().rlu_copy_block_async(dst_ptr, dst_pitch, src_ptr, src_pitch, width_bytes, rows, stream_ptr),
+                  "rlu_copy_block_async", allow_warn=False)
+
+
+def rlu_graph_launch(g, stream_ptr):
+    return _check(load().rlu_graph_launch(g, stream_ptr), "rlu_graph_launch", allow_warn=False)
+
+
+def rlu_graph_destroy(g):
+    return load().rlu_graph_destroy(g)
 
 
 def rlu_factor_csr(h, rowptr_ptr, colind_ptr, val_ptr, nnz, dtype, L_ptr, U_ptr, p_ptr, q_ptr, stream_ptr):
@@ -187,6 +225,11 @@ class RandLU:
                                    workspace.numel() * workspace.element_size(), _stream_ptr(stream))
         self.prec = prec
         rlu_set_precision(self.h, prec)
+
+    def set_csr_workspace(self, workspace, max_nnz):
+        """Caller-owned CSR scratch (device uint8 tensor, >= rlu_csr_workspace_bytes)."""
+        rlu_set_csr_workspace(self.h, max_nnz, ctypes.c_void_p(workspace.data_ptr()),
+                              workspace.numel() * workspace.element_size())
 
     @property
     def out_dtype(self):

@@ -21,7 +21,43 @@ using namespace rlu;
 
 namespace rlu {
 static std::atomic<long long> g_launches{0};
-void note_launch(int count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;  // this thread's share (graph capture counts its own)
+void note_launch(int count) {
+  g_launches.fetch_add(count, std::memory_order_relaxed);
+  t_launches += count;
+}
+
+// Page-locked host words (status and CSR counts, 4 per handle) for handles
+// built on caller memory: one slab allocated on first use (never freed),
+// handed out from a free list.
+static std::mutex g_slab_mu;
+static unsigned int* g_slab = nullptr;
+static std::vector<unsigned int*> g_slab_free;
+constexpr int kSlabWords = 1 << 14;
+
+unsigned int* status_slab_take() {
+  std::lock_guard<std::mutex> lock(g_slab_mu);
+  if (!g_slab) {
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, sizeof(unsigned int) * kSlabWords, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_slab = (unsigned int*)p;
+    g_slab_free.reserve(kSlabWords);
+    for (int i = kSlabWords / 4 - 1; i >= 0; --i) g_slab_free.push_back(g_slab + 4 * i);
+  }
+  if (g_slab_free.empty()) return nullptr;
+  unsigned int* w = g_slab_free.back();
+  g_slab_free.pop_back();
+  w[0] = w[1] = w[2] = w[3] = 0;
+  return w;
+}
+
+void status_slab_give(unsigned int* w) {
+  std::lock_guard<std::mutex> lock(g_slab_mu);
+  g_slab_free.push_back(w);
+}
 
 static std::mutex g_coop_mu;
 static cudaEvent_t g_coop_evt[64] = {};
@@ -45,7 +81,30 @@ cudaError_t launch_cooperative(const void* func, dim3 grid, dim3 block, void** a
   g_coop_any[dev] = true;
   return cudaSuccess;
 }
+
+// Launch a captured factorization as one unit of the same chain: it waits for
+// the last cooperative kernel of any stream, and later ones wait for it.
+cudaError_t launch_graph_chained(cudaGraphExec_t ge, cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_coop_mu);
+  if (!g_coop_evt[dev]) {
+    cudaError_t e = cudaEventCreateWithFlags(&g_coop_evt[dev], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e;
+  if (g_coop_any[dev] && (e = cudaStreamWaitEvent(st, g_coop_evt[dev], 0)) != cudaSuccess) return e;
+  if ((e = cudaGraphLaunch(ge, st)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(g_coop_evt[dev], st)) != cudaSuccess) return e;
+  g_coop_any[dev] = true;
+  return cudaSuccess;
+}
 }  // namespace rlu
+
+struct rlu_graph {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;  // kernels one launch of the graph runs
+};
 
 // Stages whose device time the timing hook reports, in order.
 static const int kNumStages = 9;
@@ -76,8 +135,11 @@ struct rlu_ctx {
   TcWs tcw{};
   unsigned int* status_dev = nullptr;
   unsigned int* bar2 = nullptr;
-  unsigned int* status_host = nullptr;  // pinned when status_pinned, else ordinary host memory
+  // 4 page-locked host words: status (0) and the CSR row counts (2, 3); own
+  // allocation when status_pinned, else a piece of the shared slab
+  unsigned int* status_host = nullptr;
   bool status_pinned = false;
+  bool status_slab = false;
   int debug = 0;
   double* Ydbg = nullptr;
   void* Bdbg = nullptr;
@@ -96,6 +158,7 @@ struct rlu_ctx {
   void* csr_nnz_buf = nullptr;
   void* csr_heavy_buf = nullptr;
   void* csr_rows_buf = nullptr;
+  bool csr_external = false;  // CSR scratch owned by the caller (rlu_set_csr_workspace)
   // per-stage device timing (test hook)
   int timing = 0;
   cudaEvent_t ev[kNumStages + 1] = {};
@@ -198,9 +261,14 @@ bool prec_dtype_ok(int prec, int dtype) {
   }
 }
 
-int csr_rows_alloc(rlu_ctx* h) {
-  if (h->csr_rows_ready) return RLU_OK;
-  const int64_t m = h->m, n = h->n;
+// CSR scratch: three blocks (per row, per entry, per heavy row).  Heavy rows
+// hold at least ceil(n/4) entries each, so nnz bounds their number.
+struct CsrLayout {
+  size_t rows, entries, heavy;
+  int64_t heavy_cap;
+};
+
+Sizes csr_rows_sizes(int64_t m, int64_t n, int k) {
   Sizes sz;
   for (int i = 0; i < 4; ++i) sz.add(sizeof(int32_t) * (m + 1));  // hflag, lflag, hpos, lpos
   sz.add(sizeof(int32_t) * m);                                     // heavy
@@ -208,10 +276,36 @@ int csr_rows_alloc(rlu_ctx* h) {
   sz.add(sizeof(int32_t) * 2);                                     // count
   sz.add(sizeof(int32_t) * (n + 1));                               // ccnt
   sz.add(sizeof(int32_t) * (n + 1));                               // cstart
-  sz.add((size_t)8 * m * h->k);                                    // W^T
-  char* b = nullptr;
-  if (cudaMalloc(&b, sz.total) != cudaSuccess) { cudaGetLastError(); return RLU_ENOMEM; }
-  h->csr_rows_buf = b;
+  sz.add((size_t)8 * m * k);                                       // W^T
+  return sz;
+}
+
+size_t csr_entry_bytes(int64_t nnz) {
+  const size_t rb = ((sizeof(int32_t) * (size_t)max64(nnz, 1)) + 255) & ~(size_t)255;
+  return rb + (((size_t)8 * max64(nnz, 1) + 255) & ~(size_t)255);
+}
+
+size_t csr_heavy_bytes(int64_t nheavy, int64_t n, int k, int num_sms, size_t* dbytes, size_t* wbytes) {
+  const int64_t nh = max64(nheavy, 1);
+  const size_t d = (((size_t)8 * nh * n) + 1023) & ~(size_t)1023;
+  const size_t w = (((size_t)8 * k * nh) + 1023) & ~(size_t)1023;
+  if (dbytes) *dbytes = d;
+  if (wbytes) *wbytes = w;
+  return d + w + tc_workspace_bytes(nh, n, k, num_sms);
+}
+
+CsrLayout csr_layout(int64_t m, int64_t n, int k, int64_t nnz, int num_sms) {
+  CsrLayout c;
+  c.rows = (csr_rows_sizes(m, n, k).total + 255) & ~(size_t)255;
+  c.entries = csr_entry_bytes(nnz);
+  const int64_t per = (n + 3) / 4;
+  c.heavy_cap = min64(m, max64(nnz, 0) / max64(per, 1));
+  c.heavy = (csr_heavy_bytes(c.heavy_cap, n, k, num_sms, nullptr, nullptr) + 255) & ~(size_t)255;
+  return c;
+}
+
+void csr_carve_rows(rlu_ctx* h, char* b) {
+  Sizes sz = csr_rows_sizes(h->m, h->n, h->k);
   size_t off = 0;
   int idx = 0;
   auto next = [&]() -> void* { void* p = b + off; off += sz.parts[idx++]; return p; };
@@ -219,41 +313,58 @@ int csr_rows_alloc(rlu_ctx* h) {
   w.hflag = (int32_t*)next(); w.lflag = (int32_t*)next(); w.hpos = (int32_t*)next(); w.lpos = (int32_t*)next();
   w.heavy = (int32_t*)next(); w.light = (int32_t*)next(); w.count = (int32_t*)next();
   w.ccnt = (int32_t*)next(); w.cstart = (int32_t*)next(); w.Wt = next();
+}
+
+void csr_carve_entries(rlu_ctx* h, char* b, int64_t nnz) {
+  const size_t rb = ((sizeof(int32_t) * (size_t)max64(nnz, 1)) + 255) & ~(size_t)255;
+  h->csr.crow = (int32_t*)b;
+  h->csr.cval = b + rb;
+}
+
+int csr_rows_alloc(rlu_ctx* h) {
+  if (h->csr_rows_ready) return RLU_OK;
+  char* b = nullptr;
+  if (cudaMalloc(&b, csr_rows_sizes(h->m, h->n, h->k).total) != cudaSuccess) {
+    cudaGetLastError();
+    return RLU_ENOMEM;
+  }
+  h->csr_rows_buf = b;
+  csr_carve_rows(h, b);
   h->csr_rows_ready = true;
   return RLU_OK;
 }
 
 int csr_grow(rlu_ctx* h, int64_t nnz, int64_t nheavy) {
+  if (h->csr_external) {  // caller-owned scratch, sized for csr_cap_nnz entries
+    if (nnz > h->csr_cap_nnz || nheavy > h->csr_cap_heavy) return RLU_EINVAL;
+  }
   if (nnz > h->csr_cap_nnz) {
     if (h->csr_nnz_buf) cudaFree(h->csr_nnz_buf);
     h->csr_nnz_buf = nullptr;
     h->csr_cap_nnz = -1;
-    const size_t rb = ((sizeof(int32_t) * (size_t)max64(nnz, 1)) + 255) & ~(size_t)255;
     char* b = nullptr;
-    if (cudaMalloc(&b, rb + (size_t)8 * max64(nnz, 1)) != cudaSuccess) { cudaGetLastError(); return RLU_ENOMEM; }
+    if (cudaMalloc(&b, csr_entry_bytes(nnz)) != cudaSuccess) { cudaGetLastError(); return RLU_ENOMEM; }
     h->csr_nnz_buf = b;
-    h->csr.crow = (int32_t*)b;
-    h->csr.cval = b + rb;
+    csr_carve_entries(h, b, nnz);
     h->csr_cap_nnz = nnz;
   }
   if (nheavy > h->csr_cap_heavy) {
     if (h->csr_heavy_buf) cudaFree(h->csr_heavy_buf);
     h->csr_heavy_buf = nullptr;
     h->csr_cap_heavy = -1;
-    const int64_t nh = max64(nheavy, 1);
-    const size_t dbytes = (((size_t)8 * nh * h->n) + 1023) & ~(size_t)1023;
-    const size_t wbytes = (((size_t)8 * h->k * nh) + 1023) & ~(size_t)1023;
-    const size_t tbytes = tc_workspace_bytes(nh, h->n, h->k, h->num_sms);
     char* b = nullptr;
-    if (cudaMalloc(&b, dbytes + wbytes + tbytes) != cudaSuccess) { cudaGetLastError(); return RLU_ENOMEM; }
+    if (cudaMalloc(&b, csr_heavy_bytes(nheavy, h->n, h->k, h->num_sms, nullptr, nullptr)) != cudaSuccess) {
+      cudaGetLastError();
+      return RLU_ENOMEM;
+    }
     h->csr_heavy_buf = b;
-    h->csr.D = b;
-    h->csr.Wh = b + dbytes;
     h->csr_cap_heavy = nheavy;
   }
   if (nheavy > 0) {
-    const size_t dbytes = (((size_t)8 * max64(h->csr_cap_heavy, 1) * h->n) + 1023) & ~(size_t)1023;
-    const size_t wbytes = (((size_t)8 * h->k * max64(h->csr_cap_heavy, 1)) + 1023) & ~(size_t)1023;
+    size_t dbytes = 0, wbytes = 0;
+    csr_heavy_bytes(h->csr_cap_heavy, h->n, h->k, h->num_sms, &dbytes, &wbytes);
+    h->csr.D = h->csr_heavy_buf;
+    h->csr.Wh = (char*)h->csr_heavy_buf + dbytes;
     int rc = tc_setup(h->csr.tc, (char*)h->csr_heavy_buf + dbytes + wbytes, nheavy, h->n, h->k, h->num_sms);
     if (rc) return rc;
   }
@@ -355,7 +466,9 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   h->sk.nchunks = cdiv(n, h->sk.chunk);
   if ((rc = launch_sketch_params(h->sk, n, l1, l, h->seed, st))) return rc;
   CsrRows cr{};
-  if ((rc = csr_classify(h->csr, rowptr, m, n, nnz, h->status_dev, cr, st))) return rc;
+  if ((rc = csr_classify(h->csr, rowptr, m, n, nnz, h->status_dev, cr, reinterpret_cast<int32_t*>(h->status_host + 2),
+                         st)))
+    return rc;
   if ((rc = csr_grow(h, nnz, cr.n_heavy))) return rc;
   if ((rc = mark(h, 1, st))) return rc;
   RLU_CUDA_TRY(cudaMemsetAsync(h->Y, 0, sizeof(double) * m * l, st));
@@ -440,9 +553,38 @@ int rlu_workspace_bytes(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, 
   return RLU_OK;
 }
 
+int rlu_csr_workspace_bytes(int64_t m, int64_t n, int32_t k, int64_t max_nnz, size_t* bytes) {
+  if (!bytes || m < 1 || n < 1 || k < 1 || max_nnz < 0 || max_nnz >= (1ll << 31)) return RLU_EINVAL;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const CsrLayout c = csr_layout(m, n, k, max_nnz, sms);
+  *bytes = c.rows + c.entries + c.heavy;
+  return RLU_OK;
+}
+
+int rlu_set_csr_workspace(rlu_t h, int64_t max_nnz, void* workspace, size_t workspace_bytes) {
+  if (!h || !workspace || max_nnz < 0 || max_nnz >= (1ll << 31) || ((uintptr_t)workspace % 256) != 0)
+    return RLU_EINVAL;
+  if (h->csr_rows_buf || h->csr_nnz_buf || h->csr_heavy_buf) return RLU_EINVAL;  // already has its own
+  const CsrLayout c = csr_layout(h->m, h->n, h->k, max_nnz, h->num_sms);
+  if (workspace_bytes < c.rows + c.entries + c.heavy) return RLU_EINVAL;
+  char* b = (char*)workspace;
+  h->csr_external = true;
+  h->csr_rows_buf = b;
+  csr_carve_rows(h, b);
+  h->csr_rows_ready = true;
+  h->csr_nnz_buf = b + c.rows;
+  csr_carve_entries(h, b + c.rows, max_nnz);
+  h->csr_cap_nnz = max_nnz;
+  h->csr_heavy_buf = b + c.rows + c.entries;
+  h->csr_cap_heavy = c.heavy_cap;
+  return RLU_OK;
+}
+
 // Build a handle on workspace `base` (plan_sizes(...).total bytes).  With
 // own_base the handle frees it; the caller's stream receives the twiddle
-// launch.  `pinned` chooses page-locked memory for the status read-back.
+// launch.  `pinned` gives the handle its own page-locked host words for the
+// status read-back; otherwise it takes them from the shared slab.
 static int create_common(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64_t seed, char* base,
                          bool own_base, bool pinned, cudaStream_t st, rlu_t* out) {
   int dev = 0;
@@ -497,18 +639,21 @@ static int create_common(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1,
     return RLU_ECUDA;
   }
   if (pinned) {
-    if (cudaMallocHost(&h->status_host, sizeof(unsigned int)) != cudaSuccess) {
+    if (cudaMallocHost(&h->status_host, 4 * sizeof(unsigned int)) != cudaSuccess) {
       cudaGetLastError();
       rlu_destroy(h);
       return RLU_ENOMEM;
     }
     h->status_pinned = true;
   } else {
-    h->status_host = new (std::nothrow) unsigned int(0);
+    // a word of a shared page-locked slab: the status read-back stays a plain
+    // DMA (a copy to pageable memory needs the calling thread's participation)
+    h->status_host = status_slab_take();
     if (!h->status_host) {
       rlu_destroy(h);
       return RLU_ENOMEM;
     }
+    h->status_slab = true;
   }
   if (launch_twiddles(l1, h->sk.tw64, h->sk.tw32, st) != RLU_OK) {
     rlu_destroy(h);
@@ -568,7 +713,7 @@ int rlu_destroy(rlu_t h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->status_host) {
     if (h->status_pinned) cudaFreeHost(h->status_host);
-    else delete h->status_host;
+    else if (h->status_slab) status_slab_give(h->status_host);
   }
   if (h->Ydbg) cudaFree(h->Ydbg);
   if (h->Bdbg) cudaFree(h->Bdbg);
@@ -577,9 +722,11 @@ int rlu_destroy(rlu_t h) {
   if (h->U_stage) cudaFree(h->U_stage);
   if (h->p_stage) cudaFree(h->p_stage);
   if (h->q_stage) cudaFree(h->q_stage);
-  if (h->csr_rows_buf) cudaFree(h->csr_rows_buf);
-  if (h->csr_nnz_buf) cudaFree(h->csr_nnz_buf);
-  if (h->csr_heavy_buf) cudaFree(h->csr_heavy_buf);
+  if (!h->csr_external) {
+    if (h->csr_rows_buf) cudaFree(h->csr_rows_buf);
+    if (h->csr_nnz_buf) cudaFree(h->csr_nnz_buf);
+    if (h->csr_heavy_buf) cudaFree(h->csr_heavy_buf);
+  }
   for (int i = 0; i <= kNumStages; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   delete h;
@@ -609,12 +756,81 @@ int rlu_factor_dense(rlu_t h, const void* A, int64_t lda, int dtype, void* L, vo
   return finish_sync(h, st);
 }
 
+int rlu_graph_capture_dense(rlu_t h, const void* A, int64_t lda, int dtype, void* L, void* U, int64_t* p,
+                            int64_t* q, int32_t* status_dev, void* stream, rlu_graph_t* out) {
+  if (!out) return RLU_EINVAL;
+  *out = nullptr;
+  if (!h || !A || !L || !U || !p || !q || !status_dev || !stream) return RLU_EINVAL;
+  if (lda < h->n || !prec_dtype_ok(h->prec, dtype) || h->timing || h->debug) return RLU_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  RLU_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const long long before = rlu::t_launches;
+  int rc = enqueue_dense(h, A, lda, dtype, L, U, p, q, st);
+  if (!rc) {
+    k_status_code<<<1, 1, 0, st>>>(h->status_dev, status_dev);
+    if (cudaGetLastError() != cudaSuccess) rc = RLU_ECUDA;
+    rlu::note_launch();
+  }
+  // captured launches do not run now; the count moves to each graph launch
+  const long long captured = rlu::t_launches - before;
+  rlu::g_launches.fetch_sub(captured);
+  rlu::t_launches -= captured;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc ? rc : RLU_ECUDA;
+  }
+  cudaGraphExec_t ge = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    return RLU_ECUDA;
+  }
+  rlu_graph* gr = new (std::nothrow) rlu_graph();
+  if (!gr) {
+    cudaGraphExecDestroy(ge);
+    return RLU_ENOMEM;
+  }
+  gr->exec = ge;
+  gr->kernels = captured;
+  *out = gr;
+  return RLU_OK;
+}
+
+int rlu_copy_block_async(void* dst, int64_t dst_pitch, const void* src, int64_t src_pitch, int64_t width_bytes,
+                         int64_t rows, void* stream) {
+  if (rows < 0 || width_bytes < 0) return RLU_EINVAL;
+  if (rows == 0 || width_bytes == 0) return RLU_OK;
+  if (!dst || !src || dst_pitch < width_bytes || src_pitch < width_bytes) return RLU_EINVAL;
+  RLU_CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)dst_pitch, src, (size_t)src_pitch, (size_t)width_bytes, (size_t)rows,
+                                 cudaMemcpyDefault, (cudaStream_t)stream));
+  return RLU_OK;
+}
+
+int rlu_graph_launch(rlu_graph_t g, void* stream) {
+  if (!g || !g->exec) return RLU_EINVAL;
+  RLU_CUDA_TRY(launch_graph_chained(g->exec, (cudaStream_t)stream));
+  note_launch((int)g->kernels);
+  return RLU_OK;
+}
+
+int rlu_graph_destroy(rlu_graph_t g) {
+  if (!g) return RLU_OK;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  delete g;
+  return RLU_OK;
+}
+
 int rlu_factor_csr(rlu_t h, const int64_t* rowptr, const int32_t* colind, const void* val, int64_t nnz, int dtype,
                    void* L, void* U, int64_t* p, int64_t* q, void* stream) {
   if (!h || !rowptr || !L || !U || !p || !q || nnz < 0 || nnz >= (1ll << 31)) return RLU_EINVAL;
   if (nnz > 0 && (!colind || !val)) return RLU_EINVAL;
   if (!((dtype == RLU_F64 && h->prec == RLU_PREC_F64) || (dtype == RLU_F32 && h->prec == RLU_PREC_F32)))
     return RLU_EINVAL;
+  if (h->csr_external && nnz > h->csr_cap_nnz) return RLU_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   int rc = enqueue_csr(h, rowptr, colind, val, nnz, dtype, L, U, p, q, st);
   if (rc) return rc;

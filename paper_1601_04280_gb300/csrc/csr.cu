@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) k_spmm_csc(int64_t n, int k, const int32_
 
 // ---- host side -----------------------------------------------------------------
 int csr_classify(CsrWs& w, const int64_t* rowptr, int64_t m, int64_t n, int64_t nnz, unsigned int* status,
-                 CsrRows& cr, cudaStream_t st) {
+                 CsrRows& cr, int32_t* cnt, cudaStream_t st) {
   const unsigned g = (unsigned)cdiv(m, 256);
   k_csr_classify<<<g, 256, 0, st>>>(m, n, nnz, rowptr, w.hflag, w.lflag, status);
   RLU_CUDA_TRY(cudaGetLastError());
@@ -228,8 +228,7 @@ int csr_classify(CsrWs& w, const int64_t* rowptr, int64_t m, int64_t n, int64_t 
   k_csr_lists<<<g, 256, 0, st>>>(m, w.hflag, w.lflag, w.hpos, w.lpos, w.heavy, w.light, w.count);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
-  int32_t cnt[2];
-  RLU_CUDA_TRY(cudaMemcpyAsync(cnt, w.count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+  RLU_CUDA_TRY(cudaMemcpyAsync(cnt, w.count, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   RLU_CUDA_TRY(cudaStreamSynchronize(st));
   cr.light = w.light;
   cr.heavy = w.heavy;

@@ -18,8 +18,10 @@ struct CsrWs {
   TcWs tc;   // tensor-core product of W_h and D
 };
 
+// Row classification; reads the two row counts back through `cnt` (two
+// int32 of page-locked host memory).
 int csr_classify(CsrWs& w, const int64_t* rowptr, int64_t m, int64_t n, int64_t nnz, unsigned int* status,
-                 CsrRows& cr, cudaStream_t st);
+                 CsrRows& cr, int32_t* cnt, cudaStream_t st);
 int csr_bgemm(CsrWs& w, const int64_t* rowptr, const int32_t* colind, const void* val, int dtype, int prec,
               int64_t m, int64_t n, int k, const CsrRows& cr, const void* W, void* B, unsigned int* status,
               int num_sms, cudaStream_t st);
