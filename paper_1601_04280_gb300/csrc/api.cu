@@ -82,6 +82,18 @@ cudaError_t launch_cooperative(const void* func, dim3 grid, dim3 block, void** a
   return cudaSuccess;
 }
 
+int allow_dynamic_smem(const void* kern, size_t smem) {
+  int dev = 0, optin = 0;
+  RLU_CUDA_TRY(cudaGetDevice(&dev));
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  RLU_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+  const int64_t lim = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
+  if ((int64_t)smem > lim) return RLU_EINVAL;
+  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+  return RLU_OK;
+}
+
 // Launch a captured factorization as one unit of the same chain: it waits for
 // the last cooperative kernel of any stream, and later ones wait for it.
 cudaError_t launch_graph_chained(cudaGraphExec_t ge, cudaStream_t st) {
@@ -520,6 +532,15 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   return RLU_OK;
 }
 
+// After a failed enqueue: wait for whatever was already enqueued (not while
+// capturing), so no work of the call outlives it, and return `rc`.
+int drain_after(int rc, cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) cudaStreamSynchronize(st);
+  cudaGetLastError();
+  return rc;
+}
+
 int finish_sync(rlu_ctx* h, cudaStream_t st) {
   RLU_CUDA_TRY(cudaMemcpyAsync(h->status_host, h->status_dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   RLU_CUDA_TRY(cudaStreamSynchronize(st));
@@ -739,7 +760,7 @@ int rlu_factor_dense_async(rlu_t h, const void* A, int64_t lda, int dtype, void*
   if (lda < h->n || !prec_dtype_ok(h->prec, dtype)) return RLU_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   int rc = enqueue_dense(h, A, lda, dtype, L, U, p, q, st);
-  if (rc) return rc;
+  if (rc) return drain_after(rc, st);
   k_status_code<<<1, 1, 0, st>>>(h->status_dev, status_dev);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
@@ -752,7 +773,7 @@ int rlu_factor_dense(rlu_t h, const void* A, int64_t lda, int dtype, void* L, vo
   if (lda < h->n || !prec_dtype_ok(h->prec, dtype)) return RLU_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   int rc = enqueue_dense(h, A, lda, dtype, L, U, p, q, st);
-  if (rc) return rc;
+  if (rc) return drain_after(rc, st);
   return finish_sync(h, st);
 }
 
@@ -833,7 +854,7 @@ int rlu_factor_csr(rlu_t h, const int64_t* rowptr, const int32_t* colind, const 
   if (h->csr_external && nnz > h->csr_cap_nnz) return RLU_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   int rc = enqueue_csr(h, rowptr, colind, val, nnz, dtype, L, U, p, q, st);
-  if (rc) return rc;
+  if (rc) return drain_after(rc, st);
   return finish_sync(h, st);
 }
 
@@ -863,7 +884,7 @@ int rlu_factor_dense_host(rlu_t h, const void* A_host, int dtype, void* L_host, 
   cudaStream_t st = (cudaStream_t)stream;
   RLU_CUDA_TRY(cudaMemcpyAsync(h->A_stage, A_host, abytes, cudaMemcpyHostToDevice, st));
   int rc = enqueue_dense(h, h->A_stage, h->n, dtype, h->L_stage, h->U_stage, h->p_stage, h->q_stage, st);
-  if (rc) return rc;
+  if (rc) return drain_after(rc, st);
   RLU_CUDA_TRY(cudaMemcpyAsync(L_host, h->L_stage, os * h->m * h->k, cudaMemcpyDeviceToHost, st));
   RLU_CUDA_TRY(cudaMemcpyAsync(U_host, h->U_stage, os * h->k * h->n, cudaMemcpyDeviceToHost, st));
   RLU_CUDA_TRY(cudaMemcpyAsync(p_host, h->p_stage, 8 * h->m, cudaMemcpyDeviceToHost, st));

@@ -14,20 +14,20 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+static EncodeTiledFn resolve_encode_fn() {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    return (EncodeTiledFn)p;
+  cudaGetLastError();
+  return nullptr;
+}
+
+// Resolved once (a function-local static: initialised exactly once even when
+// several threads build handles at the same time).
 static EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-    else
-      cudaGetLastError();
-  }
+  static const EncodeTiledFn fn = resolve_encode_fn();
   return fn;
 }
 
@@ -99,7 +99,7 @@ static int launch_cfg(const TcWs& w, int wplanes, const TA* A, int64_t lda, int6
   const TcPlan& p = w.plan;
   const size_t smem = tc::smem_bytes(P, wplanes, p.npad);
   auto kern = tc::k_bgemm_tc<TA>;
-  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
   dim3 grid((unsigned)cdiv(n, tc::kBM), (unsigned)p.splits, (unsigned)p.nz);
   const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(w.map);
   kern<<<grid, tc::kThreads, smem, st>>>(maps[0], maps[1], maps[2], wplanes, A, lda, m, n, k, p.npad, p.kps, w.part,

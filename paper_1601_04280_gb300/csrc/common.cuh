@@ -248,6 +248,12 @@ void note_launch(int count = 1);
 // once and waiting on each other; all other kernels still overlap freely.
 cudaError_t launch_cooperative(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st);
 
+// Lift a kernel's dynamic shared-memory limit to the most the device allows
+// beside its static shared memory.  Every call sets the same value, so a
+// launch on one thread never finds the limit lowered by another thread that
+// launches the same kernel with less.  RLU_EINVAL when `smem` is above it.
+int allow_dynamic_smem(const void* kern, size_t smem);
+
 __host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
@@ -257,5 +263,8 @@ __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return
 #define RLU_CUDA_TRY(expr)                         \
   do {                                             \
     cudaError_t _e = (expr);                       \
-    if (_e != cudaSuccess) return RLU_ECUDA;       \
+    if (_e != cudaSuccess) {                       \
+      cudaGetLastError();                          \
+      return RLU_ECUDA;                            \
+    }                                              \
   } while (0)

@@ -310,7 +310,7 @@ static int launch_cfg(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int 
   const int64_t rpc = cdiv(rows, G);
   size_t smem = pivlu_smem<T, SMEM>(rpc, cols, steps);
   auto kern = k_pivoted_lu<T, SMEM, NT>;
-  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
   int per_sm = 0;
   RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
   if (per_sm < 1) return RLU_EINVAL;

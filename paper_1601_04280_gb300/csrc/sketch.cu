@@ -877,7 +877,7 @@ static int launch_csr_cfg(const int64_t* rowptr, const int32_t* colind, const TV
     int pb = (int)((budget - fixed) / per_pair);
     if (pb > kCsrWarps / 2) pb = kCsrWarps / 2;
     const size_t smem = fixed + (size_t)pb * per_pair;
-    RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
     const int64_t groups = cdiv(cr.n_light, kCsrWarps);
     const unsigned grid = (unsigned)min64(groups, (int64_t)num_sms);
     kern<<<grid, kCsrWarps * 32, smem, st>>>(rowptr, colind, val, n, cr.light, cr.d_count, l1, l, ws.hs, ws.dsign,
@@ -889,7 +889,7 @@ static int launch_csr_cfg(const int64_t* rowptr, const int32_t* colind, const TV
     auto kern = k_sketch_csr_heavy<TV, TACC>;
     const size_t smem = (size_t)3 * l1 * sizeof(V) + (size_t)(2 + kCsrWarps) * l1 * sizeof(TACC);
     if (smem > budget) return RLU_EINVAL;
-    RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
     const int64_t pairs = cdiv(cr.n_heavy, 2);
     const unsigned grid = (unsigned)min64(pairs, (int64_t)num_sms);
     kern<<<grid, kCsrWarps * 32, smem, st>>>(rowptr, colind, val, n, cr.heavy, cr.d_count + 1, l1, l, ws.hs,
@@ -987,7 +987,7 @@ static int launch_dense_tma_cfg(const void* A, int64_t lda, int64_t m, int64_t n
   }
   if (pb > R / 2) pb = R / 2;
   const size_t smem = fixed + (size_t)pb * per_pair + (lists_in_smem ? lists : 0);
-  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
   int per_sm = 0;
   RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
   if (per_sm < 1) return RLU_EINVAL;
@@ -1017,7 +1017,7 @@ static int launch_dense_cfg(const void* A, int64_t lda, int64_t m, int64_t n, in
   size_t tile_bytes = (size_t)R * ws.chunk * sizeof(TA);
   size_t fft_bytes = (size_t)2 * l1 * sizeof(typename C2<TACC>::t);
   size_t smem = tile_bytes > fft_bytes ? tile_bytes : fft_bytes;
-  RLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
   int per_sm = 0;
   RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
   if (per_sm < 1) return RLU_EINVAL;
