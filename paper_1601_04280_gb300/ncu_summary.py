@@ -27,7 +27,8 @@ def main(path, title):
     print("# %s\n" % title)
     print("Per-kernel device time of this library's kernels over the whole command (%d factorizations: warm-up,"
           % nfact)
-    print("timed steps, stage-timing and e2e repetitions). ncu serializes launches and runs them cold: compare the")
+    print("timed steps, graph replays, stage-timing and e2e repetitions). ncu serializes launches and runs them")
+    print("cold: compare the")
     print("SHARES with bench.py's live `stage_ms`, not the absolute times.\n")
     print("| kernel | launches | total ms | mean us/launch | share |")
     print("|---|---|---|---|---|")
