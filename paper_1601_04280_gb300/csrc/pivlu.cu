@@ -53,6 +53,13 @@ __device__ __forceinline__ bool cand_better(unsigned long long ka, int pa, unsig
 
 template <typename T> __device__ __forceinline__ T recip(T x) { return one_<T>() / x; }
 
+// Load through L2 only (values written by other CTAs in this launch).
+template <typename T> __device__ __forceinline__ T ldcg_(const T* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ df32 ldcg_<df32>(const df32* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return df_make(v.x, v.y);
+}
+
 template <typename T>
 __device__ __forceinline__ T& xref(T* X, int64_t rs, int64_t cs, int64_t i, int c) {
   return X[i * rs + (int64_t)c * cs];
@@ -73,16 +80,18 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
   const int rp = (int)rpc;
   // shared layout
   T* slab = reinterpret_cast<T*>(smem);                               // nr x cols (SMEM variant)
-  T* urow = slab + (SMEM ? (size_t)rp * cols : 0);                    // cols
-  T* lval = urow + cols;                                              // rpc
+  T* urow2 = slab + (SMEM ? (size_t)rp * cols : 0);                   // 2 x cols: pivot rows, by step parity
+  T* lval = urow2 + 2 * (size_t)cols;                                 // rpc
   int32_t* lpos = reinterpret_cast<int32_t*>(lval + rp);              // rpc
   int32_t* lstep = lpos + rp;                                         // rpc
   int32_t* pwin = lstep + rp;                                         // steps
   __shared__ unsigned long long red_v[NW];
   __shared__ int red_p[NW];
   __shared__ int red_r[NW];
-  __shared__ int s_zero, s_cand;
-  __shared__ int s_wrow, s_wpos, s_wcta;
+  __shared__ int s_zero, s_stop, s_rstar;
+  __shared__ unsigned long long s_ckey;
+  __shared__ int s_cpos;
+  __shared__ T s_rpiv;
 
   const bool row_fast = (cs == 1) ? false : true;  // B^T: consecutive rows are contiguous in memory
   auto at = [&](int r, int c) -> T& {
@@ -105,179 +114,255 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
     lstep[r] = -1;
   }
   for (int t = tid; t < steps; t += NT) pwin[t] = t;
+  if (tid == 0) s_stop = 0;
   __syncthreads();
 
-  // Publish this CTA's best candidate for column jc (rows not yet pivoted):
-  // its |value|, current position and row, and the row's values jc..cols-1.
-  auto publish = [&](int jc) {
-    unsigned long long bv = 0ull;
-    int bp = 0x7fffffff, br = -1;
-    for (int r = tid; r < nr; r += NT) {
-      if (lstep[r] < 0) {
-        const unsigned long long v = mag_key(at(r, jc));
-        const int p = lpos[r];
-        if (cand_better(v, p, bv, bp)) { bv = v; bp = p; br = r; }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      unsigned long long ov = __shfl_down_sync(0xffffffffu, bv, o);
-      int op = __shfl_down_sync(0xffffffffu, bp, o);
-      int orr = __shfl_down_sync(0xffffffffu, br, o);
-      if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; br = orr; }
-    }
-    if (lane == 0) { red_v[warp] = bv; red_p[warp] = bp; red_r[warp] = br; }
-    __syncthreads();
-    if (tid == 0) {
-      for (int w = 1; w < NW; ++w)
-        if (cand_better(red_v[w], red_p[w], bv, bp)) { bv = red_v[w]; bp = red_p[w]; br = red_r[w]; }
-      s_cand = br;
-    }
-    __syncthreads();
-    return s_cand;  // local row, or -1
-  };
-  auto write_cand = [&](int jc, int lr) {
-    if (tid == 0) {
-      Cand cd;
-      cd.key = lr >= 0 ? mag_key(at(lr, jc)) : 0ull;
-      cd.pos = lr >= 0 ? lpos[lr] : 0x7fffffff;
-      cd.row = lr < 0 ? -1 : (int)(r0 + lr);
-      cand[(jc & 1) * G + blockIdx.x] = cd;
-    }
-    T* dst = candrow + ((size_t)(jc & 1) * G + blockIdx.x) * cols;
-    if (lr >= 0)
-      for (int c = jc + tid; c < cols; c += NT) dst[c - jc] = at(lr, c);
-  };
+  // Warp 0 is the control warp: it waits for the grid's candidates of step j,
+  // picks the winner, fetches the pivot row and keeps the permutation.  Warps
+  // 1.. are the workers: they scale column j, bring column j+1 and the next
+  // candidate row up to date, publish that candidate, and then apply the rest
+  // of step j's rank-1 update while the control warp already waits for step
+  // j+1.  Named barriers: 1 = pivot row of step j ready (control -> workers),
+  // 2 = candidate of step j+1 ready (workers -> control), 3 = workers only.
+  constexpr int NTW = NT - 32;
+  constexpr int NWK = NW - 1;
+  auto bar_sync = [](int id, int cnt) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(cnt) : "memory"); };
+  auto bar_arrive = [](int id, int cnt) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(cnt) : "memory"); };
 
-  // step 0 candidate
-  {
-    const int lr = publish(0);
-    write_cand(0, lr);
-    grid_arrive(bar);
-  }
-  for (int j = 0; j < steps; ++j) {
-    // 1. wait for every CTA's candidate of step j
-    if (!grid_wait(bar, (unsigned)(j + 1), status)) return;
-    // 2. every CTA picks the same winner (warp 0 scans the G candidates)
-    if (warp == 0) {
+  if (warp == 0) {
+    // ------------------------------------------------------------ control warp
+    const Cand* cands = cand;
+    for (int j = 0; j <= steps; ++j) {
+      // publish the candidate for step j (prepared by the workers)
+      if (j < steps) {
+        bar_sync(2, NT);
+        __syncwarp();
+        if (lane == 0) {
+          Cand cd;
+          cd.key = s_ckey;
+          cd.pos = s_cpos;
+          cd.row = s_rstar < 0 ? -1 : (int)(r0 + s_rstar);
+          if (s_rstar < 0) { cd.key = 0ull; cd.pos = 0x7fffffff; }
+          cand[(j & 1) * G + blockIdx.x] = cd;
+          __threadfence();
+          red_release_gpu_add(bar, 1u);
+        }
+      }
+      if (j == steps) break;
+      // wait for every CTA's candidate of step j (bounded)
+      int ok = 1;
+      if (lane == 0) {
+        const unsigned int target = (unsigned)(j + 1) * (unsigned)G;
+        const long long t0 = clock64();
+        while (true) {
+          const unsigned int v = ld_acquire_gpu(bar);
+          if ((int)(v - target) >= 0) break;
+          if (ld_acquire_gpu(status) & FLAG_TIMEOUT) { ok = 0; break; }
+          if (clock64() - t0 > kSpinLimitCycles) { set_flag(status, FLAG_TIMEOUT); ok = 0; break; }
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      __syncwarp();
+      // the winner: every lane loads its share of the G records at once
       unsigned long long bv = 0ull;
       int bp = 0x7fffffff, bc = -1, bw = -1;
-      for (int g = lane; g < G; g += 32) {
-        const Cand cd = cand[(j & 1) * G + g];
-        if (cd.row >= 0 && cand_better(cd.key, cd.pos, bv, bp)) { bv = cd.key; bp = cd.pos; bc = g; bw = cd.row; }
+      if (ok) {
+        for (int g0 = 0; g0 < G; g0 += 32 * 8) {
+          int4 raw[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int g = g0 + lane + 32 * u;
+            if (g < G) raw[u] = __ldcg(reinterpret_cast<const int4*>(cands + (j & 1) * G + g));
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int g = g0 + lane + 32 * u;
+            if (g < G) {
+              const Cand cd = *reinterpret_cast<const Cand*>(&raw[u]);
+              if (cd.row >= 0 && cand_better(cd.key, cd.pos, bv, bp)) { bv = cd.key; bp = cd.pos; bc = g; bw = cd.row; }
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          int op = __shfl_xor_sync(0xffffffffu, bp, o);
+          int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+          int ow = __shfl_xor_sync(0xffffffffu, bw, o);
+          if (cand_better(ov, op, bv, bp) || (ov == bv && op == bp && oc > bc)) { bv = ov; bp = op; bc = oc; bw = ow; }
+        }
       }
+      if (!ok || bc < 0) {  // timed out, or no row left (cannot happen with steps <= rows)
+        if (lane == 0) {
+          if (ok) set_flag(status, FLAG_ZERO_PIVOT);
+          s_stop = 1;
+        }
+        __syncwarp();
+        bar_arrive(1, NT);
+        break;
+      }
+      // the pivot row (the winner's published values of columns j..cols-1)
+      T* ub = urow2 + (size_t)(j & 1) * cols;
+      {
+        const T* src = candrow + ((size_t)(j & 1) * G + bc) * cols;
+        for (int c = j + lane; c < cols; c += 32) ub[c - j] = ldcg_(src + (c - j));
+      }
+      __syncwarp();
+      if (lane == 0) {
+        const int w = bw, wpos = bp;
+        const bool zero = (ub[0] == zero_<T>());
+        s_zero = zero ? 1 : 0;
+        if (zero && blockIdx.x == 0) set_flag(status, FLAG_ZERO_PIVOT);
+        s_rpiv = zero ? zero_<T>() : recip(ub[0]);
+        // getf2 swap of positions j and wpos
+        const int occ = pwin[j];
+        pwin[j] = w;
+        if (wpos < steps) pwin[wpos] = occ;
+        if (occ != w && occ >= r0 && occ < r0 + nr) lpos[occ - r0] = wpos;
+        if (w >= r0 && w < r0 + nr) {
+          lpos[w - r0] = j;
+          lstep[w - r0] = j;
+        }
+      }
+      __syncwarp();
+      bar_arrive(1, NT);
+    }
+  } else {
+    // ------------------------------------------------------------ workers
+    const int tw = tid - 32, wk = warp - 1;
+    // Candidate for column jc among the rows not yet pivoted: key and position
+    // from each worker thread's rows, reduced over the workers; the result
+    // (local row or -1) lands in s_rstar, s_ckey, s_cpos.
+    auto reduce_cand = [&](unsigned long long bv, int bp, int br) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         unsigned long long ov = __shfl_down_sync(0xffffffffu, bv, o);
         int op = __shfl_down_sync(0xffffffffu, bp, o);
-        int oc = __shfl_down_sync(0xffffffffu, bc, o);
-        int ow = __shfl_down_sync(0xffffffffu, bw, o);
-        if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; bc = oc; bw = ow; }
+        int orr = __shfl_down_sync(0xffffffffu, br, o);
+        if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; br = orr; }
       }
-      if (lane == 0) {
-        s_wcta = bc;
-        s_wpos = bp;
-        s_wrow = bw;
+      if (lane == 0) { red_v[wk] = bv; red_p[wk] = bp; red_r[wk] = br; }
+      bar_sync(3, NTW);
+      if (tw == 0) {
+        for (int w = 1; w < NWK; ++w)
+          if (cand_better(red_v[w], red_p[w], bv, bp)) { bv = red_v[w]; bp = red_p[w]; br = red_r[w]; }
+        s_rstar = br;
+        s_ckey = bv;
+        s_cpos = bp;
       }
-    }
-    __syncthreads();
-    const int wcta = s_wcta;
-    if (wcta < 0) {  // no row left (cannot happen with steps <= rows)
-      if (tid == 0) set_flag(status, FLAG_ZERO_PIVOT);
-      break;
-    }
-    {
-      const T* src = candrow + ((size_t)(j & 1) * G + wcta) * cols;
-      for (int c = j + tid; c < cols; c += NT) urow[c - j] = src[c - j];
-    }
-    __syncthreads();
-    if (tid == 0) {
-      const int w = s_wrow, wpos = s_wpos;
-      s_zero = (urow[0] == zero_<T>()) ? 1 : 0;
-      if (s_zero && blockIdx.x == 0) set_flag(status, FLAG_ZERO_PIVOT);
-      // getf2 swap of positions j and wpos
-      const int occ = pwin[j];
-      pwin[j] = w;
-      if (wpos < steps) pwin[wpos] = occ;
-      if (occ != w && occ >= r0 && occ < r0 + nr) lpos[occ - r0] = wpos;
-      if (w >= r0 && w < r0 + nr) {
-        lpos[w - r0] = j;
-        lstep[w - r0] = j;
+      bar_sync(3, NTW);
+    };
+    auto write_candrow = [&](int jc) {
+      const int lr = s_rstar;
+      T* dst = candrow + ((size_t)(jc & 1) * G + blockIdx.x) * cols;
+      if (lr >= 0)
+        for (int c = jc + tw; c < cols; c += NTW) dst[c - jc] = at(lr, c);
+    };
+
+    // step 0 candidate
+    if (steps > 0) {
+      unsigned long long bv = 0ull;
+      int bp = 0x7fffffff, br = -1;
+      for (int r = tw; r < nr; r += NTW) {
+        const unsigned long long v = mag_key(at(r, 0));
+        const int p = lpos[r];
+        if (cand_better(v, p, bv, bp)) { bv = v; bp = p; br = r; }
       }
+      reduce_cand(bv, bp, br);
+      write_candrow(0);
+      bar_arrive(2, NT);
     }
-    __syncthreads();
-    const bool zero = s_zero != 0;
-    // 3. column j below the pivot: l = x / pivot; then column j+1 (look-ahead)
-    if (!zero) {
-      const T rpiv = recip(urow[0]);
-      const T u1 = (j + 1 < cols) ? urow[1] : zero_<T>();
-      for (int r = tid; r < nr; r += NT) {
-        if (lstep[r] < 0) {
-          T lv = at(r, j) * rpiv;
-          at(r, j) = lv;
-          lval[r] = lv;
-          if (j + 1 < cols) {
-            T& x = at(r, j + 1);
-            x = mad(-lv, u1, x);
-          }
-        }
-      }
-    }
-    __syncthreads();
-    int rstar = -1;
-    if (j + 1 < steps) {
-      // 4. next candidate: its row is brought fully up to date before publishing
-      rstar = publish(j + 1);
-      if (!zero && rstar >= 0)
-        for (int c = j + 2 + tid; c < cols; c += NT) {
-          T& x = at(rstar, c);
-          x = mad(-lval[rstar], urow[c - j], x);
-        }
-      __syncthreads();
-      write_cand(j + 1, rstar);
-      grid_arrive(bar);
-    }
-    // 5. the rest of the rank-1 update (columns j+2.., rows other than rstar)
-    const int c0 = j + 2;
-    if (!zero && c0 < cols) {
-      if (SMEM) {
-        for (int r = warp; r < nr; r += NW) {
-          if (lstep[r] < 0 && r != rstar) {
-            const T lv = -lval[r];
-            for (int c = c0 + lane; c < cols; c += 32) {
-              T& x = at(r, c);
-              x = mad(lv, urow[c - j], x);
+    for (int j = 0; j < steps; ++j) {
+      bar_sync(1, NT);  // pivot row and bookkeeping of step j are in place
+      if (s_stop) break;
+      const bool zero = s_zero != 0;
+      const T rpiv = s_rpiv;
+      const T* ub = urow2 + (size_t)(j & 1) * cols;
+      const bool more = j + 1 < steps;
+      // column j below the pivot (l = x / pivot), then column j+1 (look-ahead),
+      // and the best candidate of column j+1 among this CTA's rows
+      unsigned long long bv = 0ull;
+      int bp = 0x7fffffff, br = -1;
+      {
+        const T u1 = (j + 1 < cols) ? ub[1] : zero_<T>();
+        for (int r = tw; r < nr; r += NTW) {
+          if (lstep[r] < 0) {
+            if (!zero) {
+              const T lv = at(r, j) * rpiv;
+              at(r, j) = lv;
+              lval[r] = lv;
+              if (j + 1 < cols) {
+                T& x = at(r, j + 1);
+                x = mad(-lv, u1, x);
+              }
+            }
+            if (more) {
+              const unsigned long long v = mag_key(at(r, j + 1));
+              const int p = lpos[r];
+              if (cand_better(v, p, bv, bp)) { bv = v; bp = p; br = r; }
             }
           }
         }
-      } else {
-        // global memory: a flat loop over (row, column) with several independent
-        // elements per thread in flight; the fast index follows the memory layout
-        const int width = cols - c0;
-        const int tot = nr * width;
-        constexpr int U = 4;
-        for (int base = tid; base < tot; base += NT * U) {
-          T xv[U];
-          int rr[U], cc[U];
-          bool act[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int idx = base + u * NT;
-            int r, c;
-            if (row_fast) { r = idx % nr; c = idx / nr; } else { c = idx % width; r = idx / width; }
-            rr[u] = r;
-            cc[u] = c0 + c;
-            act[u] = idx < tot && lstep[r < nr ? r : 0] < 0 && r != rstar;
-            if (act[u]) xv[u] = at(r, c0 + c);
+      }
+      int rstar = -1;
+      if (more) {
+        reduce_cand(bv, bp, br);  // ends with a worker barrier: lval and column j+1 are complete
+        rstar = s_rstar;
+        // the candidate row is brought fully up to date before it is published
+        if (!zero && rstar >= 0) {
+          for (int c = j + 2 + tw; c < cols; c += NTW) {
+            T& x = at(rstar, c);
+            x = mad(-lval[rstar], ub[c - j], x);
           }
+        }
+        bar_sync(3, NTW);
+        write_candrow(j + 1);
+        bar_arrive(2, NT);
+      } else {
+        bar_sync(3, NTW);
+      }
+      // the rest of the rank-1 update (columns j+2.., rows other than rstar)
+      const int c0 = j + 2;
+      if (!zero && c0 < cols) {
+        if (SMEM) {
+          for (int r = wk; r < nr; r += NWK) {
+            if (lstep[r] < 0 && r != rstar) {
+              const T lv = -lval[r];
+              for (int c = c0 + lane; c < cols; c += 32) {
+                T& x = at(r, c);
+                x = mad(lv, ub[c - j], x);
+              }
+            }
+          }
+        } else {
+          // global memory: a flat loop over (row, column) with several independent
+          // elements per thread in flight; the fast index follows the memory layout
+          const int width = cols - c0;
+          const int tot = nr * width;
+          constexpr int U = 4;
+          for (int base = tw; base < tot; base += NTW * U) {
+            T xv[U];
+            int rr[U], cc[U];
+            bool act[U];
 #pragma unroll
-          for (int u = 0; u < U; ++u)
-            if (act[u]) at(rr[u], cc[u]) = mad(-lval[rr[u]], urow[cc[u] - j], xv[u]);
+            for (int u = 0; u < U; ++u) {
+              const int idx = base + u * NTW;
+              int r, c;
+              if (row_fast) { r = idx % nr; c = idx / nr; } else { c = idx % width; r = idx / width; }
+              rr[u] = r;
+              cc[u] = c0 + c;
+              act[u] = idx < tot && lstep[r < nr ? r : 0] < 0 && r != rstar;
+              if (act[u]) xv[u] = at(r, c0 + c);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (act[u]) at(rr[u], cc[u]) = mad(-lval[rr[u]], ub[cc[u] - j], xv[u]);
+          }
         }
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
 
   // write back
   if (SMEM) {
@@ -298,7 +383,7 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
 
 template <typename T, bool SMEM>
 static size_t pivlu_smem(int64_t rpc, int cols, int steps) {
-  size_t b = (SMEM ? (size_t)rpc * cols * sizeof(T) : 0) + (size_t)cols * sizeof(T) + (size_t)rpc * sizeof(T) +
+  size_t b = (SMEM ? (size_t)rpc * cols * sizeof(T) : 0) + 2 * (size_t)cols * sizeof(T) + (size_t)rpc * sizeof(T) +
              (size_t)rpc * 8 + (size_t)steps * 4;
   return (b + 15) & ~(size_t)15;
 }

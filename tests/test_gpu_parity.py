@@ -185,6 +185,42 @@ def test_dense_f32_parity(rg, m, n, k, l, l1, rank, noise):
         assert abs(e_g / e_o - 1) <= 1e-2
 
 
+@pytest.fixture(scope="module")
+def bf16_case():
+    """BF16-stored A (1/i^2 spectrum, rank-256 truncation: tail 1.5e-5 << the BF16
+    rounding) and the oracle's factorization of the same rounded matrix."""
+    m, n, k, l, l1 = 3000, 2000, 60, 80, 640
+    A = ri.round_to_bf16(ri.dense_spectrum(m, n, ri.inverse_square_spectrum(256), 4242))[0]
+    o = oracle.factor(A.astype(np.float64), k, l, l1, seed=93)
+    e_o = oracle.relative_residual(A.astype(np.float64), o.L, o.U, o.p, o.q)
+    kappa = np.linalg.cond(o.Ly)
+    return A, (m, n, k, l, l1), o, e_o, kappa
+
+
+# Precision forms on BF16 input.  W is carried in BF16 planes: three planes
+# (24 significant bits, RLU_PREC_F32), two (hi + lo, 16 bits: the one-step
+# refinement) or one (8 bits).  An entrywise relative error eps in W moves
+# L U = L_y (W A) Q by at most eps * ||L_y|| ||W|| ||A|| = eps * kappa(L_y) ||A||
+# (W = L_y^+, so ||L_y|| ||W|| = kappa(L_y)), hence |e_gpu - e_oracle| <=
+# eps * kappa(L_y) with eps = 2^-(bits+1); the FP32 sketch and accumulation add
+# far less (the FP32 bar of 1e-5 covers them).
+@pytest.mark.parametrize("prec,bits", [("f32", 24), ("bf16_refine", 16), ("bf16", 8)])
+def test_dense_bf16_precision_forms(rg, bf16_case, prec, bits):
+    A, (m, n, k, l, l1), o, e_o, kappa = bf16_case
+    g = run(rg, A, k, l, l1, 93, prec, torch.bfloat16)
+    assert g["status"] == 0
+    check_structure(g, m, n, k)
+    e_g = oracle.relative_residual(A.astype(np.float64), g["L"], g["U"], g["p"], g["q"])
+    tol = max(1e-5, 2.0 ** -(bits + 1) * kappa)
+    assert abs(e_g - e_o) <= tol, (prec, e_g, e_o, kappa, tol)
+    if prec == "f32":
+        check_pivots(g, o, k)
+    else:
+        # the sketch (hence the row pivots) does not depend on the W planes
+        sy = separated_prefix(o.top_y, np.abs(o.Y).max(), 1e-4)
+        assert np.array_equal(g["p"][:sy], o.p[:sy])
+
+
 def test_dense_f32_8192_full_size(rg):
     """The dense FP32 workload at full size, in the configuration the bench times."""
     w = ri.DENSE_F32_8K
