@@ -6,6 +6,8 @@
 // of the pseudo-inverse (these run at the FP64 pipe rate whatever the tiling)
 // and for the small FP32 products.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace rlu {
@@ -152,6 +154,130 @@ __global__ void k_sum_slices(int64_t MN, int S, const double* __restrict__ part,
   out[e] = (TC)s;
 }
 
+// The same product accumulated in float-float on the FP32 pipes, with the
+// cheaper accumulation of Ogita, Rump and Oishi ("Accurate sum and dot
+// product", SISC 2005, Algorithm Dot2-style): each term a*b is split exactly
+// into p + e (TwoProd by FMA, plus the hi*lo cross terms), p enters the running
+// sum s through TwoSum, and the rounding errors of both go into a plain FP32
+// correction c; (s, c) is renormalised once per K slice.  12 FP32 operations
+// per term instead of the 18 of a full float-float multiply-add; error of order
+// K * 2^-48 relative to the sum of |a*b|.  Operands are held in shared memory
+// as separate hi / lo planes, each thread's 4 x 4 outputs contiguous so that
+// one 16-byte load feeds 4 terms; the next K slice is fetched into registers
+// while the current one is consumed (two shared-memory buffers).
+template <typename T> __device__ __forceinline__ df32 to_df(T x) { return cvt<df32>(x); }
+
+template <typename TC> __device__ __forceinline__ TC from_df(float s, float c);
+template <> __device__ __forceinline__ double from_df<double>(float s, float c) { return (double)s + (double)c; }
+template <> __device__ __forceinline__ float from_df<float>(float s, float c) { return s + c; }
+template <> __device__ __forceinline__ df32 from_df<df32>(float s, float c) { return quick_two_sum(s, c); }
+
+template <typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(256) k_gemm_df32(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A,
+                                                   int64_t a_rs, int64_t a_cs, const TB* __restrict__ B,
+                                                   int64_t b_rs, int64_t b_cs, TC* __restrict__ C, int64_t c_rs,
+                                                   int64_t c_cs, int64_t c_zs, int64_t k_per_split) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ __align__(16) float sAh[2][BK][BM], sAl[2][BK][BM];
+  __shared__ __align__(16) float sBh[2][BK][BN], sBl[2][BK][BN];
+  const int tid = threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+  const int64_t kbeg = (int64_t)blockIdx.z * k_per_split;
+  const int64_t kend = min(K, kbeg + k_per_split);
+  const int ti = tid / 16, tj = tid % 16;  // rows ti*4.., columns tj*4..
+  const bool a_kfast = (a_cs == 1);
+  const bool b_jfast = (b_cs == 1);
+  float s[4][4], c[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) { s[x][y] = 0.f; c[x][y] = 0.f; }
+
+  df32 ra[4], rb[4];  // the next slice, in registers
+  auto fetch = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int ii, kk;
+      if (a_kfast) { kk = e % BK; ii = e / BK; } else { ii = e % BM; kk = e / BM; }
+      const int64_t gi = i0 + ii, gk = k0 + kk;
+      ra[q] = (gi < M && gk < kend) ? to_df(A[gi * a_rs + gk * a_cs]) : df_make(0.f, 0.f);
+      int jj, kb;
+      if (b_jfast) { jj = e % BN; kb = e / BN; } else { kb = e % BK; jj = e / BK; }
+      const int64_t gj = j0 + jj, gkb = k0 + kb;
+      rb[q] = (gj < N && gkb < kend) ? to_df(B[gkb * b_rs + gj * b_cs]) : df_make(0.f, 0.f);
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int ii, kk;
+      if (a_kfast) { kk = e % BK; ii = e / BK; } else { ii = e % BM; kk = e / BM; }
+      sAh[buf][kk][ii] = ra[q].hi;
+      sAl[buf][kk][ii] = ra[q].lo;
+      int jj, kb;
+      if (b_jfast) { jj = e % BN; kb = e / BN; } else { kb = e % BK; jj = e / BK; }
+      sBh[buf][kb][jj] = rb[q].hi;
+      sBl[buf][kb][jj] = rb[q].lo;
+    }
+  };
+
+  int buf = 0;
+  if (kbeg < kend) {
+    fetch(kbeg);
+    stash(0);
+  }
+  __syncthreads();
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool next = k0 + BK < kend;
+    if (next) fetch(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 ah = *reinterpret_cast<const float4*>(&sAh[buf][kk][ti * 4]);
+      const float4 al = *reinterpret_cast<const float4*>(&sAl[buf][kk][ti * 4]);
+      const float4 bh = *reinterpret_cast<const float4*>(&sBh[buf][kk][tj * 4]);
+      const float4 bl = *reinterpret_cast<const float4*>(&sBl[buf][kk][tj * 4]);
+      const float a_h[4] = {ah.x, ah.y, ah.z, ah.w}, a_l[4] = {al.x, al.y, al.z, al.w};
+      const float b_h[4] = {bh.x, bh.y, bh.z, bh.w}, b_l[4] = {bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const float p = __fmul_rn(a_h[x], b_h[y]);
+          float e = __fmaf_rn(a_h[x], b_h[y], -p);
+          e = __fmaf_rn(a_h[x], b_l[y], e);
+          e = __fmaf_rn(a_l[x], b_h[y], e);
+          const float t = __fadd_rn(s[x][y], p);
+          const float bb = __fsub_rn(t, s[x][y]);
+          const float err = __fadd_rn(__fsub_rn(s[x][y], __fsub_rn(t, bb)), __fsub_rn(p, bb));
+          s[x][y] = t;
+          c[x][y] = __fadd_rn(c[x][y], __fadd_rn(err, e));
+        }
+    }
+    // renormalise once per slice: s + c stays exact, |c| stays below ulp(s)
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const df32 r = two_sum(s[x][y], c[x][y]);
+        s[x][y] = r.hi;
+        c[x][y] = r.lo;
+      }
+    if (next) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  TC* Cz = C + (int64_t)blockIdx.z * c_zs;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int64_t gi = i0 + ti * 4 + x, gj = j0 + tj * 4 + y;
+      if (gi < M && gj < N) Cz[gi * c_rs + gj * c_cs] = from_df<TC>(s[x][y], c[x][y]);
+    }
+}
+
 template <typename TA, typename TB, typename TC, typename TACC>
 inline int gemm_simt(cudaStream_t st, int64_t M, int64_t N, int64_t K, const TA* A, int64_t a_rs, int64_t a_cs,
                      const TB* B, int64_t b_rs, int64_t b_cs, TC* C, int64_t c_rs, int64_t c_cs, int splits = 1,
@@ -160,8 +286,11 @@ inline int gemm_simt(cudaStream_t st, int64_t M, int64_t N, int64_t K, const TA*
   int64_t kps = cdiv(K, splits);
   kps = cdiv(kps, 16) * 16;
   dim3 grid((unsigned)cdiv(N, 64), (unsigned)cdiv(M, 64), (unsigned)splits);
-  k_gemm_simt<TA, TB, TC, TACC><<<grid, 256, 0, st>>>(M, N, K, A, a_rs, a_cs, B, b_rs, b_cs, C, c_rs, c_cs, c_zs,
-                                                       kps);
+  if constexpr (std::is_same<TACC, df32>::value)
+    k_gemm_df32<TA, TB, TC><<<grid, 256, 0, st>>>(M, N, K, A, a_rs, a_cs, B, b_rs, b_cs, C, c_rs, c_cs, c_zs, kps);
+  else
+    k_gemm_simt<TA, TB, TC, TACC><<<grid, 256, 0, st>>>(M, N, K, A, a_rs, a_cs, B, b_rs, b_cs, C, c_rs, c_cs, c_zs,
+                                                         kps);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
   return RLU_OK;
