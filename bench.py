@@ -182,6 +182,9 @@ def main():
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent slots")
     ap.add_argument("--pool-gb", type=float, default=48.0, help="serving: device pool for admission (GiB)")
     ap.add_argument("--e2e-requests", type=int, default=256, help="serving: requests of the host-arrival run")
+    ap.add_argument("--coop-ctas", type=int, default=-1,
+                    help="serving: CTAs of each request's grid-synchronised kernels (0 = one per SM, -1 = the "
+                         "server's default, a quarter of the SMs)")
     ap.add_argument("--prec", default=None, help="override the workload's precision (f64, f32, bf16, bf16_refine)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -492,7 +495,8 @@ def run_serving(args, rank, world, local):
             t += s.gap / rate
             r.t_arrive = t
 
-    with serving.Server(pool_bytes, slots=args.slots) as srv:
+    coop = None if args.coop_ctas < 0 else args.coop_ctas
+    with serving.Server(pool_bytes, slots=args.slots, coop_ctas=coop) as srv:
         srv.run(warm, open_loop=False)
         torch.cuda.synchronize()
         l0 = rg.rlu_debug_launch_count()
@@ -512,7 +516,7 @@ def run_serving(args, rank, world, local):
             set_arrivals(frac * sat)
             res, span = srv.run(reqs, open_loop=True)
             runs["open_loop_%.1fx" % frac] = dict(serving.summarize(res, span), arrival_rate=frac * sat)
-    with serving.Server(pool_bytes, slots=1) as one:
+    with serving.Server(pool_bytes, slots=1, coop_ctas=0) as one:
         one.run(warm[:3], open_loop=False)
         res_one, span_one = one.run(reqs, open_loop=False)
         s1 = serving.summarize(res_one, span_one)
@@ -536,7 +540,8 @@ def run_serving(args, rank, world, local):
                 host_base[b] = r.A.as_strided((16384, 16384), (16384, 1)).cpu().pin_memory()
             q.A = host_base[b][: r.m, : r.n]
         hreqs.append(q)
-    with serving.Server(pool_bytes, slots=args.slots, return_host=(16384, 16384, 256, "f32")) as srv:
+    with serving.Server(pool_bytes, slots=args.slots, return_host=(16384, 16384, 256, "f32"),
+                        coop_ctas=coop) as srv:
         srv.run(hreqs[: args.slots], open_loop=False)
         barrier()
         res_e2e, span_e2e = srv.run(hreqs, open_loop=False)
@@ -563,6 +568,7 @@ def run_serving(args, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": SERVING_WORKLOAD, "requests": len(reqs), "slots": args.slots,
+                       "coop_ctas": srv.coop_ctas,
                        "pool_gib": args.pool_gb, "m_n": "log-uniform [512, 16384]", "k": "uniform [16, 256]",
                        "l": "k + 20", "l1": "8 k", "dense_share": rs.DENSE_SHARE, "csr_density": rs.CSR_DENSITY,
                        "dense_inputs": "leading blocks of 8 rank-96 16384^2 FP32 matrices, geometric spectrum",

@@ -116,6 +116,16 @@ int rlu_set_csr_workspace(rlu_t h, int64_t max_nnz, void* workspace, size_t work
 /* Select the arithmetic (rlu_prec).  Valid at any time between calls. */
 int rlu_set_precision(rlu_t h, int prec);
 
+/* Bound the CTAs of the two grid-synchronised kernels of handle h (the
+ * pivoted LUs of steps 3 and 6, the Cholesky factor of G) to max_ctas; 0 (the
+ * default) gives one CTA per SM.  Results do not depend on it (each kernel's
+ * arithmetic per element and its pivot choice are independent of the grid);
+ * fewer CTAs make a lone factorization's elimination steps longer but leave
+ * SMs to factorizations running beside it on other streams (serving).
+ * The library's own extension; the paper has no counterpart.
+ * Errors: RLU_EINVAL (null handle, negative bound). */
+int rlu_set_max_ctas(rlu_t h, int32_t max_ctas);
+
 /* Device bytes that rlu_create allocates for these sizes and precision
  * (for admission by HBM footprint).  Errors: RLU_EINVAL. */
 int rlu_workspace_bytes(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, int prec, size_t* bytes);

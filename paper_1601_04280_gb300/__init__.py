@@ -29,7 +29,7 @@ C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_
              "rlu_strerror", "rlu_debug_sketch_params", "rlu_debug_Y", "rlu_debug_B", "rlu_debug_enable",
              "rlu_debug_timing", "rlu_debug_stage_ms", "rlu_debug_launch_count", "rlu_sketch_dense_noalloc",
              "rlu_csr_workspace_bytes", "rlu_set_csr_workspace", "rlu_graph_capture_dense", "rlu_graph_launch",
-             "rlu_graph_destroy", "rlu_copy_block_async")
+             "rlu_graph_destroy", "rlu_copy_block_async", "rlu_set_max_ctas")
 
 #: stage names reported by rlu_debug_stage_ms, in order
 STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
@@ -78,6 +78,7 @@ def load(reload=False):
         "rlu_graph_launch": ([vp, vp], c.c_int),
         "rlu_graph_destroy": ([vp], c.c_int),
         "rlu_copy_block_async": ([vp, i64, vp, i64, i64, i64, vp], c.c_int),
+        "rlu_set_max_ctas": ([vp, i32], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -119,6 +120,10 @@ def rlu_create_in(m, n, k, l, l1, seed, workspace_ptr, workspace_bytes, stream_p
 
 def rlu_set_precision(h, prec):
     return _check(load().rlu_set_precision(h, PREC.get(prec, prec)), "rlu_set_precision")
+
+
+def rlu_set_max_ctas(h, max_ctas):
+    return _check(load().rlu_set_max_ctas(h, int(max_ctas)), "rlu_set_max_ctas")
 
 
 def rlu_workspace_bytes(m, n, k, l, l1, prec):
@@ -225,6 +230,10 @@ class RandLU:
                                    workspace.numel() * workspace.element_size(), _stream_ptr(stream))
         self.prec = prec
         rlu_set_precision(self.h, prec)
+
+    def set_max_ctas(self, max_ctas):
+        """Bound the CTAs of the grid-synchronised kernels (0: one per SM)."""
+        rlu_set_max_ctas(self.h, max_ctas)
 
     def set_csr_workspace(self, workspace, max_nnz):
         """Caller-owned CSR scratch (device uint8 tensor, >= rlu_csr_workspace_bytes)."""

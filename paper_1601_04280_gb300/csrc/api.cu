@@ -59,27 +59,14 @@ void status_slab_give(unsigned int* w) {
   g_slab_free.push_back(w);
 }
 
-static std::mutex g_coop_mu;
-static cudaEvent_t g_coop_evt[64] = {};
-static bool g_coop_any[64] = {};
-
+// Cooperative launch of a kernel with grid barriers.  Such kernels on different
+// streams are not ordered against each other: the driver starts a cooperative
+// grid only once every one of its CTAs can be resident, so two of them never
+// hold part of the GPU each while waiting for the rest (the serving loop runs
+// them side by side; the bounded grid barriers would report the opposite as
+// RLU_ETIMEOUT).
 cudaError_t launch_cooperative(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st) {
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
-  int dev = 0;
-  if (cap != cudaStreamCaptureStatusNone || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-    return cudaLaunchCooperativeKernel(func, grid, block, args, smem, st);
-  std::lock_guard<std::mutex> lock(g_coop_mu);
-  if (!g_coop_evt[dev]) {
-    cudaError_t e = cudaEventCreateWithFlags(&g_coop_evt[dev], cudaEventDisableTiming);
-    if (e != cudaSuccess) return e;
-  }
-  cudaError_t e;
-  if (g_coop_any[dev] && (e = cudaStreamWaitEvent(st, g_coop_evt[dev], 0)) != cudaSuccess) return e;
-  if ((e = cudaLaunchCooperativeKernel(func, grid, block, args, smem, st)) != cudaSuccess) return e;
-  if ((e = cudaEventRecord(g_coop_evt[dev], st)) != cudaSuccess) return e;
-  g_coop_any[dev] = true;
-  return cudaSuccess;
+  return cudaLaunchCooperativeKernel(func, grid, block, args, smem, st);
 }
 
 int allow_dynamic_smem(const void* kern, size_t smem) {
@@ -94,23 +81,6 @@ int allow_dynamic_smem(const void* kern, size_t smem) {
   return RLU_OK;
 }
 
-// Launch a captured factorization as one unit of the same chain: it waits for
-// the last cooperative kernel of any stream, and later ones wait for it.
-cudaError_t launch_graph_chained(cudaGraphExec_t ge, cudaStream_t st) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_coop_mu);
-  if (!g_coop_evt[dev]) {
-    cudaError_t e = cudaEventCreateWithFlags(&g_coop_evt[dev], cudaEventDisableTiming);
-    if (e != cudaSuccess) return e;
-  }
-  cudaError_t e;
-  if (g_coop_any[dev] && (e = cudaStreamWaitEvent(st, g_coop_evt[dev], 0)) != cudaSuccess) return e;
-  if ((e = cudaGraphLaunch(ge, st)) != cudaSuccess) return e;
-  if ((e = cudaEventRecord(g_coop_evt[dev], st)) != cudaSuccess) return e;
-  g_coop_any[dev] = true;
-  return cudaSuccess;
-}
 }  // namespace rlu
 
 struct rlu_graph {
@@ -128,6 +98,7 @@ struct rlu_ctx {
   int prec = RLU_PREC_F32;
   int device = 0;
   int num_sms = 0;
+  int max_ctas = 0;  // bound on the CTAs of the grid-synchronised kernels (0: one per SM)
   SketchWs sk{};
   double* Y = nullptr;
   PivLuWs pw{};
@@ -244,6 +215,9 @@ bool sizes_ok(int64_t m, int64_t n, int k, int l, int l1) {
   if (l > kMaxL || l1 > kMaxL1) return false;
   return true;
 }
+
+// CTAs for the grid-synchronised kernels of this handle.
+int coop_sms(const rlu_ctx* h) { return h->max_ctas > 0 && h->max_ctas < h->num_sms ? h->max_ctas : h->num_sms; }
 
 int map_flags(unsigned int f) {
   if (f & FLAG_TIMEOUT) return RLU_ETIMEOUT;
@@ -413,7 +387,7 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Ydbg, h->Y, sizeof(double) * m * l, cudaMemcpyDeviceToDevice, st));
   // step 3: P Y = L_Y U_Y (FP64, l steps)
   h->pw.perm = h->perm_y;
-  if ((rc = launch_pivoted_lu<double>(h->Y, m, l, l, 1, l, h->pw, h->status_dev, h->num_sms, st))) return rc;
+  if ((rc = launch_pivoted_lu<double>(h->Y, m, l, l, 1, l, h->pw, h->status_dev, coop_sms(h), st))) return rc;
   if ((rc = mark(h, 3, st))) return rc;
   // W = L_y^+ P
   PinvArgs pa{};
@@ -422,7 +396,7 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   pa.gram_part = h->gram_part; pa.max_gram_splits = h->max_gram_splits;
   pa.G = h->G; pa.Rinv = h->Rinv; pa.Ginv = h->Ginv;
   pa.W = h->W; pa.w64 = f64 ? 1 : 0;
-  pa.bar = h->bar2; pa.status = h->status_dev; pa.num_sms = h->num_sms;
+  pa.bar = h->bar2; pa.status = h->status_dev; pa.num_sms = h->num_sms; pa.coop_ctas = coop_sms(h);
   if ((rc = launch_gram(pa, st))) return rc;
   if ((rc = mark(h, 4, st))) return rc;
   if ((rc = launch_chol(pa, st))) return rc;
@@ -443,9 +417,9 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   h->pw.perm = h->perm_b;
   if (f64)
     rc = launch_pivoted_lu<double>(reinterpret_cast<double*>(h->B), n, k, 1, n, k, h->pw, h->status_dev,
-                                   h->num_sms, st);
+                                   coop_sms(h), st);
   else
-    rc = launch_pivoted_lu<df32>(reinterpret_cast<df32*>(h->B), n, k, 1, n, k, h->pw, h->status_dev, h->num_sms,
+    rc = launch_pivoted_lu<df32>(reinterpret_cast<df32*>(h->B), n, k, 1, n, k, h->pw, h->status_dev, coop_sms(h),
                                  st);
   if (rc) return rc;
   if ((rc = mark(h, 8, st))) return rc;
@@ -491,7 +465,7 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   if (h->debug && h->Ydbg)
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Ydbg, h->Y, sizeof(double) * m * l, cudaMemcpyDeviceToDevice, st));
   h->pw.perm = h->perm_y;
-  if ((rc = launch_pivoted_lu<double>(h->Y, m, l, l, 1, l, h->pw, h->status_dev, h->num_sms, st))) return rc;
+  if ((rc = launch_pivoted_lu<double>(h->Y, m, l, l, 1, l, h->pw, h->status_dev, coop_sms(h), st))) return rc;
   if ((rc = mark(h, 3, st))) return rc;
   PinvArgs pa{};
   pa.m = m; pa.k = k; pa.l = l;
@@ -499,7 +473,7 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   pa.gram_part = h->gram_part; pa.max_gram_splits = h->max_gram_splits;
   pa.G = h->G; pa.Rinv = h->Rinv; pa.Ginv = h->Ginv;
   pa.W = h->W; pa.w64 = f64 ? 1 : 0;
-  pa.bar = h->bar2; pa.status = h->status_dev; pa.num_sms = h->num_sms;
+  pa.bar = h->bar2; pa.status = h->status_dev; pa.num_sms = h->num_sms; pa.coop_ctas = coop_sms(h);
   if ((rc = launch_gram(pa, st))) return rc;
   if ((rc = mark(h, 4, st))) return rc;
   if ((rc = launch_chol(pa, st))) return rc;
@@ -515,9 +489,9 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   h->pw.perm = h->perm_b;
   if (f64)
     rc = launch_pivoted_lu<double>(reinterpret_cast<double*>(h->B), n, k, 1, n, k, h->pw, h->status_dev,
-                                   h->num_sms, st);
+                                   coop_sms(h), st);
   else
-    rc = launch_pivoted_lu<df32>(reinterpret_cast<df32*>(h->B), n, k, 1, n, k, h->pw, h->status_dev, h->num_sms,
+    rc = launch_pivoted_lu<df32>(reinterpret_cast<df32*>(h->B), n, k, 1, n, k, h->pw, h->status_dev, coop_sms(h),
                                  st);
   if (rc) return rc;
   if ((rc = mark(h, 8, st))) return rc;
@@ -723,6 +697,12 @@ int rlu_create_in(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64
   return create_common(m, n, k, l, l1, seed, (char*)workspace, false, false, (cudaStream_t)stream, out);
 }
 
+int rlu_set_max_ctas(rlu_t h, int32_t max_ctas) {
+  if (!h || max_ctas < 0) return RLU_EINVAL;
+  h->max_ctas = max_ctas;
+  return RLU_OK;
+}
+
 int rlu_set_precision(rlu_t h, int prec) {
   if (!h || prec < 0 || prec > 3) return RLU_EINVAL;
   h->prec = prec;
@@ -833,7 +813,7 @@ int rlu_copy_block_async(void* dst, int64_t dst_pitch, const void* src, int64_t 
 
 int rlu_graph_launch(rlu_graph_t g, void* stream) {
   if (!g || !g->exec) return RLU_EINVAL;
-  RLU_CUDA_TRY(launch_graph_chained(g->exec, (cudaStream_t)stream));
+  RLU_CUDA_TRY(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
   note_launch((int)g->kernels);
   return RLU_OK;
 }

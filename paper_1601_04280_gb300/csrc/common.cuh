@@ -242,10 +242,7 @@ template <typename T> __device__ __forceinline__ T one_() { return cvt<T>(1.0); 
 // Process-wide count of kernels this library has launched (a test hook).
 void note_launch(int count = 1);
 
-// Cooperative launch of a kernel with grid barriers.  Such kernels from
-// different streams are chained on the GPU (each waits for the previous one
-// to finish, through an event), so two of them are never partly resident at
-// once and waiting on each other; all other kernels still overlap freely.
+// Cooperative launch of a kernel with grid barriers (all CTAs co-resident).
 cudaError_t launch_cooperative(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st);
 
 // Lift a kernel's dynamic shared-memory limit to the most the device allows

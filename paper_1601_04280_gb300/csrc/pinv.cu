@@ -242,7 +242,7 @@ int launch_chol(const PinvArgs& a, cudaStream_t st) {
   int per_sm = 0;
   RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_inv, 256, smem));
   if (per_sm < 1) return RLU_EINVAL;
-  int G = a.num_sms;
+  int G = a.coop_ctas > 0 ? min(a.coop_ctas, a.num_sms) : a.num_sms;
   double* Sm = a.G;
   double* Ri = a.Rinv;
   int kk = k;

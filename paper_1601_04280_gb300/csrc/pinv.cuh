@@ -21,6 +21,7 @@ struct PinvArgs {
   unsigned int* bar;
   unsigned int* status;
   int num_sms;
+  int coop_ctas;  // CTAs of the grid-synchronised Cholesky kernel (<= num_sms)
 };
 
 struct AssembleArgs {

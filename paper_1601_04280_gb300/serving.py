@@ -36,7 +36,7 @@ import numpy as np
 
 from . import (PREC, RLU_BF16, RLU_F32, RLU_F64, RLU_OK, RLU_WRANK, load, rlu_copy_block_async, rlu_create_in,
                rlu_csr_workspace_bytes, rlu_destroy, rlu_graph_capture_dense, rlu_graph_destroy, rlu_graph_launch,
-               rlu_set_csr_workspace, rlu_set_precision, rlu_workspace_bytes)
+               rlu_set_csr_workspace, rlu_set_max_ctas, rlu_set_precision, rlu_workspace_bytes)
 
 _ALIGN = 256
 
@@ -180,10 +180,14 @@ def footprint(req):
 class Server:
     """Slots x (stream, worker thread) over one device pool."""
 
-    def __init__(self, pool_bytes, slots=8, device="cuda", keep_outputs=False, max_bypass=None, return_host=None):
+    def __init__(self, pool_bytes, slots=8, device="cuda", keep_outputs=False, max_bypass=None, return_host=None,
+                 coop_ctas=None):
         """return_host: None, or (max_m, max_n, max_k, prec): every request's L, U,
         p, q and status are copied back into page-locked host buffers of the
-        slot (sized for those maxima) before the request counts as done."""
+        slot (sized for those maxima) before the request counts as done.
+        coop_ctas: bound on the CTAs of each request's grid-synchronised kernels
+        (rlu_set_max_ctas; 0 = one per SM; None = a quarter of the SMs, so that
+        several requests' eliminations run side by side)."""
         import torch
         load()
         self.device = torch.device(device)
@@ -191,6 +195,11 @@ class Server:
             self.device = torch.device("cuda", torch.cuda.current_device())
         self.pool = DevicePool(pool_bytes, device)
         self.nslots = slots
+        if coop_ctas is None:
+            sms = torch.cuda.get_device_properties(self.device).multi_processor_count \
+                if self.device.type == "cuda" else 0
+            coop_ctas = max(1, sms // 4) if sms else 0
+        self.coop_ctas = int(coop_ctas)
         self.keep_outputs = keep_outputs
         self.max_bypass = max_bypass if max_bypass is not None else 4 * slots
         cuda = self.device.type == "cuda"
@@ -252,6 +261,8 @@ class Server:
         h = rlu_create_in(req.m, req.n, req.k, req.l, req.l1, req.seed, ptr("ws"), P["ws"][1], sptr)
         try:
             rlu_set_precision(h, PREC[req.prec])
+            if self.coop_ctas:
+                rlu_set_max_ctas(h, self.coop_ctas)
             if req.csr is not None:
                 rowptr, colind, val = req.csr
                 nnz = int(val.numel())

@@ -135,6 +135,22 @@ def test_graph_replay_equals_eager(rg):
         bucket.close()
 
 
+@pytest.mark.parametrize("kind", ["dense", "csr"])
+def test_max_ctas_does_not_change_results(rg, mix, kind):
+    # the grid of the pivoted LUs and the Cholesky kernel is bounded; the
+    # factors are bit-for-bit those of the default grid
+    q = [r for r in mix if r.kind == kind][0]
+    ref = alone(rg, q)
+    for ctas in (1, 7, 40):
+        h = rg.RandLU(q.m, q.n, q.k, q.l, q.l1, q.seed, prec=q.prec)
+        h.set_max_ctas(ctas)
+        f = h.factor_csr(*q.csr, check=False) if q.csr is not None else h.factor(q.A, check=False)
+        torch.cuda.synchronize()
+        for a, b in zip((f.L.cpu(), f.U.cpu(), f.p.cpu(), f.q.cpu()), ref[:4]):
+            assert torch.equal(a, b), (kind, ctas)
+        h.close()
+
+
 def test_create_in_rejects_small_or_misaligned_workspace(rg):
     need = rg.rlu_workspace_bytes(500, 400, 10, 16, 64, "f32")
     buf = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
