@@ -50,7 +50,7 @@ typedef enum {
   RLU_ENOMEM = 2,     /* workspace allocation failed */
   RLU_ECUDA = 3,      /* a CUDA call failed, or no usable GPU */
   RLU_ETIMEOUT = 4,   /* a bounded device wait gave up (co-residency lost); outputs undefined */
-  RLU_ENONFINITE = 5, /* A holds NaN or Inf; outputs undefined */
+  RLU_ENONFINITE = 5, /* A holds NaN or Inf (or a sum of the sketch overflows FP32); outputs undefined */
   RLU_EBADCSR = 6,    /* CSR structure invalid (found on the device); outputs undefined */
   RLU_ETOOLARGE = 7,  /* sizes exceed the fixed scratch of rlu_sketch_dense_noalloc; nothing was launched */
   RLU_WRANK = 100     /* warning: an exactly zero pivot was met (rank deficiency); outputs valid */

@@ -278,6 +278,15 @@ __global__ void __launch_bounds__(256) k_gemm_df32(int64_t M, int64_t N, int64_t
     }
 }
 
+// The same sum stored as float-float.
+static __global__ void k_sum_slices_df(int64_t MN, int S, const double* __restrict__ part, df32* __restrict__ out) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= MN) return;
+  double s = 0.0;
+  for (int z = 0; z < S; ++z) s += part[(int64_t)z * MN + e];
+  out[e] = df_from_double(s);
+}
+
 template <typename TA, typename TB, typename TC, typename TACC>
 inline int gemm_simt(cudaStream_t st, int64_t M, int64_t N, int64_t K, const TA* A, int64_t a_rs, int64_t a_cs,
                      const TB* B, int64_t b_rs, int64_t b_cs, TC* C, int64_t c_rs, int64_t c_cs, int splits = 1,

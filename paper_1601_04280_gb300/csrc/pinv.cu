@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
       double rcol[kNb];  // rcol[t] = R_JJ[t][lane]
 #pragma unroll
       for (int t = 0; t < kNb; ++t) rcol[t] = (t < jb && lane < jb) ? S[(int64_t)(c0 + t) * k + c0 + lane] : 0.0;
-      const double rinv_l = (lane < jb) ? 1.0 / rcol[lane < kNb ? lane : 0] : 1.0;
+      const double rinv_l = (lane < jb) ? 1.0 / S[(int64_t)(c0 + lane) * k + c0 + lane] : 1.0;
       for (int64_t col = gwarp; col < rest; col += nwarps) {
         const int gc = c0 + jb + (int)col;
         double b = (lane < jb) ? S[(int64_t)(c0 + lane) * k + gc] : 0.0;
@@ -267,10 +267,23 @@ int launch_wform(const PinvArgs& a, cudaStream_t st) {
                                                      reinterpret_cast<const double*>(a.Lk), 1, k,
                                                      reinterpret_cast<double*>(a.W), m, 1);
   }
-  rc = gemm_simt<double, double, double, df32>(st, k, k, k, a.Rinv, k, 1, a.Rinv, 1, k, a.Ginv, k, 1);
+  // G^{-1} = R^{-1} R^{-T}: a small product (k x k x k), split over K so that it
+  // fills the GPU; partials in the Gram scratch (free again after the
+  // Cholesky), summed in FP64 and stored as float-float for the W product.
+  const int64_t tiles = cdiv(k, 64) * cdiv(k, 64);
+  int S = (int)min64(a.max_gram_splits, max64(1, cdiv(2 * a.num_sms, tiles)));
+  S = (int)min64(S, max64(1, cdiv(k, 16)));
+  const int64_t kps = cdiv(cdiv(k, S), 16) * 16;
+  S = (int)cdiv(k, kps);
+  rc = gemm_simt<double, double, double, df32>(st, k, k, k, a.Rinv, k, 1, a.Rinv, 1, k, a.gram_part, k, 1, S,
+                                               (int64_t)k * k);
   if (rc) return rc;
-  return gemm_simt<double, df32, float, df32>(st, k, m, k, a.Ginv, k, 1, reinterpret_cast<const df32*>(a.Lk), 1,
-                                              k, reinterpret_cast<float*>(a.W), m, 1);
+  df32* Ginv = reinterpret_cast<df32*>(a.Ginv);
+  k_sum_slices_df<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>((int64_t)k * k, S, a.gram_part, Ginv);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return gemm_simt<df32, df32, float, df32>(st, k, m, k, Ginv, k, 1, reinterpret_cast<const df32*>(a.Lk), 1, k,
+                                            reinterpret_cast<float*>(a.W), m, 1);
 }
 
 // ---------------------------------------------------------------------------

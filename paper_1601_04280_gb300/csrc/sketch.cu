@@ -564,17 +564,20 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_dense_tma(const TA* __restrict
         for (int e = s0; e < s1; ++e) {
           const uint32_t ent = lsrc[e];
           const int off = (int)(ent & 0x7fffffffu);
-          const bool neg = (ent >> 31) != 0;
+          const TACC sg = (ent >> 31) ? TACC(-1) : TACC(1);
+          // a NaN or Inf entry makes its bucket sum non-finite: checked once per
+          // bucket when the row group is complete, not per element
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const TACC v = load_acc(tile + r * chunk + off, TACC(0));
-            if (r < rows) bad |= !isfinite(v);
-            acc[q][r] += neg ? -v : v;
-          }
+          for (int r = 0; r < R; ++r) acc[q][r] = fma(sg, load_acc(tile + r * chunk + off, TACC(0)), acc[q][r]);
         }
       }
     }
     if (c == nchunks - 1) {
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r < rows && tid + q * NT < l1) bad |= !isfinite(acc[q][r]);
       // Hartley transforms of the finished group's row pairs, pb pairs per batch
       for (int q0 = 0; q0 < R / 2; q0 += pb) {
         const int nbat = min(pb, R / 2 - q0);
