@@ -240,6 +240,12 @@ int rlu_debug_stage_ms(rlu_t h, float* ms, int max_stages, int* count);
 /* Number of CUDA kernels this library has launched in this process so far. */
 int rlu_debug_launch_count(int64_t* out);
 
+/* Test hook: the device FP64 reciprocal used on the Cholesky's dependent chain
+ * (Newton's iteration seeded by the FP32 reciprocal approximation), applied to
+ * n host values x (x > 0), results to host out.  Synchronous.
+ * Errors: RLU_EINVAL, RLU_ENOMEM, RLU_ECUDA. */
+int rlu_debug_recip(const double* x, double* out, int64_t n);
+
 /* ---- sketch without allocation ----
  * No counterpart in the paper: this entry point exists for callers that
  * cannot allocate device memory on their call path — a serving loop that

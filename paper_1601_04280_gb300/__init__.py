@@ -29,7 +29,8 @@ C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_
              "rlu_strerror", "rlu_debug_sketch_params", "rlu_debug_Y", "rlu_debug_B", "rlu_debug_enable",
              "rlu_debug_timing", "rlu_debug_stage_ms", "rlu_debug_launch_count", "rlu_sketch_dense_noalloc",
              "rlu_csr_workspace_bytes", "rlu_set_csr_workspace", "rlu_graph_capture_dense", "rlu_graph_launch",
-             "rlu_graph_destroy", "rlu_copy_block_async", "rlu_set_max_ctas")
+             "rlu_graph_destroy", "rlu_copy_block_async", "rlu_set_max_ctas",
+             "rlu_debug_recip")
 
 #: stage names reported by rlu_debug_stage_ms, in order
 STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
@@ -79,6 +80,7 @@ def load(reload=False):
         "rlu_graph_destroy": ([vp], c.c_int),
         "rlu_copy_block_async": ([vp, i64, vp, i64, i64, i64, vp], c.c_int),
         "rlu_set_max_ctas": ([vp, i32], c.c_int),
+        "rlu_debug_recip": ([vp, vp, i64], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -187,6 +189,15 @@ def rlu_sketch_dense_noalloc(A_ptr, lda, dtype, m, n, l, l1, seed, Y_ptr, status
     """Sketch Y = A S D H R / sqrt(l1) without any allocation (see include/rlu.h)."""
     return load().rlu_sketch_dense_noalloc(A_ptr, lda, dtype, m, n, l, l1, ctypes.c_uint64(seed & (2**64 - 1)),
                                            Y_ptr, status_ptr, stream_ptr)
+
+
+def rlu_debug_recip(x):
+    """The device FP64 reciprocal of the Cholesky step on host values (test hook)."""
+    import numpy as np
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    _check(load().rlu_debug_recip(x.ctypes.data, out.ctypes.data, x.size), "rlu_debug_recip")
+    return out
 
 
 def rlu_debug_launch_count():

@@ -227,6 +227,11 @@ int map_flags(unsigned int f) {
   return RLU_OK;
 }
 
+__global__ void k_debug_recip(int64_t n, const double* x, double* out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = rcp_newton(x[i]);
+}
+
 __global__ void k_status_code(const unsigned int* flags, int32_t* out) {
   unsigned int f = *flags;
   int code = RLU_OK;
@@ -896,6 +901,28 @@ int rlu_debug_launch_count(int64_t* out) {
   if (!out) return RLU_EINVAL;
   *out = (int64_t)rlu::g_launches.load();
   return RLU_OK;
+}
+
+int rlu_debug_recip(const double* x, double* out, int64_t n) {
+  if (!x || !out || n < 0) return RLU_EINVAL;
+  if (n == 0) return RLU_OK;
+  double* d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * 2 * n) != cudaSuccess) {
+    cudaGetLastError();
+    return RLU_ENOMEM;
+  }
+  int rc = RLU_OK;
+  if (cudaMemcpy(d, x, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess) rc = RLU_ECUDA;
+  if (!rc) {
+    k_debug_recip<<<(unsigned)cdiv(n, 256), 256>>>(n, d, d + n);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(out, d + n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = RLU_ECUDA;
+  }
+  cudaFree(d);
+  cudaGetLastError();
+  return rc;
 }
 
 int rlu_debug_enable(rlu_t h, int on) {

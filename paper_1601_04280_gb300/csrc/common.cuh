@@ -35,7 +35,11 @@ __device__ __forceinline__ void red_release_gpu_add(unsigned int* p, unsigned in
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide barrier for cooperative (co-resident) launches.  `counter` starts
+// Grid-wide barrier for cooperative (co-resident) launches.  Arrival is a
+// release reduction by one thread after a CTA barrier (release is cumulative:
+// writes of the other threads, ordered before it by the CTA barrier, become
+// visible to every thread that acquires the counter), so no separate full fence
+// is needed.  `counter` starts
 // at zero for the launch; barrier number e (1, 2, ...) waits until all
 // gridDim.x blocks have arrived e times.  The wait is bounded: on timeout it
 // sets FLAG_TIMEOUT and returns false, and the caller must leave the kernel.
@@ -45,8 +49,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    red_release_gpu_add(counter, 1u);
+    red_release_gpu_add(counter, 1u);  // release: the CTA's writes before the __syncthreads come with it
     const unsigned int target = epoch * gridDim.x;
     long long t0 = clock64();
     int ok = 1;
@@ -71,10 +74,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int
 // have arrived e times, or false after the bounded wait (FLAG_TIMEOUT).
 __device__ __forceinline__ void grid_arrive(unsigned int* counter) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    red_release_gpu_add(counter, 1u);
-  }
+  if (threadIdx.x == 0) red_release_gpu_add(counter, 1u);
 }
 
 __device__ __forceinline__ bool grid_wait(unsigned int* counter, unsigned int epoch, unsigned int* status) {
@@ -238,6 +238,23 @@ template <> struct Cvt<df32> {
 template <typename To, typename F> __device__ __forceinline__ To cvt(F x) { return Cvt<To>::f(x); }
 template <typename T> __device__ __forceinline__ T zero_() { return cvt<T>(0.0); }
 template <typename T> __device__ __forceinline__ T one_() { return cvt<T>(1.0); }
+
+// Reciprocal of a positive FP64 value by Newton's iteration r <- r (2 - x r)
+// (written as r + r (1 - x r)), seeded by the FP32 hardware reciprocal
+// approximation: two steps take the seed's ~2^-22 relative error to below
+// 2^-52, with four dependent FMAs instead of a full-precision division on a
+// latency-bound chain.  Outside the FP32 exponent range it falls back to the
+// division.
+__device__ __forceinline__ double rcp_newton(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / x;
+  float s;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"((float)x));
+  double r = (double)s;
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
 
 // Process-wide count of kernels this library has launched (a test hook).
 void note_launch(int count = 1);

@@ -29,7 +29,7 @@ __global__ void k_extract_Lk(int64_t m, int l, int k, const double* __restrict__
 
 // Blocked right-looking Cholesky G = R^T R (R upper, overwriting the upper
 // triangle of S), then R^{-1}; one cooperative kernel, FP64, with three grid
-// barriers per 32-wide panel.
+// barriers per 32-wide panel and two more before the column solves of R^{-1}.
 constexpr int kNb = 32;
 
 __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S, double* __restrict__ Rinv,
@@ -40,8 +40,6 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
   // solves, with reciprocals of the diagonal computed once per block.
   __shared__ double blk[kNb][kNb + 1];
   __shared__ double rdiag[kNb];
-  __shared__ df32 tA[kNb][kNb + 1];
-  __shared__ df32 tB[kNb][kNb + 1];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   constexpr int NW = 8;
@@ -54,7 +52,11 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
   for (int J = 0; J < nt; ++J) {
     const int c0 = J * kNb;
     const int jb = min(kNb, k - c0);
-    // (a) diagonal block by CTA 0, right-looking, all threads
+    // (a) diagonal block by CTA 0, right-looking, all threads, in the form
+    // G = U^T D^{-1} U (U = D R): column c only needs 1 / g_cc (every thread
+    // takes it from the pivot in shared memory, no serial step), the update
+    // g_rt -= g_cr g_ct / g_cc runs on unscaled rows, and the square roots and
+    // the row scaling R[c][t] = g_ct / sqrt(g_cc) wait until the block is done.
     if (blockIdx.x == 0) {
       for (int e = tid; e < kNb * kNb; e += blockDim.x) {
         int r = e / kNb, c = e % kNb;
@@ -62,28 +64,26 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
       }
       __syncthreads();
       for (int c = 0; c < jb; ++c) {
-        if (tid == 0) {
-          double d = blk[c][c];
-          if (!(d > 0.0)) {
-            set_flag(status, FLAG_ZERO_PIVOT);
-            d = 1.0;
-          }
-          d = sqrt(d);
-          blk[c][c] = d;
-          rdiag[c] = 1.0 / d;
-        }
-        __syncthreads();
-        if (tid > c && tid < jb) blk[c][tid] *= rdiag[c];
-        __syncthreads();
+        const double piv = blk[c][c];
+        const double inv = (piv > 0.0) ? rcp_newton(piv) : 0.0;
         for (int e = tid; e < kNb * kNb; e += blockDim.x) {
-          int r = e / kNb, t = e % kNb;
-          if (r > c && t >= r && t < jb) blk[r][t] -= blk[c][r] * blk[c][t];
+          const int r = e / kNb, t = e % kNb;
+          if (r > c && t >= r && t < jb) blk[r][t] = fma(-blk[c][r] * inv, blk[c][t], blk[r][t]);
         }
         __syncthreads();
       }
+      if (tid < jb) {
+        double d = blk[tid][tid];
+        if (!(d > 0.0)) {
+          set_flag(status, FLAG_ZERO_PIVOT);
+          d = 1.0;
+        }
+        rdiag[tid] = 1.0 / sqrt(d);
+      }
+      __syncthreads();
       for (int e = tid; e < jb * jb; e += blockDim.x) {
         int r = e / jb, c = e % jb;
-        S[(int64_t)(c0 + r) * k + c0 + c] = (c >= r) ? blk[r][c] : 0.0;
+        S[(int64_t)(c0 + r) * k + c0 + c] = (c >= r) ? blk[r][c] * rdiag[r] : 0.0;
       }
     }
     if (!grid_barrier(bar, ++epoch, status)) return;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
       double rcol[kNb];  // rcol[t] = R_JJ[t][lane]
 #pragma unroll
       for (int t = 0; t < kNb; ++t) rcol[t] = (t < jb && lane < jb) ? S[(int64_t)(c0 + t) * k + c0 + lane] : 0.0;
-      const double rinv_l = (lane < jb) ? 1.0 / S[(int64_t)(c0 + lane) * k + c0 + lane] : 1.0;
+      const double rinv_l = (lane < jb) ? rcp_newton(S[(int64_t)(c0 + lane) * k + c0 + lane]) : 1.0;
       for (int64_t col = gwarp; col < rest; col += nwarps) {
         const int gc = c0 + jb + (int)col;
         double b = (lane < jb) ? S[(int64_t)(c0 + lane) * k + gc] : 0.0;
@@ -126,80 +126,34 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
       if (!grid_barrier(bar, ++epoch, status)) return;
     }
   }
-  // R^{-1} (upper) by 32 x 32 blocks: the diagonal blocks X_JJ = R_JJ^{-1}
-  // (FP64, warp per column: lane t finalizes x_t from the bottom up), then
-  // block diagonal d = 1, 2, ... (one grid barrier each), in float-float:
-  //   X_{I,I+d} = -X_II * sum_{K=I+1}^{I+d} R_{I,K} X_{K,I+d}.
-  for (int J = blockIdx.x; J < nt; J += gridDim.x) {
-    const int c0 = J * kNb;
-    const int jb = min(kNb, k - c0);
-    double rrow[kNb];  // rrow[t] = R_JJ[lane][t]
-#pragma unroll
-    for (int t = 0; t < kNb; ++t) rrow[t] = (t < jb && lane < jb) ? S[(int64_t)(c0 + lane) * k + c0 + t] : 0.0;
-    const double rinv_l = (lane < jb) ? 1.0 / S[(int64_t)(c0 + lane) * k + c0 + lane] : 1.0;
-    for (int c = warp; c < jb; c += NW) {
-      double b = (lane == c) ? 1.0 : 0.0;
-      double xl = 0.0;
-#pragma unroll
-      for (int t = kNb - 1; t >= 0; --t) {
-        const double xt_local = (lane == t && t <= c) ? b * rinv_l : 0.0;
-        const double xt = __shfl_sync(0xffffffffu, xt_local, t);
-        if (lane == t) xl = xt;
-        if (lane < t) b -= rrow[t] * xt;
-      }
-      if (lane < jb) Rinv[(int64_t)(c0 + lane) * k + c0 + c] = (lane <= c) ? xl : 0.0;
-    }
-  }
-  // zero the strictly lower blocks of R^{-1}
+  // R^{-1} column by column, FP64: column j solves R x = e_j from the bottom
+  // up, one warp per column; the working vector lives in this warp's part of
+  // shared memory.  R's columns are first copied, transposed, into the free
+  // strictly lower triangle of S (S[t][i] = R[i][t], i < t), so that the
+  // update with column t reads contiguous memory.
+  if (!grid_barrier(bar, ++epoch, status)) return;
   for (int64_t e = gtid; e < (int64_t)k * k; e += gthreads) {
-    const int64_t r = e / k, c = e - r * k;
-    if (r / kNb > c / kNb) Rinv[e] = 0.0;
+    const int t = (int)(e / k), i = (int)(e - (int64_t)t * k);
+    if (i < t) S[(int64_t)t * k + i] = S[(int64_t)i * k + t];
   }
-  for (int d = 1; d < nt; ++d) {
-    if (!grid_barrier(bar, ++epoch, status)) return;
-    for (int I = blockIdx.x; I + d < nt; I += gridDim.x) {
-      const int r0 = I * kNb, cc0 = (I + d) * kNb;
-      const int rb = min(kNb, k - r0), cb = min(kNb, k - cc0);
-      df32 acc[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = df_make(0.f, 0.f);
-      for (int K = I + 1; K <= I + d; ++K) {
-        const int t0 = K * kNb, tb = min(kNb, k - t0);
-        __syncthreads();
-        for (int e = tid; e < kNb * kNb; e += blockDim.x) {
-          int r = e / kNb, c = e % kNb;
-          tA[r][c] = df_from_double((r < rb && c < tb) ? S[(int64_t)(r0 + r) * k + t0 + c] : 0.0);
-          tB[r][c] = df_from_double((r < tb && c < cb) ? Rinv[(int64_t)(t0 + r) * k + cc0 + c] : 0.0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int e = tid + q * 256, r = e / kNb, c = e % kNb;
-#pragma unroll 8
-          for (int t = 0; t < kNb; ++t) acc[q] = mad(tA[r][t], tB[t][c], acc[q]);
-        }
-      }
-      __syncthreads();
-      for (int e = tid; e < kNb * kNb; e += blockDim.x) {
-        int r = e / kNb, c = e % kNb;
-        tA[r][c] = df_from_double((r < rb && c < rb) ? Rinv[(int64_t)(r0 + r) * k + r0 + c] : 0.0);  // X_II
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = tid + q * 256, r = e / kNb, c = e % kNb;
-        tB[r][c] = acc[q];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = tid + q * 256, r = e / kNb, c = e % kNb;
-        df32 s2 = df_make(0.f, 0.f);
-#pragma unroll 8
-        for (int t = 0; t < kNb; ++t) s2 = mad(tA[r][t], tB[t][c], s2);
-        if (r < rb && c < cb) Rinv[(int64_t)(r0 + r) * k + cc0 + c] = -to_double(s2);
-      }
-      __syncthreads();
+  if (!grid_barrier(bar, ++epoch, status)) return;
+  extern __shared__ __align__(16) unsigned char chol_smem[];
+  double* rdg = reinterpret_cast<double*>(chol_smem);                     // k: 1 / R[i][i]
+  double* xw = rdg + k + (size_t)warp * k;                                 // k per warp
+  for (int i = tid; i < k; i += blockDim.x) rdg[i] = 1.0 / S[(int64_t)i * k + i];
+  __syncthreads();
+  for (int64_t j = gwarp; j < k; j += nwarps) {
+    for (int i = lane; i <= j; i += 32) xw[i] = (i == j) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int t = (int)j; t >= 0; --t) {
+      const double xt = xw[t] * rdg[t];  // every lane, same value
+      const double* rt = S + (int64_t)t * k;               // rt[i] = R[i][t], i < t
+      for (int i = lane; i < t; i += 32) xw[i] = fma(-xt, rt[i], xw[i]);
+      if (lane == 0) xw[t] = xt;
+      __syncwarp();
     }
+    for (int i = lane; i < k; i += 32) Rinv[(int64_t)i * k + j] = (i <= j) ? xw[i] : 0.0;
+    __syncwarp();
   }
 }
 
@@ -238,7 +192,8 @@ int launch_gram(const PinvArgs& a, cudaStream_t st) {
 int launch_chol(const PinvArgs& a, cudaStream_t st) {
   const int k = a.k;
   RLU_CUDA_TRY(cudaMemsetAsync(a.bar, 0, sizeof(unsigned int), st));
-  const size_t smem = 0;
+  const size_t smem = (size_t)9 * k * sizeof(double);  // 1/diag(R) and one k-vector per warp (R^{-1} columns)
+  if (int rc_ = allow_dynamic_smem((const void*)k_chol_inv, smem)) return rc_;
   int per_sm = 0;
   RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_inv, 256, smem));
   if (per_sm < 1) return RLU_EINVAL;

@@ -52,6 +52,9 @@ __device__ __forceinline__ bool cand_better(unsigned long long ka, int pa, unsig
 }
 
 template <typename T> __device__ __forceinline__ T recip(T x) { return one_<T>() / x; }
+// FP64: Newton's reciprocal (a few dependent FMAs on the slow FP64 pipe instead
+// of a full division), with the sign restored.
+template <> __device__ __forceinline__ double recip<double>(double x) { return copysign(rcp_newton(fabs(x)), x); }
 
 // Load through L2 only (values written by other CTAs in this launch).
 template <typename T> __device__ __forceinline__ T ldcg_(const T* p) { return __ldcg(p); }
@@ -70,7 +73,7 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
                                                    int64_t cs, int steps, int64_t rpc, int32_t* __restrict__ pos_out,
                                                    int32_t* __restrict__ pstep_out, int64_t* __restrict__ perm_out,
                                                    Cand* __restrict__ cand, T* __restrict__ candrow,
-                                                   unsigned int* bar, unsigned int* status) {
+                                                   unsigned int* bar, unsigned int* status, int defer) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = NT / 32;
   const int G = gridDim.x;
@@ -80,11 +83,18 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
   const int rp = (int)rpc;
   // shared layout
   T* slab = reinterpret_cast<T*>(smem);                               // nr x cols (SMEM variant)
-  T* urow2 = slab + (SMEM ? (size_t)rp * cols : 0);                   // 2 x cols: pivot rows, by step parity
-  T* lval = urow2 + 2 * (size_t)cols;                                 // rpc
-  int32_t* lpos = reinterpret_cast<int32_t*>(lval + rp);              // rpc
+  // Pivot rows live in a ring of D + 1 slots (step t in slot t mod (D + 1)) and
+  // the multipliers of the pending steps in D columns of lhist (step t in
+  // column t mod D): the global-memory variant defers the trailing update and
+  // applies D steps at once (D = 1 in shared memory: every step at once).
+  const int D = SMEM ? 1 : defer;
+  const int RU = D + 1;
+  T* ring = slab + (SMEM ? (size_t)rp * cols : 0);                    // RU x cols
+  T* lhist = ring + (size_t)RU * cols;                                // D x rpc
+  int32_t* lpos = reinterpret_cast<int32_t*>(lhist + (size_t)D * rp); // rpc
   int32_t* lstep = lpos + rp;                                         // rpc
-  int32_t* pwin = lstep + rp;                                         // steps
+  int32_t* ldone = lstep + rp;                                        // rpc: last step applied to the whole row
+  int32_t* pwin = ldone + rp;                                         // steps
   __shared__ unsigned long long red_v[NW];
   __shared__ int red_p[NW];
   __shared__ int red_r[NW];
@@ -112,6 +122,7 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
   for (int r = tid; r < rp; r += NT) {
     lpos[r] = (int32_t)(r0 + r);
     lstep[r] = -1;
+    ldone[r] = -1;
   }
   for (int t = tid; t < steps; t += NT) pwin[t] = t;
   if (tid == 0) s_stop = 0;
@@ -144,7 +155,8 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
           cd.row = s_rstar < 0 ? -1 : (int)(r0 + s_rstar);
           if (s_rstar < 0) { cd.key = 0ull; cd.pos = 0x7fffffff; }
           cand[(j & 1) * G + blockIdx.x] = cd;
-          __threadfence();
+          // release (cumulative): this record and the workers' candidate row,
+          // ordered before it by barrier 2, are visible to whoever acquires
           red_release_gpu_add(bar, 1u);
         }
       }
@@ -202,7 +214,7 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
         break;
       }
       // the pivot row (the winner's published values of columns j..cols-1)
-      T* ub = urow2 + (size_t)(j & 1) * cols;
+      T* ub = ring + (size_t)(j % RU) * cols;
       {
         const T* src = candrow + ((size_t)(j & 1) * G + bc) * cols;
         for (int c = j + lane; c < cols; c += 32) ub[c - j] = ldcg_(src + (c - j));
@@ -272,65 +284,77 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
       write_candrow(0);
       bar_arrive(2, NT);
     }
+    int F = -1;  // last step whose update every row has received (columns >= its look-ahead)
     for (int j = 0; j < steps; ++j) {
       bar_sync(1, NT);  // pivot row and bookkeeping of step j are in place
       if (s_stop) break;
       const bool zero = s_zero != 0;
       const T rpiv = s_rpiv;
-      const T* ub = urow2 + (size_t)(j & 1) * cols;
       const bool more = j + 1 < steps;
+      T* lj = lhist + (size_t)(j % D) * rp;  // multipliers of step j
+      // row r has every step up to max(F, ldone[r]) in its columns j+1..; the
+      // pending ones, oldest first: t in (max(F, ldone[r]), j]
+      auto pend_apply = [&](int r, int c, T x) -> T {
+        if (SMEM) return mad(-lj[r], ring[(size_t)(j % RU) * cols + (c - j)], x);  // D = 1: step j only
+        const int t0 = max(F, (int)ldone[r]) + 1;
+        int sl = t0 % D, su = t0 % RU;  // ring slots of step t0, advanced without divisions
+        for (int t = t0; t <= j; ++t) {
+          x = mad(-lhist[(size_t)sl * rp + r], ring[(size_t)su * cols + (c - t)], x);
+          if (++sl == D) sl = 0;
+          if (++su == RU) su = 0;
+        }
+        return x;
+      };
       // column j below the pivot (l = x / pivot), then column j+1 (look-ahead),
       // and the best candidate of column j+1 among this CTA's rows
       unsigned long long bv = 0ull;
       int bp = 0x7fffffff, br = -1;
-      {
-        const T u1 = (j + 1 < cols) ? ub[1] : zero_<T>();
-        for (int r = tw; r < nr; r += NTW) {
-          if (lstep[r] < 0) {
-            if (!zero) {
-              const T lv = at(r, j) * rpiv;
-              at(r, j) = lv;
-              lval[r] = lv;
-              if (j + 1 < cols) {
-                T& x = at(r, j + 1);
-                x = mad(-lv, u1, x);
-              }
-            }
-            if (more) {
-              const unsigned long long v = mag_key(at(r, j + 1));
-              const int p = lpos[r];
-              if (cand_better(v, p, bv, bp)) { bv = v; bp = p; br = r; }
-            }
+      for (int r = tw; r < nr; r += NTW) {
+        if (lstep[r] < 0) {
+          T lv = zero_<T>();
+          if (!zero) {
+            lv = at(r, j) * rpiv;
+            at(r, j) = lv;
+          }
+          lj[r] = lv;  // a zero pivot contributes no update
+          if (j + 1 < cols) at(r, j + 1) = pend_apply(r, j + 1, at(r, j + 1));
+          if (more) {
+            const unsigned long long v = mag_key(at(r, j + 1));
+            const int p = lpos[r];
+            if (cand_better(v, p, bv, bp)) { bv = v; bp = p; br = r; }
           }
         }
       }
       int rstar = -1;
       if (more) {
-        reduce_cand(bv, bp, br);  // ends with a worker barrier: lval and column j+1 are complete
+        reduce_cand(bv, bp, br);  // ends with a worker barrier: lhist and column j+1 are complete
         rstar = s_rstar;
         // the candidate row is brought fully up to date before it is published
-        if (!zero && rstar >= 0) {
-          for (int c = j + 2 + tw; c < cols; c += NTW) {
-            T& x = at(rstar, c);
-            x = mad(-lval[rstar], ub[c - j], x);
-          }
-        }
+        if (rstar >= 0)
+          for (int c = j + 2 + tw; c < cols; c += NTW) at(rstar, c) = pend_apply(rstar, c, at(rstar, c));
         bar_sync(3, NTW);
+        if (tw == 0 && rstar >= 0) ldone[rstar] = j;
         write_candrow(j + 1);
         bar_arrive(2, NT);
       } else {
         bar_sync(3, NTW);
       }
-      // the rest of the rank-1 update (columns j+2.., rows other than rstar)
+      // the trailing update of the pending steps (columns j+2.., every row not
+      // yet brought up to date): every step in shared memory, every D steps
+      // (and at the last step) in global memory
+      const bool flush = (j - F >= D) || !more;
       const int c0 = j + 2;
-      if (!zero && c0 < cols) {
+      if (flush && c0 < cols) {
         if (SMEM) {
-          for (int r = wk; r < nr; r += NWK) {
-            if (lstep[r] < 0 && r != rstar) {
-              const T lv = -lval[r];
-              for (int c = c0 + lane; c < cols; c += 32) {
-                T& x = at(r, c);
-                x = mad(lv, ub[c - j], x);
+          const T* ub = ring + (size_t)(j % RU) * cols;
+          if (!zero) {
+            for (int r = wk; r < nr; r += NWK) {
+              if (lstep[r] < 0 && r != rstar) {
+                const T lv = -lj[r];
+                for (int c = c0 + lane; c < cols; c += 32) {
+                  T& x = at(r, c);
+                  x = mad(lv, ub[c - j], x);
+                }
               }
             }
           }
@@ -351,15 +375,18 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
               if (row_fast) { r = idx % nr; c = idx / nr; } else { c = idx % width; r = idx / width; }
               rr[u] = r;
               cc[u] = c0 + c;
-              act[u] = idx < tot && lstep[r < nr ? r : 0] < 0 && r != rstar;
+              // rstar was brought up to date above (its watermark is set by one
+              // thread and is not yet visible to all): excluded by index
+              act[u] = idx < tot && r != rstar && lstep[r < nr ? r : 0] < 0 && ldone[r < nr ? r : 0] < j;
               if (act[u]) xv[u] = at(r, c0 + c);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-              if (act[u]) at(rr[u], cc[u]) = mad(-lval[rr[u]], ub[cc[u] - j], xv[u]);
+              if (act[u]) at(rr[u], cc[u]) = pend_apply(rr[u], cc[u], xv[u]);
           }
         }
       }
+      if (flush) F = j;
     }
   }
   __syncthreads();
@@ -381,11 +408,22 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
   }
 }
 
+// Shared memory: the slab (shared-memory variant), D + 1 pivot rows, D columns
+// of multipliers, and per-row position, pivot step and watermark.
 template <typename T, bool SMEM>
-static size_t pivlu_smem(int64_t rpc, int cols, int steps) {
-  size_t b = (SMEM ? (size_t)rpc * cols * sizeof(T) : 0) + 2 * (size_t)cols * sizeof(T) + (size_t)rpc * sizeof(T) +
-             (size_t)rpc * 8 + (size_t)steps * 4;
+static size_t pivlu_smem(int64_t rpc, int cols, int steps, int D) {
+  size_t b = (SMEM ? (size_t)rpc * cols * sizeof(T) : 0) + (size_t)(D + 1) * cols * sizeof(T) +
+             (size_t)D * rpc * sizeof(T) + (size_t)rpc * 12 + (size_t)steps * 4;
   return (b + 15) & ~(size_t)15;
+}
+
+// Deferral depth of the global-memory variant: up to 16 steps per pass over
+// the trailing block, as many as fit in the shared-memory budget.
+template <typename T>
+static int pivlu_defer(int64_t rpc, int cols, int steps, size_t budget) {
+  int D = 16;
+  while (D > 1 && pivlu_smem<T, false>(rpc, cols, steps, D) > budget) --D;
+  return D;
 }
 
 template <typename T, bool SMEM>
@@ -393,7 +431,8 @@ static int launch_cfg(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int 
                       unsigned int* status, cudaStream_t st) {
   constexpr int NT = SMEM ? 256 : 1024;
   const int64_t rpc = cdiv(rows, G);
-  size_t smem = pivlu_smem<T, SMEM>(rpc, cols, steps);
+  int defer = SMEM ? 1 : pivlu_defer<T>(rpc, cols, steps, 200 * 1024);
+  size_t smem = pivlu_smem<T, SMEM>(rpc, cols, steps, defer);
   auto kern = k_pivoted_lu<T, SMEM, NT>;
   if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
   int per_sm = 0;
@@ -403,7 +442,7 @@ static int launch_cfg(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int 
   Cand* cand = reinterpret_cast<Cand*>(ws.cand);
   T* candrow = reinterpret_cast<T*>(ws.candrow);
   void* args[] = {&X, &rows, &cols, &rs, &cs, &steps, (void*)&rpc, &ws.pos, &ws.pstep, &ws.perm,
-                  &cand, &candrow, &ws.bar, &status};
+                  &cand, &candrow, &ws.bar, &status, &defer};
   RLU_CUDA_TRY(launch_cooperative((void*)kern, G, NT, args, smem, st));
   note_launch();
   return RLU_OK;
@@ -419,7 +458,7 @@ int launch_pivoted_lu(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int 
   int G = (int)min64(num_sms, cdiv(rows, 8));
   if (G > ws.max_ctas) G = ws.max_ctas;
   const int64_t rpc = cdiv(rows, G);
-  size_t smem = pivlu_smem<T, true>(rpc, cols, steps);
+  size_t smem = pivlu_smem<T, true>(rpc, cols, steps, 1);
   if (smem <= 200 * 1024) return launch_cfg<T, true>(X, rows, cols, rs, cs, steps, G, ws, status, st);
   return launch_cfg<T, false>(X, rows, cols, rs, cs, steps, G, ws, status, st);
 }

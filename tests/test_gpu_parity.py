@@ -297,3 +297,45 @@ def test_host_and_async_entry_points_match(rg):
     h.factor_host(Ah, oh)
     for a, b, c in zip((ref.L, ref.U, ref.p, ref.q), outs, oh):
         assert torch.equal(a.cpu(), b.cpu()) and torch.equal(a.cpu(), c)
+
+
+def test_newton_reciprocal_within_two_ulp(rg):
+    """The FP64 reciprocal of the Cholesky's critical path (Newton's iteration
+    from the FP32 approximation) against the correctly rounded 1/x, across the
+    range it serves and the range where it falls back to the division."""
+    rng = np.random.default_rng(17)
+    x = np.concatenate([10.0 ** rng.uniform(-29.5, 29.5, 200000), 10.0 ** rng.uniform(-300, -31, 1000),
+                        10.0 ** rng.uniform(31, 300, 1000), [1.0, 2.0, 3.0, 0.1, 1e-30, 1e30, 7.0 / 3.0]])
+    r = rg.rlu_debug_recip(x)
+    ref = 1.0 / x
+    ulp = np.spacing(np.abs(ref))
+    assert np.all(np.abs(r - ref) <= 2 * ulp), np.max(np.abs(r - ref) / ulp)
+
+
+# Tall panels whose rows per CTA do not fit in shared memory take the
+# global-memory LU, which defers the trailing update and applies up to 16 steps
+# per pass (the same multiply-adds in the same order, only later).
+def test_global_memory_lu_of_Y_f64(rg):
+    m, n, k, l, l1 = 60000, 800, 100, 240, 1920
+    A = ri.dense_low_rank_plus_noise(m, n, 120, 1e-3, seed=31, dtype=np.float64)
+    o = oracle.factor(A, k, l, l1, seed=94)
+    g = run(rg, A, k, l, l1, 94, "f64", torch.float64)
+    assert g["status"] == 0
+    check_structure(g, m, n, k)
+    check_pivots(g, o, k)
+    e_o = oracle.relative_residual(A, o.L, o.U, o.p, o.q)
+    e_g = oracle.relative_residual(A, g["L"], g["U"], g["p"], g["q"])
+    assert abs(e_g - e_o) <= 1e-12, (e_g, e_o)
+
+
+def test_global_memory_lu_of_B_f32(rg):
+    m, n, k, l, l1 = 3000, 40000, 150, 170, 1360
+    A = ri.dense_low_rank_plus_noise(m, n, 150, 1e-6, seed=32)
+    o = oracle.factor(A.astype(np.float64), k, l, l1, seed=95)
+    g = run(rg, A, k, l, l1, 95, "f32", torch.float32)
+    assert g["status"] == 0
+    check_structure(g, m, n, k)
+    check_pivots(g, o, k)
+    e_o = oracle.relative_residual(A, o.L, o.U, o.p, o.q)
+    e_g = oracle.relative_residual(A, g["L"], g["U"], g["p"], g["q"])
+    assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
