@@ -19,6 +19,8 @@
 #include "common.cuh"
 #include "sketch.cuh"
 
+#include <type_traits>
+
 namespace rlu {
 
 // ---------------------------------------------------------------------------
@@ -324,7 +326,8 @@ __global__ void __launch_bounds__(NT) k_sketch_dense(const TA* __restrict__ A, i
                                                      const uint32_t* __restrict__ blist,
                                                      const float* __restrict__ dsign, const int32_t* __restrict__ Rsel,
                                                      const typename C2<TACC>::t* __restrict__ tw, FftPlan plan,
-                                                     double* __restrict__ Y, unsigned int* status) {
+                                                     double* __restrict__ Y, const int32_t* __restrict__ rowmap,
+                                                     unsigned int* status) {
   using V = typename C2<TACC>::t;
   extern __shared__ __align__(16) unsigned char smem[];
   TA* tile = reinterpret_cast<TA*>(smem);
@@ -426,8 +429,8 @@ __global__ void __launch_bounds__(NT) k_sketch_dense(const TA* __restrict__ A, i
         const V z = src[f], w = src[fm];
         const TACC h1 = TACC(0.5) * ((z.x + w.x) - (z.y - w.y));
         const TACC h2 = TACC(0.5) * ((z.x - w.x) + (z.y + w.y));
-        if (ra < m) Y[ra * l + cidx] = (double)(h1 * scale);
-        if (rb < m) Y[rb * l + cidx] = (double)(h2 * scale);
+        if (ra < m) Y[(rowmap ? (int64_t)rowmap[ra] : ra) * l + cidx] = (double)(h1 * scale);
+        if (rb < m) Y[(rowmap ? (int64_t)rowmap[rb] : rb) * l + cidx] = (double)(h2 * scale);
       }
     }
   }
@@ -483,7 +486,7 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_dense_tma(const TA* __restrict
                                                          const int32_t* __restrict__ Rsel,
                                                          const typename C2<TACC>::t* __restrict__ tw, FftPlan plan,
                                                          int pb, int lists_in_smem, double* __restrict__ Y,
-                                                         unsigned int* status) {
+                                                         const int32_t* __restrict__ rowmap, unsigned int* status) {
   using V = typename C2<TACC>::t;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[2];
@@ -620,8 +623,8 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_dense_tma(const TA* __restrict
           const V z = zz[f], w = zz[fm];
           const TACC h1 = TACC(0.5) * ((z.x + w.x) - (z.y - w.y));
           const TACC h2 = TACC(0.5) * ((z.x - w.x) + (z.y + w.y));
-          if (2 * q2 < rows) Y[ra * l + cidx] = (double)(h1 * scale);
-          if (2 * q2 + 1 < rows) Y[rb * l + cidx] = (double)(h2 * scale);
+          if (2 * q2 < rows) Y[(rowmap ? (int64_t)rowmap[ra] : ra) * l + cidx] = (double)(h1 * scale);
+          if (2 * q2 + 1 < rows) Y[(rowmap ? (int64_t)rowmap[rb] : rb) * l + cidx] = (double)(h2 * scale);
         }
       }
 #pragma unroll
@@ -637,15 +640,13 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_dense_tma(const TA* __restrict
 
 // ---------------------------------------------------------------------------
 // CSR sketch.  Rows are split by the host side into light rows (a warp per
-// row) and heavy rows (a whole CTA per row): a warp scatters 32 entries at a
-// time into its row's buckets in shared memory; lanes whose bucket no other
-// lane of the round hits add directly, colliding lanes add one after another
-// in lane order, so every bucket sums its entries in a fixed order.  Heavy
-// rows give each warp a contiguous part of the row and a private bucket
-// array, summed over the warps in warp order, and are also written densely
-// (row-major, n columns) for the tensor-core product.  Then the Hartley
-// transforms of row pairs run as in the dense sketch.
-// ---------------------------------------------------------------------------
+// row) and heavy rows (at least n/4 entries).  A warp scatters 32 entries of
+// a light row at a time into the row's buckets in shared memory; lanes whose
+// bucket no other lane of the round hits add directly, colliding lanes add one
+// after another in lane order, so every bucket sums its entries in a fixed
+// order; then the Hartley transforms of row pairs run as in the dense sketch.
+// Heavy rows are densified (they are needed densely for the tensor-core
+// product anyway) and sketched by the dense kernels.
 template <typename TV, typename TACC>
 __device__ __forceinline__ void csr_scatter_warp(const int32_t* __restrict__ colind, const TV* __restrict__ val,
                                                  int64_t e0, int64_t e1, int64_t n, const uint32_t* __restrict__ hs,
@@ -783,85 +784,43 @@ __global__ void __launch_bounds__(kCsrWarps * 32, 1)
   if (bad_val) set_flag(status, FLAG_NONFINITE);
 }
 
-// Heavy rows: a CTA per pair of rows (list[2p], list[2p+1]); the dense copy of
-// heavy row r of the list goes to D[r * n ...].
-template <typename TV, typename TACC>
-__global__ void __launch_bounds__(kCsrWarps * 32, 1)
-    k_sketch_csr_heavy(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                       const TV* __restrict__ val, int64_t n, const int32_t* __restrict__ list, const int32_t* count,
-                       int l1, int l, const uint32_t* __restrict__ hs, const float* __restrict__ dsign,
-                       const int32_t* __restrict__ Rsel, const typename C2<TACC>::t* __restrict__ tw, FftPlan plan,
-                       TV* __restrict__ D, double* __restrict__ Y, unsigned int* status) {
-  using V = typename C2<TACC>::t;
-  extern __shared__ __align__(16) unsigned char smem[];
-  V* twsm = reinterpret_cast<V*>(smem);
-  V* fbuf = twsm + l1;                                               // [1][2][l1]
-  TACC* yrows = reinterpret_cast<TACC*>(fbuf + (size_t)2 * l1);     // [2][l1]
-  TACC* part = yrows + (size_t)2 * l1;                               // [kCsrWarps][l1]
-  __shared__ int32_t rows[2];
-  __shared__ int first_col[kCsrWarps], last_col[kCsrWarps], warp_inc[kCsrWarps];
-  __shared__ int s_redo;
-  const int warp = threadIdx.x >> 5;
+// Heavy rows: densified, a CTA per row, into D (row i of D = heavy row
+// list[i], n columns; repeated coordinates summed), then sketched by the dense
+// kernels with the row map list.  A row with exactly n strictly increasing
+// columns is a plain copy; otherwise zeros, then stores, and if the columns
+// are not strictly increasing, zeros again and atomic adds.
+template <typename TV>
+__global__ void __launch_bounds__(512) k_csr_densify(const int64_t* __restrict__ rowptr,
+                                                     const int32_t* __restrict__ colind, const TV* __restrict__ val,
+                                                     int64_t n, const int32_t* __restrict__ list, const int32_t* count,
+                                                     TV* __restrict__ D, unsigned int* status) {
   const int nrows = *count;
-  const int npairs = (nrows + 1) / 2;
-  for (int e = threadIdx.x; e < l1; e += blockDim.x) twsm[e] = tw[e];
-  bool bad_csr = false, bad_val = false;
-  for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
-    for (int rr = 0; rr < 2; ++rr) {
+  bool bad_csr = false;
+  for (int i = blockIdx.x; i < nrows; i += gridDim.x) {
+    const int row = list[i];
+    TV* drow = D + (int64_t)i * n;
+    const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
+    if (e1 - e0 != n)
+      for (int64_t c = threadIdx.x; c < n; c += blockDim.x) drow[c] = TV(0);
+    __syncthreads();
+    int inc = 1;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int c = colind[e];
+      if (c < 0 || (int64_t)c >= n) { bad_csr = true; continue; }
+      if (e > e0 && colind[e - 1] >= c) inc = 0;
+      drow[c] = val[e];
+    }
+    if (!__syncthreads_and(inc)) {  // repeated or unordered columns: rebuild with sums
+      for (int64_t c = threadIdx.x; c < n; c += blockDim.x) drow[c] = TV(0);
       __syncthreads();
-      const int li = 2 * p + rr;
-      const int row = li < nrows ? list[li] : -1;
-      if (threadIdx.x == 0) rows[rr] = row;
-      for (int e = threadIdx.x; e < kCsrWarps * l1; e += blockDim.x) part[e] = TACC(0);
-      if (row >= 0) {
-        TV* drow = D + (int64_t)li * n;
-        const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
-        if (e1 - e0 != n)  // not a full row: its dense copy starts from zeros
-          for (int64_t c = threadIdx.x; c < n; c += blockDim.x) drow[c] = TV(0);
-        __syncthreads();
-        const int64_t len = e1 - e0, per = (len + kCsrWarps - 1) / kCsrWarps;
-        const int64_t a = e0 + min64(len, (int64_t)warp * per), b = e0 + min64(len, (int64_t)(warp + 1) * per);
-        bool inc = true;
-        csr_scatter_warp<TV, TACC>(colind, val, a, b, n, hs, part + (size_t)warp * l1, drow, bad_csr, bad_val, &inc);
-        if ((threadIdx.x & 31) == 0) {
-          warp_inc[warp] = inc ? 1 : 0;
-          first_col[warp] = a < b ? colind[a] : -1;
-          last_col[warp] = a < b ? colind[b - 1] : -1;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          // plain stores are right only for strictly increasing columns (no duplicates); a full
-          // row (n entries, no zero-fill) with strictly increasing columns holds exactly 0..n-1
-          int ok = 1;
-          int last = -1;
-          for (int w = 0; w < kCsrWarps; ++w) {
-            if (first_col[w] < 0) continue;
-            ok &= warp_inc[w] && first_col[w] > last;
-            last = last_col[w];
-          }
-          s_redo = ok ? 0 : 1;
-        }
-        __syncthreads();
-        if (s_redo) {  // rebuild the dense copy: zeros, then every entry added (duplicates summed)
-          for (int64_t c = threadIdx.x; c < n; c += blockDim.x) drow[c] = TV(0);
-          __syncthreads();
-          for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const int c = colind[e];
-            if (c >= 0 && (int64_t)c < n) atomicAdd(drow + c, val[e]);
-          }
-        }
-      }
-      __syncthreads();
-      for (int b = threadIdx.x; b < l1; b += blockDim.x) {
-        TACC s = TACC(0);
-        for (int w = 0; w < kCsrWarps; ++w) s += part[(size_t)w * l1 + b];
-        yrows[(size_t)rr * l1 + b] = s;
+      for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int c = colind[e];
+        if (c >= 0 && (int64_t)c < n) atomicAdd(drow + c, val[e]);
       }
     }
-    csr_pairs_fft<TACC>(yrows, 1, rows, l1, l, dsign, Rsel, twsm, fbuf, 1, plan, Y);
+    __syncthreads();
   }
   if (bad_csr) set_flag(status, FLAG_BAD_CSR);
-  if (bad_val) set_flag(status, FLAG_NONFINITE);
 }
 
 template <typename TV, typename TACC>
@@ -889,16 +848,14 @@ static int launch_csr_cfg(const int64_t* rowptr, const int32_t* colind, const TV
     note_launch();
   }
   if (cr.n_heavy > 0) {
-    auto kern = k_sketch_csr_heavy<TV, TACC>;
-    const size_t smem = (size_t)3 * l1 * sizeof(V) + (size_t)(2 + kCsrWarps) * l1 * sizeof(TACC);
-    if (smem > budget) return RLU_EINVAL;
-    if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
-    const int64_t pairs = cdiv(cr.n_heavy, 2);
-    const unsigned grid = (unsigned)min64(pairs, (int64_t)num_sms);
-    kern<<<grid, kCsrWarps * 32, smem, st>>>(rowptr, colind, val, n, cr.heavy, cr.d_count + 1, l1, l, ws.hs,
-                                             ws.dsign, ws.R, tw, ws.plan, D, Y, status);
+    const unsigned grid = (unsigned)min64(cr.n_heavy, (int64_t)num_sms * 4);
+    k_csr_densify<TV><<<grid, 512, 0, st>>>(rowptr, colind, val, n, cr.heavy, cr.d_count + 1, D, status);
     RLU_CUDA_TRY(cudaGetLastError());
     note_launch();
+    const int dt = std::is_same<TV, double>::value ? RLU_F64 : RLU_F32;
+    int rc = launch_sketch_dense(D, n, dt, dt == RLU_F64, cr.n_heavy, n, l1, l, ws, Y, status, num_sms, st,
+                                 cr.heavy);
+    if (rc) return rc;
   }
   return RLU_OK;
 }
@@ -970,7 +927,8 @@ int sketch_chunk_cols(int dtype) {
 
 template <typename TA, typename TACC, int NT, int NB, int R>
 static int launch_dense_tma_cfg(const void* A, int64_t lda, int64_t m, int64_t n, int l1, int l, const SketchWs& ws,
-                                double* Y, unsigned int* status, int num_sms, cudaStream_t st) {
+                                double* Y, const int32_t* rowmap, unsigned int* status, int num_sms,
+                                cudaStream_t st) {
   auto kern = k_sketch_dense_tma<TA, TACC, NT, NB, R>;
   using V = typename C2<TACC>::t;
   const size_t ring = (size_t)2 * R * ws.chunk * sizeof(TA);
@@ -1000,7 +958,7 @@ static int launch_dense_tma_cfg(const void* A, int64_t lda, int64_t m, int64_t n
   const typename C2<TACC>::t* tw;
   if constexpr (sizeof(TACC) == 8) tw = ws.tw64; else tw = ws.tw32;
   kern<<<(unsigned)grid, NT, smem, st>>>(reinterpret_cast<const TA*>(A), lda, m, n, l1, l, ws.chunk, ws.bstart,
-                                         ws.blist, ws.dsign, ws.R, tw, ws.plan, pb, lists_in_smem, Y, status);
+                                         ws.blist, ws.dsign, ws.R, tw, ws.plan, pb, lists_in_smem, Y, rowmap, status);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
   return RLU_OK;
@@ -1008,14 +966,14 @@ static int launch_dense_tma_cfg(const void* A, int64_t lda, int64_t m, int64_t n
 
 template <typename TA, typename TACC, int NT, int NB, int R>
 static int launch_dense_cfg(const void* A, int64_t lda, int64_t m, int64_t n, int l1, int l, const SketchWs& ws,
-                            double* Y, unsigned int* status, int num_sms, cudaStream_t st) {
+                            double* Y, const int32_t* rowmap, unsigned int* status, int num_sms, cudaStream_t st) {
   // TMA-fed kernel when every row segment is a 16-byte-aligned run of 16-byte multiples
   // and the ring plus FFT buffers fit in shared memory
   const bool aligned = ((uintptr_t)A % 16 == 0) && ((lda * (int64_t)sizeof(TA)) % 16 == 0) &&
                        ((n * (int64_t)sizeof(TA)) % 16 == 0) && ((ws.chunk * (int64_t)sizeof(TA)) % 16 == 0);
   const size_t tma_smem = (size_t)2 * R * ws.chunk * sizeof(TA) + (size_t)3 * l1 * sizeof(typename C2<TACC>::t);
   if (aligned && tma_smem <= 220 * 1024)
-    return launch_dense_tma_cfg<TA, TACC, NT, NB, R>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    return launch_dense_tma_cfg<TA, TACC, NT, NB, R>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
   auto kern = k_sketch_dense<TA, TACC, NT, NB, R>;
   size_t tile_bytes = (size_t)R * ws.chunk * sizeof(TA);
   size_t fft_bytes = (size_t)2 * l1 * sizeof(typename C2<TACC>::t);
@@ -1030,34 +988,35 @@ static int launch_dense_cfg(const void* A, int64_t lda, int64_t m, int64_t n, in
   const typename C2<TACC>::t* tw;
   if constexpr (sizeof(TACC) == 8) tw = ws.tw64; else tw = ws.tw32;
   kern<<<(unsigned)grid, NT, smem, st>>>(reinterpret_cast<const TA*>(A), lda, m, n, l1, l, ws.chunk, ws.bstart,
-                                         ws.blist, ws.dsign, ws.R, tw, ws.plan, Y, status);
+                                         ws.blist, ws.dsign, ws.R, tw, ws.plan, Y, rowmap, status);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
   return RLU_OK;
 }
 
 int launch_sketch_dense(const void* A, int64_t lda, int dtype, bool acc64, int64_t m, int64_t n, int l1, int l,
-                        const SketchWs& ws, double* Y, unsigned int* status, int num_sms, cudaStream_t st) {
+                        const SketchWs& ws, double* Y, unsigned int* status, int num_sms, cudaStream_t st,
+                        const int32_t* rowmap) {
   // 1024 threads per CTA; each thread owns NB buckets of R rows in registers
   if (dtype == RLU_F64) {
-    if (l1 <= 2048) return launch_dense_cfg<double, double, 1024, 2, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    if (l1 <= 4096) return launch_dense_cfg<double, double, 1024, 4, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    if (l1 <= 8192) return launch_dense_cfg<double, double, 1024, 8, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    return launch_dense_cfg<double, double, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 2048) return launch_dense_cfg<double, double, 1024, 2, 4>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
+    if (l1 <= 4096) return launch_dense_cfg<double, double, 1024, 4, 4>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
+    if (l1 <= 8192) return launch_dense_cfg<double, double, 1024, 8, 2>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
+    return launch_dense_cfg<double, double, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
   }
   if (acc64) return RLU_EINVAL;
   if (dtype == RLU_F32) {
-    if (l1 <= 2048) return launch_dense_cfg<float, float, 1024, 2, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    if (l1 <= 4096) return launch_dense_cfg<float, float, 1024, 4, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    if (l1 <= 8192) return launch_dense_cfg<float, float, 1024, 8, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    return launch_dense_cfg<float, float, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 2048) return launch_dense_cfg<float, float, 1024, 2, 8>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
+    if (l1 <= 4096) return launch_dense_cfg<float, float, 1024, 4, 8>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
+    if (l1 <= 8192) return launch_dense_cfg<float, float, 1024, 8, 4>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
+    return launch_dense_cfg<float, float, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
   }
   if (dtype == RLU_BF16) {
     using B = __nv_bfloat16;
-    if (l1 <= 2048) return launch_dense_cfg<B, float, 1024, 2, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    if (l1 <= 4096) return launch_dense_cfg<B, float, 1024, 4, 8>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    if (l1 <= 8192) return launch_dense_cfg<B, float, 1024, 8, 4>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
-    return launch_dense_cfg<B, float, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, status, num_sms, st);
+    if (l1 <= 2048) return launch_dense_cfg<B, float, 1024, 2, 8>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
+    if (l1 <= 4096) return launch_dense_cfg<B, float, 1024, 4, 8>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
+    if (l1 <= 8192) return launch_dense_cfg<B, float, 1024, 8, 4>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
+    return launch_dense_cfg<B, float, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
   }
   return RLU_EINVAL;
 }

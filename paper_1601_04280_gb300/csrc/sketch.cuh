@@ -44,8 +44,11 @@ int launch_sketch_params(const SketchWs& ws, int64_t n, int l1, int l, uint64_t 
 int launch_twiddles(int N, double2* tw64, float2* tw32, cudaStream_t st);
 // exclusive scan of count int32 values into count + 1 offsets (one CTA)
 int launch_scan_i32(int64_t count, const int32_t* cnt, int32_t* start, cudaStream_t st);
+// Dense sketch of the m rows of A; row i of the result goes to Y row rowmap[i]
+// (row i when rowmap is null).
 int launch_sketch_dense(const void* A, int64_t lda, int dtype, bool acc64, int64_t m, int64_t n, int l1, int l,
-                        const SketchWs& ws, double* Y, unsigned int* status, int num_sms, cudaStream_t st);
+                        const SketchWs& ws, double* Y, unsigned int* status, int num_sms, cudaStream_t st,
+                        const int32_t* rowmap = nullptr);
 // Sketch of CSR A; heavy rows also written densely to D (n_heavy x n, row i of D = heavy[i]).
 int launch_sketch_csr(const int64_t* rowptr, const int32_t* colind, const void* val, int dtype, int64_t n,
                       const CsrRows& cr, int l1, int l, const SketchWs& ws, void* D, double* Y, unsigned int* status,
