@@ -31,19 +31,33 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
+// Split-K: FP32 accumulation in tensor memory runs over at most max_kps rows
+// of A (its rounding error grows with that depth); the split partials are
+// summed in float-float.  Enough splits to fill the GPU twice over.
+static void tc_splits(int64_t m, int64_t n, int nz, int num_sms, int64_t max_kps, int64_t& kps, int& splits) {
+  const int64_t xt = cdiv(n, tc::kBM);
+  int64_t S = max64(cdiv(m, max_kps), cdiv(2 * (int64_t)num_sms, xt * nz));
+  S = min64(S, max64(1, cdiv(m, tc::kBK)));
+  kps = cdiv(cdiv(m, S), tc::kBK) * tc::kBK;
+  splits = (int)cdiv(m, kps);
+}
+
+// Deepest split for each arithmetic: 512 rows keeps the FP32 product within
+// FP32 parity; with W in two BF16 planes (16 bits) or one (8 bits) the W
+// representation error dominates the accumulation error of much deeper splits
+// (the typical relative rounding of a depth-d FP32 sum, sqrt(d) 2^-24, stays
+// below 2^-17 and 2^-9 for d = 2048 and 8192).  Fewer splits, fewer partials.
+static int64_t tc_max_kps(int prec) {
+  if (prec == RLU_PREC_BF16) return 8192;
+  if (prec == RLU_PREC_BF16_REFINE) return 2048;
+  return 512;
+}
+
 void tc_plan(int64_t m, int64_t n, int k, int num_sms, TcPlan& p) {
   p.nz = (k + 207) / 208;                 // N blocks of at most 208 rows of W (fits two stages in shared memory)
   p.npad = (int)cdiv(cdiv(k, p.nz), 16) * 16;
   p.ldw = cdiv(m, 8) * 8;                 // TMA row stride: multiple of 16 bytes
-  // Split-K: FP32 accumulation in tensor memory runs over at most kMaxKps rows
-  // of A (its rounding error grows with that depth); the split partials are
-  // summed in float-float.  Enough splits to fill the GPU twice over.
-  const int64_t xt = cdiv(n, tc::kBM);
-  const int64_t kMaxKps = 512;
-  int64_t S = max64(cdiv(m, kMaxKps), cdiv(2 * (int64_t)num_sms, xt * p.nz));
-  S = min64(S, max64(1, cdiv(m, tc::kBK)));
-  p.kps = cdiv(cdiv(m, S), tc::kBK) * tc::kBK;
-  p.splits = (int)cdiv(m, p.kps);
+  tc_splits(m, n, p.nz, num_sms, 512, p.kps, p.splits);  // the most splits any precision uses
 }
 
 size_t tc_workspace_bytes(int64_t m, int64_t n, int k, int num_sms) {
@@ -54,6 +68,7 @@ size_t tc_workspace_bytes(int64_t m, int64_t n, int k, int num_sms) {
 
 int tc_setup(TcWs& w, void* base, int64_t m, int64_t n, int k, int num_sms) {
   tc_plan(m, n, k, num_sms, w.plan);
+  w.num_sms = num_sms;
   unsigned char* b = (unsigned char*)base;
   const size_t plane = (size_t)k * w.plan.ldw * 2;
   for (int q = 0; q < 3; ++q) w.wp[q] = (__nv_bfloat16*)(b + q * plane);
@@ -94,15 +109,15 @@ __global__ void k_split_w_rows(int64_t m, int k, int64_t ldw, const float* __res
 
 template <typename TA>
 static int launch_cfg(const TcWs& w, int wplanes, const TA* A, int64_t lda, int64_t m, int64_t n, int k,
-                      unsigned int* status, cudaStream_t st) {
+                      int64_t kps, int splits, unsigned int* status, cudaStream_t st) {
   constexpr int P = std::is_same<TA, float>::value ? 2 : 1;
   const TcPlan& p = w.plan;
   const size_t smem = tc::smem_bytes(P, wplanes, p.npad);
   auto kern = tc::k_bgemm_tc<TA>;
   if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
-  dim3 grid((unsigned)cdiv(n, tc::kBM), (unsigned)p.splits, (unsigned)p.nz);
+  dim3 grid((unsigned)cdiv(n, tc::kBM), (unsigned)splits, (unsigned)p.nz);
   const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(w.map);
-  kern<<<grid, tc::kThreads, smem, st>>>(maps[0], maps[1], maps[2], wplanes, A, lda, m, n, k, p.npad, p.kps, w.part,
+  kern<<<grid, tc::kThreads, smem, st>>>(maps[0], maps[1], maps[2], wplanes, A, lda, m, n, k, p.npad, kps, w.part,
                                          status);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
@@ -120,15 +135,19 @@ int launch_bgemm_tc(const TcWs& w, const float* W, const void* A, int64_t lda, i
   int wplanes = 3;
   if (prec == RLU_PREC_BF16) wplanes = 1;
   if (prec == RLU_PREC_BF16_REFINE) wplanes = 2;
+  int64_t kps = p.kps;
+  int splits = p.splits;
+  tc_splits(m, n, p.nz, w.num_sms, tc_max_kps(prec), kps, splits);
+  if (splits > p.splits) return RLU_EINVAL;  // the partial buffer holds p.splits
   int rc;
   if (dtype == RLU_F32)
-    rc = launch_cfg<float>(w, wplanes, (const float*)A, lda, m, n, k, status, st);
+    rc = launch_cfg<float>(w, wplanes, (const float*)A, lda, m, n, k, kps, splits, status, st);
   else if (dtype == RLU_BF16)
-    rc = launch_cfg<__nv_bfloat16>(w, wplanes, (const __nv_bfloat16*)A, lda, m, n, k, status, st);
+    rc = launch_cfg<__nv_bfloat16>(w, wplanes, (const __nv_bfloat16*)A, lda, m, n, k, kps, splits, status, st);
   else
     return RLU_EINVAL;
   if (rc) return rc;
-  tc::k_sum_parts<<<(unsigned)cdiv((int64_t)k * n, 256), 256, 0, st>>>((int64_t)k * n, p.splits, w.part, B);
+  tc::k_sum_parts<<<(unsigned)cdiv((int64_t)k * n, 256), 256, 0, st>>>((int64_t)k * n, splits, w.part, B);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
   return RLU_OK;

@@ -21,6 +21,7 @@ struct TcWs {
   __nv_bfloat16* wp[3];          // BF16 planes of W, k x ldw
   float* part;                    // splits x k x n FP32 partials
   alignas(64) unsigned char map[3][128];  // TMA descriptors of the planes
+  int num_sms;
   bool ready;
 };
 
