@@ -166,7 +166,8 @@ struct Sizes {
 };
 
 int max_gram_splits_for(int k, int num_sms) {
-  int64_t tiles = cdiv(k, 64) * cdiv(k, 64);
+  const int64_t tk = cdiv(k, 64);
+  int64_t tiles = tk * (tk + 1) / 2;  // the symmetric Gram product computes the upper tiles only
   int64_t s = cdiv(2 * (int64_t)num_sms, tiles);
   return (int)(s < 1 ? 1 : s);
 }
@@ -433,6 +434,7 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   aa.m = m; aa.n = n; aa.k = k;
   aa.Lk = h->Lk; aa.perm_y = h->perm_y; aa.perm_b = h->perm_b; aa.Bp = h->B;
   aa.LyP = h->LyP; aa.Lb = h->Lb; aa.L = L; aa.U = U; aa.p = p; aa.q = q;
+  aa.fp32_product = (h->prec == RLU_PREC_BF16 || h->prec == RLU_PREC_BF16_REFINE) ? 1 : 0;
   rc = f64 ? launch_assemble<double, double>(aa, st) : launch_assemble<df32, float>(aa, st);
   if (rc) return rc;
   if ((rc = mark(h, 9, st))) return rc;
@@ -504,6 +506,7 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   aa.m = m; aa.n = n; aa.k = k;
   aa.Lk = h->Lk; aa.perm_y = h->perm_y; aa.perm_b = h->perm_b; aa.Bp = h->B;
   aa.LyP = h->LyP; aa.Lb = h->Lb; aa.L = L; aa.U = U; aa.p = p; aa.q = q;
+  aa.fp32_product = (h->prec == RLU_PREC_BF16 || h->prec == RLU_PREC_BF16_REFINE) ? 1 : 0;
   rc = f64 ? launch_assemble<double, double>(aa, st) : launch_assemble<df32, float>(aa, st);
   if (rc) return rc;
   if ((rc = mark(h, 9, st))) return rc;

@@ -144,6 +144,18 @@ inline int gemm_chunked(cudaStream_t st, int64_t M, int64_t N, int64_t K, const 
   return RLU_OK;
 }
 
+// Sum S split-K slices of a symmetric n x n product whose partials hold only
+// the 64 x 64 tiles on and above the diagonal (fixed order).
+static __global__ void k_sum_slices_sym(int64_t nn, int S, const double* __restrict__ part, double* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nn * nn) return;
+  const int64_t i = e / nn, j = e - i * nn;
+  const int64_t src = (i / 64 > j / 64) ? j * nn + i : e;
+  double s = 0.0;
+  for (int z = 0; z < S; ++z) s += part[(int64_t)z * nn * nn + src];
+  out[e] = s;
+}
+
 // Sum S split-K slices of an M x N row-major partial buffer (fixed order).
 template <typename TC>
 __global__ void k_sum_slices(int64_t MN, int S, const double* __restrict__ part, TC* __restrict__ out) {
@@ -176,8 +188,12 @@ template <typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(256) k_gemm_df32(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A,
                                                    int64_t a_rs, int64_t a_cs, const TB* __restrict__ B,
                                                    int64_t b_rs, int64_t b_cs, TC* __restrict__ C, int64_t c_rs,
-                                                   int64_t c_cs, int64_t c_zs, int64_t k_per_split) {
+                                                   int64_t c_cs, int64_t c_zs, int64_t k_per_split,
+                                                   int upper_only) {
   constexpr int BM = 64, BN = 64, BK = 16;
+  // symmetric products (C = A A^T): the tiles below the diagonal are skipped
+  // and read transposed by the consumer
+  if (upper_only && blockIdx.y > blockIdx.x) return;
   __shared__ __align__(16) float sAh[2][BK][BM], sAl[2][BK][BM];
   __shared__ __align__(16) float sBh[2][BK][BN], sBl[2][BK][BN];
   const int tid = threadIdx.x;
@@ -290,13 +306,14 @@ static __global__ void k_sum_slices_df(int64_t MN, int S, const double* __restri
 template <typename TA, typename TB, typename TC, typename TACC>
 inline int gemm_simt(cudaStream_t st, int64_t M, int64_t N, int64_t K, const TA* A, int64_t a_rs, int64_t a_cs,
                      const TB* B, int64_t b_rs, int64_t b_cs, TC* C, int64_t c_rs, int64_t c_cs, int splits = 1,
-                     int64_t c_zs = 0) {
+                     int64_t c_zs = 0, int upper_only = 0) {
   if (M <= 0 || N <= 0) return RLU_OK;
   int64_t kps = cdiv(K, splits);
   kps = cdiv(kps, 16) * 16;
   dim3 grid((unsigned)cdiv(N, 64), (unsigned)cdiv(M, 64), (unsigned)splits);
   if constexpr (std::is_same<TACC, df32>::value)
-    k_gemm_df32<TA, TB, TC><<<grid, 256, 0, st>>>(M, N, K, A, a_rs, a_cs, B, b_rs, b_cs, C, c_rs, c_cs, c_zs, kps);
+    k_gemm_df32<TA, TB, TC><<<grid, 256, 0, st>>>(M, N, K, A, a_rs, a_cs, B, b_rs, b_cs, C, c_rs, c_cs, c_zs, kps,
+                                                  upper_only);
   else
     k_gemm_simt<TA, TB, TC, TACC><<<grid, 256, 0, st>>>(M, N, K, A, a_rs, a_cs, B, b_rs, b_cs, C, c_rs, c_cs, c_zs,
                                                          kps);

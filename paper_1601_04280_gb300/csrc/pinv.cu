@@ -5,6 +5,8 @@
 // ORIGINAL row order (so no row gather of A is ever needed: W = L_y^+ P acts
 // on A directly) and G = Lk^T Lk.  G = R^T R by a blocked Cholesky, R^{-1}
 // by column back-substitution, G^{-1} = R^{-1} R^{-T}; all FP64.
+#include <type_traits>
+
 #include "common.cuh"
 #include "gemm_simt.cuh"
 #include "pinv.cuh"
@@ -162,7 +164,8 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
 int launch_gram(const PinvArgs& a, cudaStream_t st) {
   const int64_t m = a.m;
   const int k = a.k, l = a.l;
-  const int64_t tiles = cdiv(k, 64) * cdiv(k, 64);
+  const int64_t tk = cdiv(k, 64);
+  const int64_t tiles = a.w64 ? tk * tk : tk * (tk + 1) / 2;  // the float-float product skips the lower tiles
   int S = (int)min64(a.max_gram_splits, max64(1, cdiv(2 * a.num_sms, tiles)));
   S = (int)min64(S, max64(1, cdiv(m, 64)));
   int rc;
@@ -178,8 +181,14 @@ int launch_gram(const PinvArgs& a, cudaStream_t st) {
     k_extract_Lk<df32><<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, l, k, a.Y, a.pstep, Lk);
     RLU_CUDA_TRY(cudaGetLastError());
     note_launch();
+    // G is symmetric: only the tiles on and above the diagonal are computed
     rc = gemm_simt<df32, df32, double, df32>(st, k, k, m, Lk, 1, k, Lk, k, 1, a.gram_part, k, 1, S,
-                                             (int64_t)k * k);
+                                             (int64_t)k * k, 1);
+    if (rc) return rc;
+    k_sum_slices_sym<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(k, S, a.gram_part, a.G);
+    RLU_CUDA_TRY(cudaGetLastError());
+    note_launch();
+    return RLU_OK;
   }
   if (rc) return rc;
   k_sum_slices<double><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>((int64_t)k * k, S, a.gram_part, a.G);
@@ -293,7 +302,14 @@ int launch_assemble(const AssembleArgs& a, cudaStream_t st) {
                                                                           reinterpret_cast<TO*>(a.U));
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch(3);
-  int rc = gemm_simt<T, T, TO, T>(st, m, k, k, LyP, k, 1, Lb, k, 1, reinterpret_cast<TO*>(a.L), k, 1);
+  // L = L_y L_b: float-float (or FP64) by default; FP32 accumulation in the
+  // BF16 forms, whose error is set by the BF16 representation of A and W
+  // (~1e-3 of ||A||), far above an FP32 product's
+  int rc;
+  if (a.fp32_product && !std::is_same<T, double>::value)
+    rc = gemm_simt<T, T, TO, float>(st, m, k, k, LyP, k, 1, Lb, k, 1, reinterpret_cast<TO*>(a.L), k, 1);
+  else
+    rc = gemm_simt<T, T, TO, T>(st, m, k, k, LyP, k, 1, Lb, k, 1, reinterpret_cast<TO*>(a.L), k, 1);
   if (rc) return rc;
   RLU_CUDA_TRY(cudaMemcpyAsync(a.p, a.perm_y, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
   RLU_CUDA_TRY(cudaMemcpyAsync(a.q, a.perm_b, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, st));
