@@ -65,13 +65,19 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
         blk[r][c] = (r < jb && c < jb) ? S[(int64_t)(c0 + r) * k + c0 + c] : (r == c ? 1.0 : 0.0);
       }
       __syncthreads();
+      // FP64 issues at a small fraction of the FP32 rate whatever the active
+      // lanes, so each FP64 instruction is issued once: warp 0 forms the
+      // scaled row u_t = g_ct / g_cc, then warp w updates rows r = w, w+8, ...
+      // (lane t, one FMA per row), skipping the rows already eliminated.
       for (int c = 0; c < jb; ++c) {
-        const double piv = blk[c][c];
-        const double inv = (piv > 0.0) ? rcp_newton(piv) : 0.0;
-        for (int e = tid; e < kNb * kNb; e += blockDim.x) {
-          const int r = e / kNb, t = e % kNb;
-          if (r > c && t >= r && t < jb) blk[r][t] = fma(-blk[c][r] * inv, blk[c][t], blk[r][t]);
+        if (warp == 0) {
+          const double piv = blk[c][c];
+          const double inv = (piv > 0.0) ? rcp_newton(piv) : 0.0;
+          if (lane > c && lane < jb) rdiag[lane] = blk[c][lane] * inv;
         }
+        __syncthreads();
+        for (int r = c + 1 + ((warp - (c + 1)) % NW + NW) % NW; r < jb; r += NW)
+          if (lane >= r && lane < jb) blk[r][lane] = fma(-blk[c][r], rdiag[lane], blk[r][lane]);
         __syncthreads();
       }
       if (tid < jb) {
