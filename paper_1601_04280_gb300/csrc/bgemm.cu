@@ -112,13 +112,17 @@ static int launch_cfg(const TcWs& w, int wplanes, const TA* A, int64_t lda, int6
                       int64_t kps, int splits, unsigned int* status, cudaStream_t st) {
   constexpr int P = std::is_same<TA, float>::value ? 2 : 1;
   const TcPlan& p = w.plan;
-  const size_t smem = tc::smem_bytes(P, wplanes, p.npad);
+  int dev = 0, optin = 0;
+  RLU_CUDA_TRY(cudaGetDevice(&dev));
+  RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int nst = tc::stages_for(P, wplanes, p.npad, (size_t)optin - 2048);  // room for the static barriers
+  const size_t smem = tc::smem_bytes(P, wplanes, p.npad, nst);
   auto kern = tc::k_bgemm_tc<TA>;
   if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
   dim3 grid((unsigned)cdiv(n, tc::kBM), (unsigned)splits, (unsigned)p.nz);
   const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(w.map);
   kern<<<grid, tc::kThreads, smem, st>>>(maps[0], maps[1], maps[2], wplanes, A, lda, m, n, k, p.npad, kps, w.part,
-                                         status);
+                                         status, nst);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
   return RLU_OK;

@@ -32,7 +32,7 @@ namespace tc {
 constexpr int kThreads = 192;
 constexpr int kBM = 128;        // columns of A per CTA (MMA M)
 constexpr int kBK = 64;         // rows of A per k-block (one 128-byte swizzle atom of BF16)
-constexpr int kStages = 2;
+constexpr int kMaxStages = 4;  // shared-memory ring depth (the host picks 2..4 by tile size)
 constexpr int kMaxN = 256;      // k rounded up to 16
 constexpr uint32_t kTmemCols = 256;
 constexpr long long kWaitLimit = 2000000000ll;  // cycles, about a second
@@ -173,10 +173,11 @@ template <typename TA>
 __global__ void __launch_bounds__(kThreads, 1)
     k_bgemm_tc(const __grid_constant__ CUtensorMap tmW1, const __grid_constant__ CUtensorMap tmW2,
                const __grid_constant__ CUtensorMap tmW3, int wplanes, const TA* __restrict__ A, int64_t lda,
-               int64_t m, int64_t n, int k, int npad, int64_t kps, float* __restrict__ part, unsigned int* status) {
+               int64_t m, int64_t n, int k, int npad, int64_t kps, float* __restrict__ part, unsigned int* status,
+               int nst) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full_w[kStages], full_a[kStages], empty[kStages], accum_full;
+  __shared__ __align__(8) uint64_t full_w[kMaxStages], full_a[kMaxStages], empty[kMaxStages], accum_full;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
 
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t wbytes = w_tile_bytes(npad);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(&full_w[s], 1);
       mbar_init(&full_a[s], 128);
       mbar_init(&empty[s], 1);
@@ -219,8 +220,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int issued = 0;
       for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % kStages;
-        if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) { s_fail = 1; break; }
+        const int s = kb % nst;
+        if (kb >= nst && !mbar_wait(&empty[s], ((kb / nst) - 1) & 1)) { s_fail = 1; break; }
         if (s_fail) break;
         mbar_arrive_expect_tx(&full_w[s], wbytes * wplanes);
         const int x = (int)(kbeg + (int64_t)kb * kBK);
@@ -230,8 +231,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         issued = kb + 1;
       }
       // drain: every issued load has landed before the CTA may exit
-      for (int kb = issued - kStages < 0 ? 0 : issued - kStages; kb < issued; ++kb)
-        if (!mbar_wait(&full_w[kb % kStages], (kb / kStages) & 1)) s_fail = 1;
+      for (int kb = issued - nst < 0 ? 0 : issued - nst; kb < issued; ++kb)
+        if (!mbar_wait(&full_w[kb % nst], (kb / nst) & 1)) s_fail = 1;
     }
   } else if (warp == 1) {
     // ---- MMA issuer ----
@@ -239,8 +240,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = idesc_bf16(kBM, npad);
       bool ok = true;
       for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int s = kb % kStages;
-        const uint32_t par = (kb / kStages) & 1;
+        const int s = kb % nst;
+        const uint32_t par = (kb / nst) & 1;
         if (!mbar_wait(&full_w[s], par) || !mbar_wait(&full_a[s], par)) { ok = false; break; }
         tc_fence_after();
         const uint32_t a1 = smem_u32(stageA(s, 0)), a2 = smem_u32(stageA(s, P - 1));
@@ -272,8 +273,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int t = threadIdx.x - 64;  // 0..127: row of the tile = column j0 + t of A
     const int64_t j = j0 + t;
     for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % kStages;
-      if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) { s_fail = 1; break; }
+      const int s = kb % nst;
+      if (kb >= nst && !mbar_wait(&empty[s], ((kb / nst) - 1) & 1)) { s_fail = 1; break; }
       if (s_fail) break;
       const int64_t k0 = kbeg + (int64_t)kb * kBK;
       unsigned char* A1 = stageA(s, 0);
@@ -349,8 +350,16 @@ __global__ void k_split_w(int64_t km, const TW* __restrict__ W, __nv_bfloat16* _
   W3[e] = __float2bfloat16_rn(r2);
 }
 
-inline size_t smem_bytes(int pieces, int wplanes, int npad) {
-  return (size_t)kStages * stage_bytes(pieces, wplanes, npad) + 1024;
+// Ring depth for a tile size: as many stages (2..kMaxStages) as fit in the
+// shared memory of one CTA.
+inline int stages_for(int pieces, int wplanes, int npad, size_t optin) {
+  int st = kMaxStages;
+  while (st > 2 && (size_t)st * stage_bytes(pieces, wplanes, npad) + 1024 > optin) --st;
+  return st;
+}
+
+inline size_t smem_bytes(int pieces, int wplanes, int npad, int nst) {
+  return (size_t)nst * stage_bytes(pieces, wplanes, npad) + 1024;
 }
 
 }  // namespace tc
