@@ -6,5 +6,6 @@ benchmark's CPU-baseline leg, never by the product path.
 from .rlu import (KEY_TAG, STATUS_OK, STATUS_WRANK, SketchParams, LUResult,
                   OracleResult, sketch_params, sem_matrix, countsketch,
                   hartley_columns, fjl, lu_partial_pivot, unit_lower,
-                  pinv_householder, factor, relative_residual, check_sizes)
+                  pinv_householder, factor, relative_residual, check_sizes,
+                  second_projection, factor_two_sketch)
 from .philox import philox4x64_10, mulhilo64, stream_blocks

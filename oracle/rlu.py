@@ -17,7 +17,9 @@ sparse projections" (arXiv 1601.04280), step by step and in FP64:
   step 3                  P Y = L_Y U_Y, partial (row) pivoting; L_y is the
                           first k columns of L_Y;
   steps 5-6 (replaced)    B = L_y^+ P A with the exact pseudo-inverse, the
-                          object bounded by Corollary 3.3 (col:A_LLA);
+                          object bounded by Corollary 3.3 (col:A_LLA), or
+                          (factor_two_sketch) the paper's own steps 4-5:
+                          B = (Omega_2 L_1)^+ Omega_2 P A;
   step 6                  B Q = L_b U_b, LU with right (column) pivoting;
   step 7                  L = L_y L_b, U = U_b.
 
@@ -241,6 +243,8 @@ class OracleResult:
     gaps_b: np.ndarray  # pivot separation of the LU of B
     top_y: np.ndarray = None  # (l, 2) two largest candidate magnitudes per step
     top_b: np.ndarray = None  # (k, 2)
+    Y2: np.ndarray = None     # k2 x n, Omega_2 P A (second projection only)
+    Z: np.ndarray = None      # k2 x k, Omega_2 L_y (second projection only)
 
 
 def check_sizes(m, n, k, l, l1):
@@ -286,6 +290,63 @@ def factor(A, k, l, l1, seed):
     return OracleResult(L=L, U=Ub, p=p, q=q, status=status, params=params,
                         Y=Y, Ly=Ly, W=W, B=B, Lb=Lb, Ub=Ub,
                         gaps_y=ly.gaps, gaps_b=lb.gaps, top_y=ly.top, top_b=lb.top)
+
+
+def second_projection(M, params2, l2):
+    """Omega_2 M for an m x c matrix M: the second sparse projection of
+    Algorithm 1 (steps 4-5), Omega_2 = Pi_2 S_2 of size k2 x m, acting on the
+    rows of M.  It is the first projection applied to M^T: CountSketch of the
+    m rows into l2 buckets (S_2, Sec. 2.2), signs, real Hartley transform,
+    subsample of k2 outputs (Pi_2, Sec. 2.1), transposed back."""
+    if scipy.sparse.issparse(M):
+        Mt = M.T.tocsr()
+    else:
+        Mt = np.asarray(M, dtype=np.float64).T
+    return fjl(countsketch(Mt, params2, l2), params2, l2).T
+
+
+def factor_two_sketch(A, k, l, l1, k2, l2, seed, seed2):
+    """Algorithm 1 with its own second projection (steps 4-6).
+
+    Steps 1-3 as in factor().  Step 4 draws Omega_2 = Pi_2 S_2 (k2 x m) from
+    seed2; step 5 forms Z = Omega_2 L_1 and its pseudo-inverse; step 6 factors
+    B = Z^+ Omega_2 P A with right pivoting.  Reading: S_2 hashes the ORIGINAL
+    row index i of A (bucket h_2(i), sign s_2(i)), i.e. the sketch of P A is
+    Omega_2' P^T with Omega_2' acting on A's rows; P does not depend on
+    Omega_2, so this is an SEM of the same law, and it lets both Omega_2 P A =
+    Omega_2' A and Omega_2 L_1 = Omega_2' Lk (Lk = L_1 with its rows put back in
+    the original order) be formed without gathering rows.
+    """
+    m, n = A.shape
+    check_sizes(m, n, k, l, l1)
+    if not (k <= k2 <= l2):
+        raise ValueError("need k <= k2 <= l2")
+    status = STATUS_OK
+    params = sketch_params(n, l1, l, seed)
+    Y = fjl(countsketch(A, params, l1), params, l1)
+    ly = lu_partial_pivot(Y, steps=l)
+    if ly.zero_pivot:
+        status = STATUS_WRANK
+    p = ly.perm
+    Ly = unit_lower(ly.lu, k)
+    # steps 4-5: Omega_2 over the original rows
+    params2 = sketch_params(m, l2, k2, seed2)
+    Lk = np.empty_like(Ly)
+    Lk[p] = Ly
+    Z = second_projection(Lk, params2, l2)    # k2 x k
+    Y2 = second_projection(A, params2, l2)    # k2 x n
+    W = pinv_householder(Z)                   # k x k2
+    B = W @ Y2
+    lb = lu_partial_pivot(B.T, steps=k)
+    if lb.zero_pivot:
+        status = STATUS_WRANK
+    q = lb.perm
+    Lb = np.triu(lb.lu[:k, :k]).T
+    Ub = unit_lower(lb.lu, k).T
+    L = Ly @ Lb
+    return OracleResult(L=L, U=Ub, p=p, q=q, status=status, params=params,
+                        Y=Y, Ly=Ly, W=W, B=B, Lb=Lb, Ub=Ub,
+                        gaps_y=ly.gaps, gaps_b=lb.gaps, top_y=ly.top, top_b=lb.top, Y2=Y2, Z=Z)
 
 
 def relative_residual(A, L, U, p, q):
