@@ -123,11 +123,14 @@ def oracle_input(w, A):
     return A.astype(np.float64)
 
 
-def oracle_factor_seconds(w, A):
+def oracle_factor_seconds(w, A, second=None):
     import oracle
     Ao = oracle_input(w, A)
     t0 = time.perf_counter()
-    oracle.factor(Ao, w.k, w.l, w.l1, w.sketch_seed)
+    if second:
+        oracle.factor_two_sketch(Ao, w.k, w.l, w.l1, second["k2"], second["l2"], w.sketch_seed, second["seed2"])
+    else:
+        oracle.factor(Ao, w.k, w.l, w.l1, w.sketch_seed)
     return time.perf_counter() - t0
 
 
@@ -186,6 +189,8 @@ def main():
                     help="serving: CTAs of each request's grid-synchronised kernels (0 = one per SM, -1 = the "
                          "server's default, a quarter of the SMs)")
     ap.add_argument("--prec", default=None, help="override the workload's precision (f64, f32, bf16, bf16_refine)")
+    ap.add_argument("--second-projection", action="store_true",
+                    help="B by the paper's second projection (k2 = min(2 l, 1024), l2 = min(8 k2, 4096)) instead of the exact L_y^+")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -226,6 +231,13 @@ def main():
         dev_in = (torch.from_numpy(A_np).to(dev, tdt),)
         a_bytes = dev_in[0].element_size() * m * n
     h = rg.RandLU(m, n, k, l, l1, w.sketch_seed + rank, prec=prec)
+    second = None
+    if args.second_projection:
+        if kind == "csr":
+            raise SystemExit("--second-projection is built for dense inputs")
+        k2 = min(2 * l, 1024)
+        second = {"k2": k2, "l2": min(8 * k2, 4096), "seed2": w.sketch_seed + 7}
+        h.set_second_sketch(second["k2"], second["l2"], second["seed2"])
     outs = h.alloc_outputs(dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -372,7 +384,7 @@ def main():
                             frac=ach / peaks["bf16_tflops"], peak_kind=peak_kind)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            secs = oracle_factor_seconds(w, A_np)
+            secs = oracle_factor_seconds(w, A_np, second)
             cpu = {"value": 1.0 / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": "one full factorization of the workload by the FP64 oracle (numpy/scipy)"}
         line = {
@@ -383,6 +395,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "m": m, "n": n, "k": k, "l": l, "l1": l1, "A_dtype": w.dtype,
                        "precision": prec, "nnz": nnz,
+                       "B": ("second projection (Algorithm 1 steps 4-6), k2=%d l2=%d" % (second["k2"], second["l2"])
+                             if second else "exact pseudo-inverse L_y^+ (Corollary 3.3)"),
                        "l2": "inputs larger than L2 (A %.0f MB > 129 MB L2)" % (a_bytes / 1e6)
                        if a_bytes > 135e6 else "inputs smaller than L2 (latency-bound workload)",
                        "parallelism": "independent problems per GPU" if world > 1 else "single GPU"},

@@ -116,6 +116,22 @@ int rlu_set_csr_workspace(rlu_t h, int64_t max_nnz, void* workspace, size_t work
 /* Select the arithmetic (rlu_prec).  Valid at any time between calls. */
 int rlu_set_precision(rlu_t h, int prec);
 
+/* Use the paper's own second projection for B (Algorithm 1, steps 4-6)
+ * instead of the exact pseudo-inverse of Corollary 3.3: Omega_2 = Pi_2 S_2
+ * (k2 x m: a CountSketch of the m rows into l2 buckets with random signs, the
+ * real Hartley transform and k2 of its l2 outputs, drawn from seed2 exactly
+ * as the first projection is drawn from seed, over A's ORIGINAL row order),
+ * Z = Omega_2 L_1 (k2 x k) and B = Z^+ Omega_2 P A, Z^+ by the Cholesky factor
+ * of Z^T Z.  The dense product W A is replaced by a second pass over A (A is
+ * transposed into a handle buffer of m n elements allocated on first use) and
+ * small k2-wide products.  Requires k <= k2 <= l2, k2 <= 1024, l2 <= 4096 (Z is
+ * sketched in FP64);
+ * k2 = 0 switches back to the exact pseudo-inverse.  Dense A only
+ * (rlu_factor_csr returns RLU_EINVAL while it is on).  Allocates its
+ * parameters and k2-wide buffers now and waits for the device.
+ * Errors: RLU_EINVAL, RLU_ENOMEM, RLU_ECUDA. */
+int rlu_set_second_sketch(rlu_t h, int32_t k2, int32_t l2, uint64_t seed2);
+
 /* Bound the CTAs of the two grid-synchronised kernels of handle h (the
  * pivoted LUs of steps 3 and 6, the Cholesky factor of G) to max_ctas; 0 (the
  * default) gives one CTA per SM.  Results do not depend on it (each kernel's

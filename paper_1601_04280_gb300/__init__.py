@@ -30,7 +30,7 @@ C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_
              "rlu_debug_timing", "rlu_debug_stage_ms", "rlu_debug_launch_count", "rlu_sketch_dense_noalloc",
              "rlu_csr_workspace_bytes", "rlu_set_csr_workspace", "rlu_graph_capture_dense", "rlu_graph_launch",
              "rlu_graph_destroy", "rlu_copy_block_async", "rlu_set_max_ctas",
-             "rlu_debug_recip")
+             "rlu_debug_recip", "rlu_set_second_sketch")
 
 #: stage names reported by rlu_debug_stage_ms, in order
 STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
@@ -81,6 +81,7 @@ def load(reload=False):
         "rlu_copy_block_async": ([vp, i64, vp, i64, i64, i64, vp], c.c_int),
         "rlu_set_max_ctas": ([vp, i32], c.c_int),
         "rlu_debug_recip": ([vp, vp, i64], c.c_int),
+        "rlu_set_second_sketch": ([vp, i32, i32, u64], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -122,6 +123,11 @@ def rlu_create_in(m, n, k, l, l1, seed, workspace_ptr, workspace_bytes, stream_p
 
 def rlu_set_precision(h, prec):
     return _check(load().rlu_set_precision(h, PREC.get(prec, prec)), "rlu_set_precision")
+
+
+def rlu_set_second_sketch(h, k2, l2, seed2):
+    return _check(load().rlu_set_second_sketch(h, int(k2), int(l2), ctypes.c_uint64(seed2 & (2**64 - 1))),
+                  "rlu_set_second_sketch")
 
 
 def rlu_set_max_ctas(h, max_ctas):
@@ -241,6 +247,10 @@ class RandLU:
                                    workspace.numel() * workspace.element_size(), _stream_ptr(stream))
         self.prec = prec
         rlu_set_precision(self.h, prec)
+
+    def set_second_sketch(self, k2, l2, seed2):
+        """B by the paper's second projection (k2 x m, l2 buckets); k2 = 0: exact pseudo-inverse."""
+        rlu_set_second_sketch(self.h, k2, l2, seed2)
 
     def set_max_ctas(self, max_ctas):
         """Bound the CTAs of the grid-synchronised kernels (0: one per SM)."""

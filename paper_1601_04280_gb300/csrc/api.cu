@@ -142,6 +142,15 @@ struct rlu_ctx {
   void* csr_heavy_buf = nullptr;
   void* csr_rows_buf = nullptr;
   bool csr_external = false;  // CSR scratch owned by the caller (rlu_set_csr_workspace)
+  // the paper's second projection (rlu_set_second_sketch): off when k2 == 0
+  int k2 = 0, l2 = 0;
+  uint64_t seed2 = 0;
+  SketchWs sk2{};
+  void* sk2_buf = nullptr;  // Omega_2 parameters and lists, Y2T, LkT, ZT, W2
+  double *Y2T = nullptr, *LkT = nullptr, *ZT = nullptr;
+  void* W2 = nullptr;
+  void* at_buf = nullptr;   // A transposed, grown on use
+  size_t at_bytes = 0;
   // per-stage device timing (test hook)
   int timing = 0;
   cudaEvent_t ev[kNumStages + 1] = {};
@@ -403,20 +412,41 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   pa.G = h->G; pa.Rinv = h->Rinv; pa.Ginv = h->Ginv;
   pa.W = h->W; pa.w64 = f64 ? 1 : 0;
   pa.bar = h->bar2; pa.status = h->status_dev; pa.num_sms = h->num_sms; pa.coop_ctas = coop_sms(h);
-  if ((rc = launch_gram(pa, st))) return rc;
-  if ((rc = mark(h, 4, st))) return rc;
-  if ((rc = launch_chol(pa, st))) return rc;
-  if ((rc = mark(h, 5, st))) return rc;
-  if ((rc = launch_wform(pa, st))) return rc;
-  if ((rc = mark(h, 6, st))) return rc;
-  // B = W A: tensor cores (BF16 splits) when available, else SIMT
-  if (!f64 && h->tcw.ready)
-    rc = launch_bgemm_tc(h->tcw, reinterpret_cast<const float*>(h->W), A, lda, dtype, h->prec, m, n, k,
-                         reinterpret_cast<df32*>(h->B), h->status_dev, st);
-  else
-    rc = launch_bgemm_simt(h->W, f64 ? 1 : 0, A, lda, dtype, m, n, k, h->B, h->bpart, h->num_sms, st);
-  if (rc) return rc;
-  if ((rc = mark(h, 7, st))) return rc;
+  if (h->k2 > 0) {
+    // steps 4-6 of Algorithm 1: B = (Omega_2 L_1)^+ Omega_2 P A (the timing stage
+    // "gram" covers all of it; chol, wform and bgemm then read zero)
+    const size_t esz = dtype == RLU_F64 ? 8 : (dtype == RLU_F32 ? 4 : 2);
+    const size_t need = esz * (size_t)m * n;
+    if (h->at_bytes < need) {
+      if (h->at_buf) cudaFree(h->at_buf);
+      h->at_buf = nullptr;
+      h->at_bytes = 0;
+      if (cudaMalloc(&h->at_buf, need) != cudaSuccess) { cudaGetLastError(); return RLU_ENOMEM; }
+      h->at_bytes = need;
+    }
+    SecondArgs sa{};
+    sa.m = m; sa.n = n; sa.k = k; sa.k2 = h->k2; sa.l2 = h->l2; sa.seed2 = h->seed2;
+    sa.A = A; sa.lda = lda; sa.dtype = dtype; sa.AT = h->at_buf;
+    sa.LkT = h->LkT; sa.Y2T = h->Y2T; sa.ZT = h->ZT; sa.W2 = h->W2; sa.B = h->B;
+    if ((rc = launch_second_projection(sa, pa, h->sk2, st))) return rc;
+    for (int sidx = 4; sidx <= 7; ++sidx)
+      if ((rc = mark(h, sidx, st))) return rc;
+  } else {
+    if ((rc = launch_gram(pa, st))) return rc;
+    if ((rc = mark(h, 4, st))) return rc;
+    if ((rc = launch_chol(pa, st))) return rc;
+    if ((rc = mark(h, 5, st))) return rc;
+    if ((rc = launch_wform(pa, st))) return rc;
+    if ((rc = mark(h, 6, st))) return rc;
+    // B = W A: tensor cores (BF16 splits) when available, else SIMT
+    if (!f64 && h->tcw.ready)
+      rc = launch_bgemm_tc(h->tcw, reinterpret_cast<const float*>(h->W), A, lda, dtype, h->prec, m, n, k,
+                           reinterpret_cast<df32*>(h->B), h->status_dev, st);
+    else
+      rc = launch_bgemm_simt(h->W, f64 ? 1 : 0, A, lda, dtype, m, n, k, h->B, h->bpart, h->num_sms, st);
+    if (rc) return rc;
+    if ((rc = mark(h, 7, st))) return rc;
+  }
   if (h->debug && h->Bdbg)
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Bdbg, h->B, 8 * (size_t)k * n, cudaMemcpyDeviceToDevice, st));
   // step 6: B Q = L_b U_b as partial pivoting of B^T
@@ -705,6 +735,60 @@ int rlu_create_in(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1, uint64
   return create_common(m, n, k, l, l1, seed, (char*)workspace, false, false, (cudaStream_t)stream, out);
 }
 
+int rlu_set_second_sketch(rlu_t h, int32_t k2, int32_t l2, uint64_t seed2) {
+  if (!h) return RLU_EINVAL;
+  if (k2 == 0) {
+    h->k2 = 0;
+    return RLU_OK;
+  }
+  // Z = Omega_2 L_1 is sketched in FP64, whose FFT buffers bound l2 by 4096
+  if (k2 < h->k || k2 > l2 || k2 > kMaxL || l2 > 4096) return RLU_EINVAL;
+  if (h->sk2_buf) cudaFree(h->sk2_buf);
+  h->sk2_buf = nullptr;
+  h->k2 = 0;
+  const int64_t m = h->m, n = h->n, k = h->k;
+  const int64_t nch = cdiv(m, 1024);
+  Sizes sz;
+  sz.add(sizeof(uint32_t) * m);                 // hs
+  sz.add(sizeof(float) * l2);                   // dsign
+  sz.add(sizeof(uint64_t) * l2);                // keys
+  sz.add(sizeof(int32_t) * k2);                 // R
+  sz.add(sizeof(int32_t) * (nch * l2 + 1));     // bcnt
+  sz.add(sizeof(int32_t) * (nch * l2 + 1));     // bstart
+  sz.add(sizeof(uint32_t) * m);                 // blist
+  sz.add(sizeof(double2) * l2);                 // tw64
+  sz.add(sizeof(float2) * l2);                  // tw32
+  sz.add(sizeof(double) * n * k2);              // Y2T
+  sz.add(sizeof(double) * k * m);               // LkT
+  sz.add(sizeof(double) * k * k2);              // ZT
+  sz.add((size_t)8 * k * k2);                   // W2
+  char* b = nullptr;
+  if (cudaMalloc(&b, sz.total) != cudaSuccess) {
+    cudaGetLastError();
+    return RLU_ENOMEM;
+  }
+  size_t off = 0;
+  int idx = 0;
+  auto next = [&]() -> void* { void* p = b + off; off += sz.parts[idx++]; return p; };
+  SketchWs& w = h->sk2;
+  w.hs = (uint32_t*)next(); w.dsign = (float*)next(); w.keys = (uint64_t*)next(); w.R = (int32_t*)next();
+  w.bcnt = (int32_t*)next(); w.bstart = (int32_t*)next(); w.blist = (uint32_t*)next();
+  w.tw64 = (double2*)next(); w.tw32 = (float2*)next();
+  w.plan = make_fft_plan(l2);
+  w.chunk = 1024;
+  w.nchunks = nch;
+  h->Y2T = (double*)next(); h->LkT = (double*)next(); h->ZT = (double*)next(); h->W2 = next();
+  h->sk2_buf = b;
+  if (launch_twiddles(l2, w.tw64, w.tw32, 0) != RLU_OK || cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return RLU_ECUDA;
+  }
+  h->k2 = k2;
+  h->l2 = l2;
+  h->seed2 = seed2;
+  return RLU_OK;
+}
+
 int rlu_set_max_ctas(rlu_t h, int32_t max_ctas) {
   if (!h || max_ctas < 0) return RLU_EINVAL;
   h->max_ctas = max_ctas;
@@ -731,6 +815,8 @@ int rlu_destroy(rlu_t h) {
   if (h->U_stage) cudaFree(h->U_stage);
   if (h->p_stage) cudaFree(h->p_stage);
   if (h->q_stage) cudaFree(h->q_stage);
+  if (h->sk2_buf) cudaFree(h->sk2_buf);
+  if (h->at_buf) cudaFree(h->at_buf);
   if (!h->csr_external) {
     if (h->csr_rows_buf) cudaFree(h->csr_rows_buf);
     if (h->csr_nnz_buf) cudaFree(h->csr_nnz_buf);
@@ -840,6 +926,7 @@ int rlu_factor_csr(rlu_t h, const int64_t* rowptr, const int32_t* colind, const 
   if (!((dtype == RLU_F64 && h->prec == RLU_PREC_F64) || (dtype == RLU_F32 && h->prec == RLU_PREC_F32)))
     return RLU_EINVAL;
   if (h->csr_external && nnz > h->csr_cap_nnz) return RLU_EINVAL;
+  if (h->k2 > 0) return RLU_EINVAL;  // the second projection is built for dense A
   cudaStream_t st = (cudaStream_t)stream;
   int rc = enqueue_csr(h, rowptr, colind, val, nnz, dtype, L, U, p, q, st);
   if (rc) return drain_after(rc, st);

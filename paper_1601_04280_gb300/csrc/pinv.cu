@@ -167,6 +167,127 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
 
 // Lk and the Gram matrix G = Lk^T Lk (split over row ranges, summed in fixed
 // order).  FP64 in the FP64 mode; float-float (about 48 bits) otherwise.
+int launch_extract_Lk(const PinvArgs& a, cudaStream_t st) {
+  const int64_t m = a.m;
+  const int k = a.k, l = a.l;
+  if (a.w64)
+    k_extract_Lk<double><<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, l, k, a.Y, a.pstep,
+                                                                      reinterpret_cast<double*>(a.Lk));
+  else
+    k_extract_Lk<df32><<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, l, k, a.Y, a.pstep,
+                                                                    reinterpret_cast<df32*>(a.Lk));
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return RLU_OK;
+}
+
+// out (cols x rows) = in (rows x cols, leading dimension ld_in) transposed,
+// through 32 x 32 shared-memory tiles; TO(x) converts (FP64 from float-float).
+template <typename TI, typename TO> __device__ __forceinline__ TO tr_cvt(TI x) { return (TO)x; }
+template <> __device__ __forceinline__ double tr_cvt<df32, double>(df32 x) { return to_double(x); }
+
+template <typename TI, typename TO>
+__global__ void k_transpose_cvt(int64_t rows, int64_t cols, const TI* __restrict__ in, int64_t ld_in,
+                                TO* __restrict__ out) {
+  __shared__ TO t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t r = r0 + y, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[y][threadIdx.x] = tr_cvt<TI, TO>(in[r * ld_in + c]);
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t c = c0 + y, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[c * rows + r] = t[threadIdx.x][y];
+  }
+}
+
+template <typename TI, typename TO>
+static int transpose_cvt(int64_t rows, int64_t cols, const TI* in, int64_t ld_in, TO* out, cudaStream_t st) {
+  dim3 grid((unsigned)cdiv(cols, 32), (unsigned)cdiv(rows, 32));
+  k_transpose_cvt<TI, TO><<<grid, dim3(32, 8), 0, st>>>(rows, cols, in, ld_in, out);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return RLU_OK;
+}
+
+int launch_second_projection(const SecondArgs& s, const PinvArgs& a, SketchWs& ws2, cudaStream_t st) {
+  const int64_t m = s.m, n = s.n;
+  const int k = s.k, k2 = s.k2, l2 = s.l2;
+  const bool w64 = a.w64 != 0;
+  int rc;
+  // step 4: Omega_2 over the m rows (hash, signs, frequencies, bucket lists)
+  ws2.chunk = 1024;
+  ws2.nchunks = cdiv(m, ws2.chunk);
+  if ((rc = launch_sketch_params(ws2, m, l2, k2, s.seed2, st))) return rc;
+  // step 5: Omega_2' A (through A^T: the first sketch applied to the n columns)
+  if (s.dtype == RLU_F64)
+    rc = transpose_cvt<double, double>(m, n, (const double*)s.A, s.lda, (double*)s.AT, st);
+  else if (s.dtype == RLU_F32)
+    rc = transpose_cvt<float, float>(m, n, (const float*)s.A, s.lda, (float*)s.AT, st);
+  else
+    rc = transpose_cvt<__nv_bfloat16, __nv_bfloat16>(m, n, (const __nv_bfloat16*)s.A, s.lda, (__nv_bfloat16*)s.AT,
+                                                      st);
+  if (rc) return rc;
+  if ((rc = launch_sketch_dense(s.AT, m, s.dtype, s.dtype == RLU_F64, n, m, l2, k2, ws2, s.Y2T, a.status,
+                                a.num_sms, st)))
+    return rc;
+  // ... and Omega_2' Lk, in FP64 (Lk is the L_1 of step 3 in A's row order)
+  if ((rc = launch_extract_Lk(a, st))) return rc;
+  if (w64)
+    rc = transpose_cvt<double, double>(m, k, (const double*)a.Lk, k, s.LkT, st);
+  else
+    rc = transpose_cvt<df32, double>(m, k, (const df32*)a.Lk, k, s.LkT, st);
+  if (rc) return rc;
+  if ((rc = launch_sketch_dense(s.LkT, m, RLU_F64, true, k, m, l2, k2, ws2, s.ZT, a.status, a.num_sms, st)))
+    return rc;
+  // Z^+ = (Z^T Z)^{-1} Z^T with Z = ZT^T (k2 x k): Gram, Cholesky, inverse, as for L_y^+
+  const int64_t tk = cdiv(k, 64);
+  const int64_t tiles = w64 ? tk * tk : tk * (tk + 1) / 2;
+  int S = (int)min64(a.max_gram_splits, max64(1, cdiv(2 * a.num_sms, tiles)));
+  S = (int)min64(S, max64(1, cdiv(k2, 64)));
+  const int64_t kps = cdiv(cdiv(k2, S), 16) * 16;
+  S = (int)cdiv(k2, kps);
+  if (w64) {
+    rc = gemm_simt<double, double, double, double>(st, k, k, k2, s.ZT, k2, 1, s.ZT, 1, k2, a.gram_part, k, 1, S,
+                                                   (int64_t)k * k);
+    if (rc) return rc;
+    k_sum_slices<double><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>((int64_t)k * k, S, a.gram_part, a.G);
+  } else {
+    rc = gemm_simt<double, double, double, df32>(st, k, k, k2, s.ZT, k2, 1, s.ZT, 1, k2, a.gram_part, k, 1, S,
+                                                 (int64_t)k * k, 1);
+    if (rc) return rc;
+    k_sum_slices_sym<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(k, S, a.gram_part, a.G);
+  }
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  if ((rc = launch_chol(a, st))) return rc;
+  // G^{-1} = R^{-1} R^{-T} (as in the W form), then W2 = G^{-1} Z^T and B = W2 Y2
+  if (w64) {
+    rc = gemm_simt<double, double, double, double>(st, k, k, k, a.Rinv, k, 1, a.Rinv, 1, k, a.Ginv, k, 1);
+    if (rc) return rc;
+    rc = gemm_simt<double, double, double, double>(st, k, k2, k, a.Ginv, k, 1, s.ZT, k2, 1, (double*)s.W2, k2, 1);
+    if (rc) return rc;
+    return gemm_simt<double, double, double, double>(st, k, n, k2, (const double*)s.W2, k2, 1, s.Y2T, 1, k2,
+                                                     (double*)s.B, n, 1);
+  }
+  int Sg = (int)min64(a.max_gram_splits, max64(1, cdiv(2 * a.num_sms, tk * tk)));
+  Sg = (int)min64(Sg, max64(1, cdiv(k, 16)));
+  const int64_t kpsg = cdiv(cdiv(k, Sg), 16) * 16;
+  Sg = (int)cdiv(k, kpsg);
+  rc = gemm_simt<double, double, double, df32>(st, k, k, k, a.Rinv, k, 1, a.Rinv, 1, k, a.gram_part, k, 1, Sg,
+                                               (int64_t)k * k);
+  if (rc) return rc;
+  df32* Ginv = reinterpret_cast<df32*>(a.Ginv);
+  k_sum_slices_df<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>((int64_t)k * k, Sg, a.gram_part, Ginv);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  rc = gemm_simt<df32, double, df32, df32>(st, k, k2, k, Ginv, k, 1, s.ZT, k2, 1, (df32*)s.W2, k2, 1);
+  if (rc) return rc;
+  return gemm_simt<df32, double, df32, df32>(st, k, n, k2, (const df32*)s.W2, k2, 1, s.Y2T, 1, k2, (df32*)s.B, n,
+                                             1);
+}
+
 int launch_gram(const PinvArgs& a, cudaStream_t st) {
   const int64_t m = a.m;
   const int k = a.k, l = a.l;

@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "sketch.cuh"
+
 namespace rlu {
 
 struct PinvArgs {
@@ -41,6 +43,26 @@ struct AssembleArgs {
 };
 
 int launch_gram(const PinvArgs& a, cudaStream_t st);
+
+// The paper's own second projection (Algorithm 1, steps 4-6):
+// B = (Omega_2 L_1)^+ Omega_2 P A with Omega_2 = Pi_2 S_2 drawn over A's
+// original rows (so Omega_2 P A = Omega_2' A and Omega_2 L_1 = Omega_2' Lk).
+struct SecondArgs {
+  int64_t m, n;
+  int k, k2, l2;
+  uint64_t seed2;
+  const void* A;
+  int64_t lda;
+  int dtype;
+  void* AT;        // n x m, A's element type: A transposed
+  double* LkT;     // k x m: Lk transposed, FP64
+  double* Y2T;     // n x k2: (Omega_2' A)^T
+  double* ZT;      // k x k2: (Omega_2' Lk)^T
+  void* W2;        // k x k2: (Z^T Z)^{-1} Z^T, double if w64 else float-float
+  void* B;         // k x n output, double if w64 else float-float
+};
+int launch_extract_Lk(const PinvArgs& a, cudaStream_t st);
+int launch_second_projection(const SecondArgs& s, const PinvArgs& a, SketchWs& ws2, cudaStream_t st);
 int launch_chol(const PinvArgs& a, cudaStream_t st);
 int launch_wform(const PinvArgs& a, cudaStream_t st);
 template <typename T, typename TO>

@@ -339,3 +339,61 @@ def test_global_memory_lu_of_B_f32(rg):
     e_o = oracle.relative_residual(A, o.L, o.U, o.p, o.q)
     e_g = oracle.relative_residual(A, g["L"], g["U"], g["p"], g["q"])
     assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
+
+
+# The paper's own second projection (Algorithm 1, steps 4-6) on the GPU against
+# the oracle's factor_two_sketch: same Omega_2 (bit-exact parameters), same
+# tolerances as the exact-pseudo-inverse path.
+@pytest.mark.parametrize("m,n,k,l,l1,k2,l2,prec", [
+    (1024, 1024, 20, 30, 240, 60, 480, "f64"),
+    (1500, 1200, 24, 32, 256, 64, 512, "f32"),
+    (3000, 2000, 40, 52, 400, 104, 832, "f32"),   # l2 = 2^6 13: a generic radix in the second FFT
+])
+def test_second_projection_parity(rg, m, n, k, l, l1, k2, l2, prec):
+    if prec == "f64":
+        A = ri.dense_spectrum(m, n, ri.geometric_spectrum(min(m, n)), 41)
+        tdt = torch.float64
+    else:
+        A = ri.dense_low_rank_plus_noise(m, n, k + 10, 1e-4, seed=m + 7)
+        tdt = torch.float32
+    o = oracle.factor_two_sketch(A.astype(np.float64), k, l, l1, k2, l2, seed=96, seed2=97)
+    h = rg.RandLU(m, n, k, l, l1, 96, prec=prec)
+    h.set_second_sketch(k2, l2, 97)
+    h.debug_enable(True)
+    f = h.factor(to_dev(A, tdt), check=False)
+    torch.cuda.synchronize()
+    g = dict(L=f.L.double().cpu().numpy(), U=f.U.double().cpu().numpy(), p=f.p.cpu().numpy(),
+             q=f.q.cpu().numpy(), status=f.status)
+    assert g["status"] == 0
+    check_structure(g, m, n, k)
+    check_pivots(g, o, k)
+    B = h.debug_B()
+    e_o = oracle.relative_residual(A, o.L, o.U, o.p, o.q)
+    e_g = oracle.relative_residual(A, g["L"], g["U"], g["p"], g["q"])
+    if prec == "f64":
+        assert np.abs(B - o.B).max() <= 1e-9 * np.abs(o.B).max()
+        assert abs(e_g - e_o) <= 1e-12, (e_g, e_o)
+    else:
+        assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
+    # the exact pseudo-inverse on the same handle is no worse (it is optimal in range(L_1))
+    h.set_second_sketch(0, 0, 0)
+    f2 = h.factor(to_dev(A, tdt), check=False)
+    torch.cuda.synchronize()
+    e_x = oracle.relative_residual(A, f2.L.double().cpu().numpy(), f2.U.double().cpu().numpy(), f2.p.cpu().numpy(),
+                                   f2.q.cpu().numpy())
+    assert e_x <= e_g * (1 + 1e-6) + 1e-7
+    h.close()
+
+
+def test_second_projection_rejects_bad_sizes_and_csr(rg):
+    h = rg.RandLU(500, 400, 20, 30, 240, 1, prec="f32")
+    for k2, l2 in ((10, 100), (64, 32), (2048, 4096), (100, 8192)):
+        with pytest.raises(rg.RluError):
+            h.set_second_sketch(k2, l2, 2)
+    h.set_second_sketch(40, 320, 2)
+    import scipy.sparse
+    As = scipy.sparse.random(500, 400, density=0.02, random_state=1, format="csr", dtype=np.float32)
+    f = h.factor_csr(torch.from_numpy(As.indptr.astype(np.int64)).cuda(), torch.from_numpy(As.indices).cuda(),
+                     torch.from_numpy(As.data).cuda(), check=False)
+    assert f.status == rg.RLU_EINVAL
+    h.close()
