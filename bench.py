@@ -163,13 +163,16 @@ def run_reference(args, rank):
     return 0
 
 
-def stage_work(kind, w, a_bytes, nnz):
-    """Algorithmic work of each stage for one factorization: (amount, unit, bound)."""
+def stage_work(kind, w, a_bytes, nnz, prec="f32"):
+    """Algorithmic work of each stage for one factorization: (amount, unit, bound).
+    B = W A runs on the tensor cores except in FP64 (FP64 SIMT) and for the
+    light CSR entries (sparse)."""
     m, n, k, l = w.m, w.n, w.k, w.l
+    bflops = (2.0 * k * nnz) if kind == "csr" else (2.0 * k * m * n)
     return {
         "sketch": (a_bytes, "bytes", "hbm"),
         "panel_lu": (algorithmic_flops_panel_lu(m, l), "fp64_flops", "alu"),
-        "bgemm": ((2.0 * k * nnz) if kind == "csr" else (2.0 * k * m * n), "flops", "tensor"),
+        "bgemm": (bflops, "fp64_flops", "alu") if prec == "f64" else (bflops, "flops", "tensor"),
     }
 
 
@@ -362,7 +365,7 @@ def main():
 
     if rank == 0:
         peaks, peak_kind = measured_peaks()
-        works = stage_work(kind, w, a_bytes, nnz)
+        works = stage_work(kind, w, a_bytes, nnz, prec)
         dom = max(stage_acc, key=stage_acc.get)
         roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None}
