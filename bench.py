@@ -52,6 +52,11 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
+# of the current kernels (profiles/top_kernels_dense_f32_8192.md: k_pivoted_lu of Y);
+# a workload without a capture of its current dominant kernel reports null.
+MEASURED_TRAFFIC = {("dense_f32_8192x8192_k200", "panel_lu"): 14484480 + 512}
+
 # FP64 vector peak: 152 SMs x 2 FP64 FMA/clk/SM (1/64 of the 128 FP32 FMA/clk/SM)
 # x 2 flop x 2.07 GHz max clock = 1.259 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -368,7 +373,7 @@ def main():
         works = stage_work(kind, w, a_bytes, nnz, prec)
         dom = max(stage_acc, key=stage_acc.get)
         roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None}
+                "traffic": MEASURED_TRAFFIC.get((args.workload, dom)) if prec == prec_default else None}
         if dom in works:
             amount, unit, bound = works[dom]
             secs = stage_acc[dom] / 1e3
