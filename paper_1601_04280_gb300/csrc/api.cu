@@ -390,7 +390,11 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   h->ev_recorded = 0;
   if ((rc = mark(h, 0, st))) return rc;
   // step 1: S, D, R
-  h->sk.chunk = sketch_chunk_cols(dtype);
+  {
+    const size_t es = dtype == RLU_F64 ? 8 : (dtype == RLU_F32 ? 4 : 2);
+    const bool al = ((uintptr_t)A % 16 == 0) && (((size_t)lda * es) % 16 == 0);
+    h->sk.chunk = sketch_chunk_cols(dtype, m, n, l1, al, h->num_sms);
+  }
   h->sk.nchunks = cdiv(n, h->sk.chunk);
   if ((rc = launch_sketch_params(h->sk, n, l1, l, h->seed, st))) return rc;
   if ((rc = mark(h, 1, st))) return rc;
@@ -485,7 +489,8 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   RLU_CUDA_TRY(cudaMemsetAsync(h->status_dev, 0, sizeof(unsigned int), st));
   h->ev_recorded = 0;
   if ((rc = mark(h, 0, st))) return rc;
-  h->sk.chunk = sketch_chunk_cols(dtype);
+  // heavy rows are sketched from an aligned dense copy with row stride n
+  h->sk.chunk = sketch_chunk_cols(dtype, m, n, l1, true, h->num_sms);
   h->sk.nchunks = cdiv(n, h->sk.chunk);
   if ((rc = launch_sketch_params(h->sk, n, l1, l, h->seed, st))) return rc;
   CsrRows cr{};

@@ -109,7 +109,10 @@ extern "C" int rlu_sketch_dense_noalloc(const void* A, int64_t lda, int dtype, i
   ws.tw64 = reinterpret_cast<double2*>(b + kOffTw64);
   ws.tw32 = reinterpret_cast<float2*>(b + kOffTw32);
   ws.plan = make_fft_plan(l1);
-  ws.chunk = sketch_chunk_cols(dtype);
+  {
+    const size_t es = dtype == RLU_F64 ? 8 : (dtype == RLU_F32 ? 4 : 2);
+    ws.chunk = sketch_chunk_cols(dtype, m, n, l1, ((uintptr_t)A % 16 == 0) && (((size_t)lda * es) % 16 == 0), sms);
+  }
   ws.nchunks = cdiv(n, ws.chunk);
   unsigned int* status = reinterpret_cast<unsigned int*>(b + kOffStatus);
   cudaStream_t st = static_cast<cudaStream_t>(stream);

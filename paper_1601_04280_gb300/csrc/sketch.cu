@@ -164,17 +164,49 @@ template <typename V> __device__ __forceinline__ V cmi(V a) { return V{a.y, -a.x
 // The same stage applied to `nb` independent transforms at once: transform t
 // reads in + t * stride and writes out + t * stride (one barrier per stage
 // for the whole batch instead of one per transform).
+// Division by a plan constant (see FftPlan): exact for x < 2^16.
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, uint32_t m, uint32_t d) { return m ? __umulhi(x, m) : x / d; }
+__host__ __device__ __forceinline__ uint32_t div_magic(int d) {
+  return d < 2 ? 0u : (uint32_t)(((1ull << 32) + (unsigned long long)d - 1) / (unsigned long long)d);
+}
+
+// Length-5 DFT in place: X_u = sum_q x_q w^(u q), w = exp(-2 pi i / 5), from
+// the symmetric sums s = x1 + x4, x2 + x3 and differences d = x1 - x4, x2 - x3
+// (cos and sin of 2 pi / 5 and 4 pi / 5).
 template <typename V, typename S>
-__device__ void stockham_stage_batch(const V* __restrict__ in, V* __restrict__ out, int stride, int nb, int N, int r,
-                                     int p, const V* tw) {
-  const int T = N / r;
-  const int step = N / (p * r);
+__device__ __forceinline__ void dft5(V& x0, V& x1, V& x2, V& x3, V& x4) {
+  const S c1 = S(0.30901699437494742410), c2 = S(-0.80901699437494742410);
+  const S s1 = S(0.95105651629515357212), s2 = S(0.58778525229247312917);
+  const V a = cadd(x1, x4), b = csub(x1, x4), c = cadd(x2, x3), d = csub(x2, x3);
+  const V y1 = V{x0.x + c1 * a.x + c2 * c.x, x0.y + c1 * a.y + c2 * c.y};
+  const V y2 = V{x0.x + c2 * a.x + c1 * c.x, x0.y + c2 * a.y + c1 * c.y};
+  const V z1 = V{s1 * b.x + s2 * d.x, s1 * b.y + s2 * d.y};  // X1 = y1 - i z1, X4 = y1 + i z1
+  const V z2 = V{s2 * b.x - s1 * d.x, s2 * b.y - s1 * d.y};  // X2 = y2 - i z2, X3 = y2 + i z2
+  x0 = V{x0.x + a.x + c.x, x0.y + a.y + c.y};
+  x1 = V{y1.x + z1.y, y1.y - z1.x};
+  x4 = V{y1.x - z1.y, y1.y + z1.x};
+  x2 = V{y2.x + z2.y, y2.y - z2.x};
+  x3 = V{y2.x - z2.y, y2.y + z2.x};
+}
+
+// One Stockham stage (stage `st` of `plan`) applied to `nb` independent
+// transforms at once: transform t reads in + t * stride and writes out + t *
+// stride (one barrier per stage for the whole batch instead of one per
+// transform).  Butterfly i < T reads in[i + t T] (t < r), applies the twiddles
+// exp(-2 pi i t (i mod p) / (p r)) and a length-r DFT, and writes
+// out[(i - i mod p) r + i mod p + u p] (u < r).  Output is in natural order
+// after the last stage.
+template <typename V, typename S>
+__device__ void stockham_stage_batch(const V* __restrict__ in, V* __restrict__ out, int stride, int nb, int N,
+                                     const FftPlan& plan, int st, const V* tw, int t0, int nthr) {
+  const int r = plan.radix[st], p = plan.p[st], T = plan.T[st], step = plan.step[st];
+  const uint32_t mT = plan.mT[st], mp = plan.mp[st];
   const int total = nb * T;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int tb = idx / T, i = idx - tb * T;
+  for (int idx = t0; idx < total; idx += nthr) {
+    const int tb = (int)fdiv((uint32_t)idx, mT, (uint32_t)T), i = idx - tb * T;
     const V* src = in + (size_t)tb * stride;
     V* dst = out + (size_t)tb * stride;
-    const int k = i % p;
+    const int k = p == 1 ? 0 : i - (int)fdiv((uint32_t)i, mp, (uint32_t)p) * p;
     const int obase = (i - k) * r + k;
     if (r == 4) {
       V x0 = src[i], x1 = src[i + T], x2 = src[i + 2 * T], x3 = src[i + 3 * T];
@@ -207,21 +239,19 @@ __device__ void stockham_stage_batch(const V* __restrict__ in, V* __restrict__ o
       dst[obase + p] = cadd(t, u);
       dst[obase + 2 * p] = csub(t, u);
     } else if (r == 5) {
-      V x[5];
-      x[0] = src[i];
-#pragma unroll
-      for (int q = 1; q < 5; ++q) {
-        V v = src[i + q * T];
-        x[q] = k ? cmul(v, tw[q * k * step]) : v;
+      V x0 = src[i], x1 = src[i + T], x2 = src[i + 2 * T], x3 = src[i + 3 * T], x4 = src[i + 4 * T];
+      if (k) {
+        x1 = cmul(x1, tw[k * step]);
+        x2 = cmul(x2, tw[2 * k * step]);
+        x3 = cmul(x3, tw[3 * k * step]);
+        x4 = cmul(x4, tw[4 * k * step]);
       }
-      const int wstep = N / 5;
-#pragma unroll
-      for (int u = 0; u < 5; ++u) {
-        V y = x[0];
-#pragma unroll
-        for (int q = 1; q < 5; ++q) y = cadd(y, cmul(x[q], tw[((u * q) % 5) * wstep]));
-        dst[obase + u * p] = y;
-      }
+      dft5<V, S>(x0, x1, x2, x3, x4);
+      dst[obase] = x0;
+      dst[obase + p] = x1;
+      dst[obase + 2 * p] = x2;
+      dst[obase + 3 * p] = x3;
+      dst[obase + 4 * p] = x4;
     } else {
       const int wstep = N / r;
       for (int u = 0; u < r; ++u) {
@@ -470,6 +500,9 @@ __device__ __forceinline__ bool sk_mbar_wait(uint64_t* bar, uint32_t parity) {
     if (clock64() - t0 > kSpinLimitCycles) return false;
   }
 }
+__device__ __forceinline__ void sk_mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_addr(dst)),
@@ -500,6 +533,7 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_dense_tma(const TA* __restrict
   const int64_t ngroups = cdiv(m, R);
   const int nchunks = (int)cdiv(n, chunk);
   const TACC scale = TACC(1) / sqrt(TACC(l1));
+  const uint32_t ml = div_magic(l);
   // tiles of this CTA: t -> group blockIdx.x + (t / nchunks) * gridDim.x, chunk t % nchunks
   const int64_t my_groups = blockIdx.x < ngroups ? cdiv(ngroups - blockIdx.x, gridDim.x) : 0;
   const int64_t ntiles = my_groups * nchunks;
@@ -603,18 +637,15 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_dense_tma(const TA* __restrict
         __syncthreads();
         V* src = fbuf;
         V* dst = fbuf + l1;
-        int p = 1;
         for (int st = 0; st < plan.nstages; ++st) {
-          const int r = plan.radix[st];
-          stockham_stage_batch<V, TACC>(src, dst, 2 * l1, nbat, l1, r, p, twsm);
-          p *= r;
+          stockham_stage_batch<V, TACC>(src, dst, 2 * l1, nbat, l1, plan, st, twsm, threadIdx.x, blockDim.x);
           __syncthreads();
           V* tmp = src;
           src = dst;
           dst = tmp;
         }
         for (int idx = tid; idx < nbat * l; idx += NT) {
-          const int qb = idx / l, cidx = idx - qb * l;
+          const int qb = (int)fdiv((uint32_t)idx, ml, (uint32_t)l), cidx = idx - qb * l;
           const V* zz = src + (size_t)qb * 2 * l1;
           const int q2 = q0 + qb;
           const int64_t ra = row0 + 2 * q2, rb = ra + 1;
@@ -636,6 +667,328 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_dense_tma(const TA* __restrict
   }
   if (bad) set_flag(status, FLAG_NONFINITE);
   if (tid == 0 && s_fail) set_flag(status, FLAG_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
+// Fused dense sketch over whole rows (rows that fit in shared memory): warp 0
+// streams rows of A into an S-slot ring with one bulk copy per row (full /
+// empty mbarriers per slot); the other warps sum each row's buckets (bucket b
+// owned by one thread: its columns in ascending order, the same order as the
+// chunked kernels, with the bucket lists built for a single chunk = n) and
+// write d_b times the sum straight into the FFT buffer of its row pair (real
+// part for the even row, imaginary for the odd one).  After 2 pb rows the
+// batch of pb complex FFTs runs on the summing warps (named barrier 1) while
+// the ring keeps filling; the Hartley outputs of the selected frequencies go
+// to Y.  Nothing is kept in registers across rows.
+// For n < 32768 each CTA first lays the bucket lists out in shared memory as
+// 16-bit entries (column | sign << 15): buckets sorted by length (longest
+// first) in groups of 32, one group per warp pass, the t-th entries of a
+// group's 32 buckets side by side (padded with 0xffff), so a warp reads 32
+// entries in one access and its lanes run for about the same number of
+// entries.  A bucket is still summed by one thread in ascending column order,
+// so the sums are the same as with plain lists.  Lists that do not fit that
+// layout (a bucket longer than 255 entries, or too much padding) are kept as
+// plain 16-bit lists; for n >= 32768 they are read through L1.
+// ---------------------------------------------------------------------------
+constexpr int kRowSlotsMax = 4;
+
+// OR of `v` over the `nthr` threads of named barrier 1 (also a barrier).
+__device__ __forceinline__ bool bar1_any(bool v, int nthr) {
+  unsigned int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned int)v), "r"(nthr)
+      : "memory");
+  return r != 0;
+}
+
+template <typename TA, typename TACC, int NT>
+__global__ void __launch_bounds__(NT, 1) k_sketch_rows(const TA* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                                                    int l1, int l, const int32_t* __restrict__ bstart,
+                                                    const uint32_t* __restrict__ blist,
+                                                    const float* __restrict__ dsign, const int32_t* __restrict__ Rsel,
+                                                    const typename C2<TACC>::t* __restrict__ tw, FftPlan plan, int pb,
+                                                    int nslots, int lists16, double* __restrict__ Y,
+                                                    const int32_t* __restrict__ rowmap, unsigned int* status) {
+  using V = typename C2<TACC>::t;
+  constexpr int NC = NT - 32;  // summing / FFT threads
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kRowSlotsMax], empty[kRowSlotsMax];
+  __shared__ int s_fail;
+  __shared__ long long s_used;  // rows the summing warps have taken from the ring
+  const size_t rowb = (size_t)n * sizeof(TA);
+  TA* ring = reinterpret_cast<TA*>(smem);                              // [nslots][n]
+  V* twsm = reinterpret_cast<V*>(smem + (size_t)nslots * rowb);       // l1 twiddles
+  V* fbuf = twsm + l1;                                                 // [pb][2][l1]
+  TACC* zs = reinterpret_cast<TACC*>(fbuf);                            // scalar view
+  // list area: transposed layout = group offsets (ngroups + 1, int) | slot ->
+  // bucket (l1, u16) | entries (n + 1024, u16); plain layout = starts (l1 + 1,
+  // u16) | entries (n, u16), over the same bytes
+  const int ngroups = (l1 + 31) >> 5;
+  int* goff = reinterpret_cast<int*>(fbuf + (size_t)pb * 2 * l1);
+  uint16_t* ord16 = reinterpret_cast<uint16_t*>(goff + ngroups + 1);
+  uint16_t* tl16 = ord16 + l1;
+  const int tcap = (int)n + 1024;
+  uint16_t* st16 = reinterpret_cast<uint16_t*>(goff);
+  uint16_t* ls16 = st16 + l1 + 1;
+  __shared__ int s_hist[256];
+  __shared__ int s_plain;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t rows_per_batch = 2 * (int64_t)pb;
+  const int64_t nbatches = cdiv(m, rows_per_batch);
+  const TACC scale = TACC(1) / sqrt(TACC(l1));
+  const uint32_t ml = div_magic(l);
+  if (tid == 0) {
+    for (int s = 0; s < nslots; ++s) {
+      sk_mbar_init(&full[s], 1);
+      sk_mbar_init(&empty[s], 1);
+    }
+    s_fail = 0;
+    s_used = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int e = tid; e < l1; e += NT) twsm[e] = tw[e];
+  auto enc16 = [](uint32_t ent) -> uint16_t { return (uint16_t)((ent & 0x7fffu) | ((ent >> 31) << 15)); };
+  if (lists16) {
+    // counting sort of the buckets by length, longest first
+    for (int i = tid; i < 256; i += NT) s_hist[i] = 0;
+    if (tid == 0) s_plain = 0;
+    __syncthreads();
+    for (int b = tid; b < l1; b += NT) {
+      const int len = bstart[b + 1] - bstart[b];
+      if (len > 255) s_plain = 1;
+      else atomicAdd(&s_hist[255 - len], 1);
+    }
+    __syncthreads();
+    if (tid < 32) {  // exclusive scan of the 256 bins, 8 per lane
+      int v[8], sum = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { v[i] = s_hist[lane * 8 + i]; sum += v[i]; }
+      int inc = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      int run = inc - sum;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { s_hist[lane * 8 + i] = run; run += v[i]; }
+    }
+    __syncthreads();
+    if (!s_plain)
+      for (int b = tid; b < l1; b += NT) {
+        const int len = bstart[b + 1] - bstart[b];
+        ord16[atomicAdd(&s_hist[255 - len], 1)] = (uint16_t)b;
+      }
+    __syncthreads();
+    if (!s_plain && tid < 32) {  // group offsets: 32 x the length of each group's first (longest) bucket
+      int run = 0;
+      for (int g0 = 0; g0 < ngroups; g0 += 32) {
+        const int g = g0 + lane;
+        int w = 0;
+        if (g < ngroups) {
+          const int b = ord16[32 * g];
+          w = 32 * (bstart[b + 1] - bstart[b]);
+        }
+        int inc = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += t;
+        }
+        if (g < ngroups) goff[g] = run + inc - w;
+        run += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      if (lane == 0) {
+        goff[ngroups] = run;
+        if (run > tcap) s_plain = 1;
+      }
+    }
+    __syncthreads();
+    if (!s_plain) {
+      for (int k = tid; k < 32 * ngroups; k += NT) {
+        const int g = k >> 5, ln = k & 31;
+        const int L = (goff[g + 1] - goff[g]) >> 5;
+        const int b = k < l1 ? (int)ord16[k] : -1;
+        const int e0 = b >= 0 ? bstart[b] : 0, len = b >= 0 ? bstart[b + 1] - e0 : 0;
+        for (int it = 0; it < L; ++it) tl16[goff[g] + it * 32 + ln] = it < len ? enc16(blist[e0 + it]) : (uint16_t)0xffffu;
+      }
+    } else {
+      for (int b = tid; b <= l1; b += NT) st16[b] = (uint16_t)bstart[b];
+      for (int64_t e = tid; e < n; e += NT) ls16[e] = enc16(blist[e]);
+    }
+  }
+  __syncthreads();
+  const bool transposed = lists16 && !s_plain;
+
+  long long issued = 0;
+  if (tid < 32) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      for (int64_t bt = blockIdx.x; bt < nbatches; bt += gridDim.x) {
+        const int64_t row0 = bt * rows_per_batch;
+        const int rows = (int)min64(rows_per_batch, m - row0);
+        bool quit = false;
+        for (int rr = 0; rr < rows; ++rr) {
+          const int s = (int)(issued % nslots);
+          // the slot's previous row has been summed (bounded; the summing
+          // warps raise s_fail if they stop early)
+          if (issued >= nslots && !sk_mbar_wait(&empty[s], (uint32_t)(((issued / nslots) - 1) & 1))) {
+            quit = true;
+            break;
+          }
+          if (*(volatile int*)&s_fail) { quit = true; break; }
+          sk_mbar_expect_tx(&full[s], (uint32_t)rowb);
+          bulk_g2s(ring + (size_t)s * n, A + (row0 + rr) * lda, (uint32_t)rowb, &full[s]);
+          ++issued;
+        }
+        if (quit) break;
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ summing and FFT warps
+    const int ct = tid - 32;
+    long long used = 0;
+    int slot = 0;         // ring slot of row `used`
+    uint32_t phase = 0;   // its fill parity
+    bool bad = false, stop = false;
+    for (int64_t bt = blockIdx.x; bt < nbatches && !stop; bt += gridDim.x) {
+      const int64_t row0 = bt * rows_per_batch;
+      const int rows = (int)min64(rows_per_batch, m - row0);
+      for (int rr = 0; rr < (int)rows_per_batch; ++rr) {
+        const int qb = rr >> 1, part = rr & 1;
+        if (rr >= rows) {  // past the last row: that half of the pair is zero
+          for (int b = ct; b < l1; b += NC) zs[2 * ((size_t)qb * 2 * l1 + b) + part] = TACC(0);
+          continue;
+        }
+        const int s = slot;
+        const bool ok = sk_mbar_wait(&full[s], phase);
+        if (ok) {
+          const TA* row = ring + (size_t)s * n;
+          if (transposed) {
+            // warp pass over group g: lane = bucket slot, entries 32 apart
+            for (int g = ct >> 5; g < ngroups; g += NC / 32) {
+              const int base = goff[g], L = (goff[g + 1] - base) >> 5;
+              const uint16_t* pl = tl16 + base + (ct & 31);
+              TACC acc = TACC(0);
+              int it = 0;
+              for (; it + 4 <= L; it += 4) {
+                uint16_t x[4];
+                TACC v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = pl[(it + u) * 32];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = x[u] != 0xffffu ? load_acc(row + (x[u] & 0x7fffu), TACC(0)) : TACC(0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  if (x[u] != 0xffffu) acc = fma((x[u] >> 15) ? TACC(-1) : TACC(1), v[u], acc);
+              }
+              for (; it < L; ++it) {
+                const uint16_t x = pl[it * 32];
+                if (x != 0xffffu) acc = fma((x >> 15) ? TACC(-1) : TACC(1), load_acc(row + (x & 0x7fffu), TACC(0)), acc);
+              }
+              const int k = 32 * g + (ct & 31);
+              if (k < l1) {
+                const int b = ord16[k];
+                bad |= !isfinite(acc);
+                zs[2 * ((size_t)qb * 2 * l1 + b) + part] = (TACC)dsign[b] * acc;
+              }
+            }
+          } else
+          for (int b = ct; b < l1; b += NC) {
+            // entries in ascending column order, four loads in flight at a time
+            TACC acc = TACC(0);
+            if (lists16) {
+              const int e0 = st16[b], e1 = st16[b + 1];
+              int e = e0;
+              for (; e + 4 <= e1; e += 4) {
+                uint16_t x[4];
+                TACC v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = ls16[e + u];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = load_acc(row + (x[u] & 0x7fffu), TACC(0));
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc = fma((x[u] >> 15) ? TACC(-1) : TACC(1), v[u], acc);
+              }
+              for (; e < e1; ++e) {
+                const uint16_t x = ls16[e];
+                acc = fma((x >> 15) ? TACC(-1) : TACC(1), load_acc(row + (x & 0x7fffu), TACC(0)), acc);
+              }
+            } else {
+              const int e0 = __ldg(bstart + b), e1 = __ldg(bstart + b + 1);
+              int e = e0;
+              for (; e + 4 <= e1; e += 4) {
+                uint32_t x[4];
+                TACC v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = __ldg(blist + e + u);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = load_acc(row + (x[u] & 0x7fffffffu), TACC(0));
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc = fma((x[u] >> 31) ? TACC(-1) : TACC(1), v[u], acc);
+              }
+              for (; e < e1; ++e) {
+                const uint32_t x = __ldg(blist + e);
+                acc = fma((x >> 31) ? TACC(-1) : TACC(1), load_acc(row + (x & 0x7fffffffu), TACC(0)), acc);
+              }
+            }
+            bad |= !isfinite(acc);
+            zs[2 * ((size_t)qb * 2 * l1 + b) + part] = (TACC)dsign[b] * acc;
+          }
+        }
+        // every summing thread is done with slot s (or one of them timed out)
+        if (bar1_any(!ok, NC)) {
+          stop = true;
+          break;
+        }
+        ++used;
+        if (++slot == nslots) { slot = 0; phase ^= 1u; }
+        if (ct == 0) sk_mbar_arrive(&empty[s]);
+      }
+      if (stop) break;
+      // the batch's FFTs (pairs past the last row are not needed)
+      const int nbat = (rows + 1) / 2;
+      V* src = fbuf;
+      V* dst = fbuf + l1;
+      for (int st = 0; st < plan.nstages; ++st) {
+        stockham_stage_batch<V, TACC>(src, dst, 2 * l1, nbat, l1, plan, st, twsm, ct, NC);
+        asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory");
+        V* tmp = src;
+        src = dst;
+        dst = tmp;
+      }
+      for (int idx = ct; idx < nbat * l; idx += NC) {
+        const int q = (int)fdiv((uint32_t)idx, ml, (uint32_t)l), cidx = idx - q * l;
+        const V* zz = src + (size_t)q * 2 * l1;
+        const int64_t ra = row0 + 2 * q, rb = ra + 1;
+        const int f = Rsel[cidx];
+        const int fm = f == 0 ? 0 : l1 - f;
+        const V z = zz[f], w = zz[fm];
+        const TACC h1 = TACC(0.5) * ((z.x + w.x) - (z.y - w.y));
+        const TACC h2 = TACC(0.5) * ((z.x - w.x) + (z.y + w.y));
+        Y[(rowmap ? (int64_t)rowmap[ra] : ra) * l + cidx] = (double)(h1 * scale);
+        if (rb < m) Y[(rowmap ? (int64_t)rowmap[rb] : rb) * l + cidx] = (double)(h2 * scale);
+      }
+      // the next batch writes the FFT inputs again
+      asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory");
+    }
+    if (bad) set_flag(status, FLAG_NONFINITE);
+    if (ct == 0) {
+      if (stop) {
+        *(volatile int*)&s_fail = 1;
+        set_flag(status, FLAG_TIMEOUT);
+      }
+      s_used = used;
+    }
+  }
+  __syncthreads();
+  // copies still in flight (only after a failure): wait for them (bounded)
+  // before the CTA's shared memory is released
+  if (tid == 0) {
+    for (long long u = s_used; u < issued; ++u) sk_mbar_wait(&full[u % nslots], (uint32_t)((u / nslots) & 1));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -705,11 +1058,12 @@ __device__ void csr_pairs_fft(const TACC* __restrict__ yrows, int np, const int3
                               double* __restrict__ Y) {
   using V = typename C2<TACC>::t;
   const TACC scale = TACC(1) / sqrt(TACC(l1));
+  const uint32_t ml = div_magic(l), ml1 = div_magic(l1);
   for (int q0 = 0; q0 < np; q0 += pb) {
     const int nbat = min(pb, np - q0);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nbat * l1; idx += blockDim.x) {
-      const int qb = idx / l1, b = idx - qb * l1;
+      const int qb = (int)fdiv((uint32_t)idx, ml1, (uint32_t)l1), b = idx - qb * l1;
       const int q2 = q0 + qb;
       const TACC ds = (TACC)dsign[b];
       fbuf[(size_t)qb * 2 * l1 + b] = V{ds * yrows[(size_t)(2 * q2) * l1 + b], ds * yrows[(size_t)(2 * q2 + 1) * l1 + b]};
@@ -717,18 +1071,15 @@ __device__ void csr_pairs_fft(const TACC* __restrict__ yrows, int np, const int3
     __syncthreads();
     V* src = fbuf;
     V* dst = fbuf + l1;
-    int p = 1;
     for (int st = 0; st < plan.nstages; ++st) {
-      const int r = plan.radix[st];
-      stockham_stage_batch<V, TACC>(src, dst, 2 * l1, nbat, l1, r, p, twsm);
-      p *= r;
+      stockham_stage_batch<V, TACC>(src, dst, 2 * l1, nbat, l1, plan, st, twsm, threadIdx.x, blockDim.x);
       __syncthreads();
       V* tmp = src;
       src = dst;
       dst = tmp;
     }
     for (int idx = threadIdx.x; idx < nbat * l; idx += blockDim.x) {
-      const int qb = idx / l, cidx = idx - qb * l;
+      const int qb = (int)fdiv((uint32_t)idx, ml, (uint32_t)l), cidx = idx - qb * l;
       const V* zz = src + (size_t)qb * 2 * l1;
       const int q2 = q0 + qb;
       const int f = Rsel[cidx];
@@ -884,6 +1235,16 @@ FftPlan make_fft_plan(int N) {
   for (int f = 3; x > 1; f += 2) {
     while (x % f == 0) { push(f); x /= f; }
   }
+  int p = 1;
+  for (int s = 0; s < pl.nstages; ++s) {
+    const int r = pl.radix[s];
+    pl.p[s] = p;
+    pl.T[s] = N / r;
+    pl.step[s] = N / (p * r);
+    pl.mT[s] = div_magic(N / r);
+    pl.mp[s] = div_magic(p);
+    p *= r;
+  }
   return pl;
 }
 
@@ -918,7 +1279,46 @@ int launch_twiddles(int N, double2* tw64, float2* tw32, cudaStream_t st) {
   return RLU_OK;
 }
 
-int sketch_chunk_cols(int dtype) {
+// Shape of the whole-row sketch (k_sketch_rows) for rows of n elements of
+// `es` bytes: ring slots and row pairs per FFT batch, or {0, 0} when the rows
+// do not fit (or cannot be bulk-copied: rows must start on 16-byte boundaries
+// and span a multiple of 16 bytes).
+struct RowsShape {
+  int nslots, pb;
+};
+static size_t rows_lists16_bytes(int64_t n, int l1) {
+  // transposed layout (the larger of the two): group offsets, slot map, padded entries
+  if (n >= 32768) return 0;
+  const size_t b = (size_t)4 * ((l1 + 31) / 32 + 1) + (size_t)2 * l1 + (size_t)2 * (n + 1024);
+  return (b + 15) & ~(size_t)15;
+}
+static RowsShape rows_shape(int64_t m, int64_t n, int l1, size_t es, size_t sv, bool aligned, int num_sms) {
+  const size_t budget = 225 * 1024 - rows_lists16_bytes(n, l1);
+  const size_t rowb = (size_t)n * es;
+  if (!aligned || rowb % 16 != 0 || n < 1 || rows_lists16_bytes(n, l1) >= 225 * 1024) return {0, 0};
+  int pb_cap = (int)(m / (2 * (int64_t)(num_sms > 0 ? num_sms : 1)));
+  pb_cap = pb_cap < 1 ? 1 : (pb_cap > 8 ? 8 : pb_cap);
+  const size_t pair = (size_t)2 * l1 * sv, fixed = (size_t)l1 * sv;
+  auto pairs_with = [&](int ns) -> int {
+    const size_t used = (size_t)ns * rowb + fixed;
+    if (used + pair > budget) return 0;
+    const int64_t p = (int64_t)((budget - used) / pair);
+    return (int)(p < pb_cap ? p : pb_cap);
+  };
+  const int want = pb_cap < 2 ? pb_cap : 2;
+  for (int ns = 3; ns >= 2; --ns) {
+    const int pb = pairs_with(ns);
+    if (pb >= want) return {ns, pb};
+  }
+  const int pb = pairs_with(2);
+  if (pb >= 1) return {2, pb};
+  return {0, 0};
+}
+
+int sketch_chunk_cols(int dtype, int64_t m, int64_t n, int l1, bool aligned, int num_sms) {
+  const size_t es = dtype == RLU_F64 ? 8 : (dtype == RLU_F32 ? 4 : 2);
+  const size_t sv = dtype == RLU_F64 ? 16 : 8;
+  if (rows_shape(m, n, l1, es, sv, aligned, num_sms).nslots > 0) return (int)n;  // one chunk: whole rows
   // 32 KB of A per staged tile (a two-stage ring leaves room for batched FFT buffers)
   if (dtype == RLU_F64) return 1024;  // 4 rows x 1024 x 8 B
   if (dtype == RLU_F32) return 1024;  // 8 rows x 1024 x 4 B
@@ -964,9 +1364,44 @@ static int launch_dense_tma_cfg(const void* A, int64_t lda, int64_t m, int64_t n
   return RLU_OK;
 }
 
+template <typename TA, typename TACC>
+static int launch_rows_cfg(const void* A, int64_t lda, int64_t m, int64_t n, int l1, int l, const SketchWs& ws,
+                           double* Y, const int32_t* rowmap, unsigned int* status, int num_sms, RowsShape sh,
+                           cudaStream_t st) {
+  constexpr int NT = 1024;
+  auto kern = k_sketch_rows<TA, TACC, NT>;
+  using V = typename C2<TACC>::t;
+  const size_t lb = rows_lists16_bytes(n, l1);
+  const int lists16 = lb > 0 ? 1 : 0;
+  const size_t smem =
+      (size_t)sh.nslots * n * sizeof(TA) + (size_t)l1 * sizeof(V) + (size_t)sh.pb * 2 * l1 * sizeof(V) + lb;
+  if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
+  int per_sm = 0;
+  RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+  if (per_sm < 1) return RLU_EINVAL;
+  const int64_t batches = cdiv(m, 2 * (int64_t)sh.pb);
+  int64_t grid = (int64_t)per_sm * num_sms;
+  if (grid > batches) grid = batches;
+  const V* tw;
+  if constexpr (sizeof(TACC) == 8) tw = ws.tw64; else tw = ws.tw32;
+  kern<<<(unsigned)grid, NT, smem, st>>>(reinterpret_cast<const TA*>(A), lda, m, n, l1, l, ws.bstart, ws.blist,
+                                         ws.dsign, ws.R, tw, ws.plan, sh.pb, sh.nslots, lists16, Y, rowmap,
+                                         status);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return RLU_OK;
+}
+
 template <typename TA, typename TACC, int NT, int NB, int R>
 static int launch_dense_cfg(const void* A, int64_t lda, int64_t m, int64_t n, int l1, int l, const SketchWs& ws,
                             double* Y, const int32_t* rowmap, unsigned int* status, int num_sms, cudaStream_t st) {
+  // whole rows when the bucket lists were built for one chunk and the rows fit
+  if (ws.chunk == n) {
+    const bool al = ((uintptr_t)A % 16 == 0) && ((lda * (int64_t)sizeof(TA)) % 16 == 0);
+    const RowsShape sh = rows_shape(m, n, l1, sizeof(TA), sizeof(typename C2<TACC>::t), al, num_sms);
+    if (sh.nslots > 0)
+      return launch_rows_cfg<TA, TACC>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, sh, st);
+  }
   // TMA-fed kernel when every row segment is a 16-byte-aligned run of 16-byte multiples
   // and the ring plus FFT buffers fit in shared memory
   const bool aligned = ((uintptr_t)A % 16 == 0) && ((lda * (int64_t)sizeof(TA)) % 16 == 0) &&

@@ -8,9 +8,19 @@ namespace rlu {
 constexpr int kMaxFftStages = 24;
 
 // Radices of the mixed-radix FFT of length l1, applied in order.
+// Mixed-radix plan of an N-point Stockham FFT.  Per stage: radix r, the
+// product p of the radices already applied, T = N / r butterflies per
+// transform, the twiddle stride N / (p r), and multipliers for division by T
+// and by p without a divide instruction: for 0 <= x < 2^16 and 2 <= d < 2^16,
+// floor(x / d) = umulhi(x, ceil(2^32 / d)) exactly (0 marks d = 1).
 struct FftPlan {
   int nstages;
   int radix[kMaxFftStages];
+  int p[kMaxFftStages];
+  int T[kMaxFftStages];
+  int step[kMaxFftStages];
+  uint32_t mT[kMaxFftStages];
+  uint32_t mp[kMaxFftStages];
 };
 
 // Device buffers of the sketch step (owned by the handle).
@@ -39,7 +49,10 @@ struct CsrRows {
 };
 
 FftPlan make_fft_plan(int N);
-int sketch_chunk_cols(int dtype);
+// Columns per staged tile of the dense sketch: all n (whole rows, one chunk)
+// when the rows of A (`aligned`: 16-byte aligned base and row stride) fit the
+// whole-row kernel, else a fixed width by element size.
+int sketch_chunk_cols(int dtype, int64_t m, int64_t n, int l1, bool aligned, int num_sms);
 int launch_sketch_params(const SketchWs& ws, int64_t n, int l1, int l, uint64_t seed, cudaStream_t st);
 int launch_twiddles(int N, double2* tw64, float2* tw32, cudaStream_t st);
 // exclusive scan of count int32 values into count + 1 offsets (one CTA)
