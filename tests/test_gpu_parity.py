@@ -142,6 +142,35 @@ def test_sketch_Y_bf16(rg):
     assert np.abs(g["Y"] - Yo).max() <= 5e-6 * rown
 
 
+# Shapes that reach each way the dense sketch reads A: whole rows with the
+# lists sorted and transposed per warp (the cases above), whole rows with plain
+# 16-bit lists (a bucket longer than 255 entries), whole rows with the lists
+# read through L1 (n >= 32768), and column chunks (rows too long for shared
+# memory).  Same bar as the FP32 cases above.
+SKETCH_LAYOUT_CASES = [
+    ("f32", 50, 20000, 32, 16),     # ~625 entries per bucket: plain lists
+    ("bf16", 60, 40000, 2000, 50),  # n >= 32768: lists through L1
+    ("f32", 64, 60000, 960, 60),    # 240 KB rows: column chunks
+    ("f32", 13, 4096, 1600, 12),    # odd row count, batches of one pair
+]
+
+
+@pytest.mark.parametrize("dt,m,n,l1,l", SKETCH_LAYOUT_CASES)
+def test_sketch_Y_layouts(rg, dt, m, n, l1, l):
+    rng = np.random.default_rng(m + n + l1)
+    if dt == "bf16":
+        A = ri.round_to_bf16(rng.standard_normal((m, n)))[0]
+        tdt = torch.bfloat16
+    else:
+        A = rng.standard_normal((m, n)).astype(np.float32)
+        tdt = torch.float32
+    g = run(rg, A, min(l, 8), l, l1, 81, "f32", tdt, debug=True)
+    pr = oracle.sketch_params(n, l1, l, 81)
+    Yo = oracle.fjl(oracle.countsketch(A.astype(np.float64), pr, l1), pr, l1)
+    rown = np.linalg.norm(A.astype(np.float64), axis=1).max()
+    assert np.abs(g["Y"] - Yo).max() <= 5e-6 * rown
+
+
 # ---------------------------------------------------------------------------
 # Whole factorizations
 # ---------------------------------------------------------------------------
