@@ -43,25 +43,20 @@ __global__ void k_sketch_params(int64_t n, int l1, uint64_t seed, uint32_t* hs, 
 }
 
 // R = the l indices b with the smallest (key[b], b), in increasing order:
-// each b counts the keys below its own and, if that rank is < l, lands at R[rank].
+// each b counts the keys below its own (one warp per b, the lanes splitting
+// the l1 keys) and, if that rank is < l, lands at R[rank].
 __global__ void k_select_R(int l1, int l, const uint64_t* keys, int32_t* R) {
-  __shared__ uint64_t sk[1024];
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  uint64_t kb = b < l1 ? keys[b] : 0;
+  const int b = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (b >= l1) return;
+  const uint64_t kb = keys[b];
   int rank = 0;
-  for (int base = 0; base < l1; base += 1024) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < 1024 && base + t < l1; t += blockDim.x) sk[t] = keys[base + t];
-    __syncthreads();
-    int lim = min(1024, l1 - base);
-    if (b < l1) {
-      for (int t = 0; t < lim; ++t) {
-        uint64_t kt = sk[t];
-        rank += (kt < kb) || (kt == kb && base + t < b);
-      }
-    }
+  for (int t = lane; t < l1; t += 32) {
+    const uint64_t kt = __ldg(keys + t);
+    rank += (kt < kb) || (kt == kb && t < b);
   }
-  if (b < l1 && rank < l) R[rank] = b;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+  if (lane == 0 && rank < l) R[rank] = b;
 }
 
 // ---------------------------------------------------------------------------
@@ -111,6 +106,81 @@ __global__ void k_bucket_fill(int64_t n, int l1, int chunk, const uint32_t* hs, 
     int64_t sb = c * l1 + (e & 0x7fffffffu);
     int pos = start[sb] + atomicAdd(&cursor[sb], 1);
     list[pos] = (uint32_t)(j - c * chunk) | (e & 0x80000000u);
+  }
+}
+
+// All of the above in one CTA when the super-buckets fit in shared memory:
+// counts, exclusive scan into start[0..count], fill, then each list sorted by
+// column.  Same lists as the four kernels.
+constexpr int kListsOneMax = 8192;
+__global__ void __launch_bounds__(1024) k_bucket_lists_one(int64_t n, int l1, int chunk, int count,
+                                                           const uint32_t* __restrict__ hs, int32_t* start,
+                                                           uint32_t* list) {
+  extern __shared__ int lsm[];  // cnt[count + 1], cursor[count]
+  __shared__ int wsum[32];
+  int* cnt = lsm;
+  int* cur = lsm + count + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i <= count; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  for (int64_t j = tid; j < n; j += blockDim.x) atomicAdd(&cnt[(j / chunk) * l1 + (hs[j] & 0x7fffffffu)], 1);
+  __syncthreads();
+  // exclusive scan: a contiguous segment per thread, then warp and block offsets
+  const int per = (count + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int a = min(count, tid * per), e = min(count, a + per);
+  int sum = 0;
+  for (int i = a; i < e; ++i) sum += cnt[i];
+  int inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (int)blockDim.x >> 5;
+    int v = lane < nw ? wsum[lane] : 0, w = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    if (lane < nw) wsum[lane] = w - v;
+    if (lane == 31) cnt[count] = w;  // total (cnt[count] is not part of any segment)
+  }
+  __syncthreads();
+  int run = wsum[warp] + inc - sum;
+  for (int i = a; i < e; ++i) {
+    const int v = cnt[i];
+    cnt[i] = run;
+    run += v;
+  }
+  __syncthreads();
+  for (int i = tid; i <= count; i += blockDim.x) {
+    start[i] = cnt[i];
+    if (i < count) cur[i] = cnt[i];
+  }
+  __syncthreads();
+  for (int64_t j = tid; j < n; j += blockDim.x) {
+    const uint32_t v = hs[j];
+    const int64_t c = j / chunk;
+    const int pos = atomicAdd(&cur[c * l1 + (v & 0x7fffffffu)], 1);
+    list[pos] = (uint32_t)(j - c * chunk) | (v & 0x80000000u);
+  }
+  __syncthreads();
+  for (int sb = tid; sb < count; sb += blockDim.x) {
+    const int lo = cnt[sb], hi = cnt[sb + 1];
+    for (int i = lo + 1; i < hi; ++i) {
+      const uint32_t v = list[i];
+      const uint32_t kv = v & 0x7fffffffu;
+      int t = i - 1;
+      while (t >= lo && (list[t] & 0x7fffffffu) > kv) {
+        list[t + 1] = list[t];
+        --t;
+      }
+      list[t + 1] = v;
+    }
   }
 }
 
@@ -1251,9 +1321,17 @@ FftPlan make_fft_plan(int N) {
 int launch_sketch_params(const SketchWs& ws, int64_t n, int l1, int l, uint64_t seed, cudaStream_t st) {
   int64_t cnt = n > l1 ? n : l1;
   k_sketch_params<<<(unsigned)cdiv(cnt, 256), 256, 0, st>>>(n, l1, seed, ws.hs, ws.dsign, ws.keys);
-  k_select_R<<<(unsigned)cdiv(l1, 256), 256, 0, st>>>(l1, l, ws.keys, ws.R);
+  k_select_R<<<(unsigned)cdiv((int64_t)l1 * 32, 256), 256, 0, st>>>(l1, l, ws.keys, ws.R);
   // bucket lists for the dense path
   const int64_t nsb = ws.nchunks * (int64_t)l1;
+  if (nsb <= kListsOneMax) {
+    const size_t smem = sizeof(int) * (size_t)(2 * nsb + 1);
+    if (int rc_ = allow_dynamic_smem((const void*)k_bucket_lists_one, smem)) return rc_;
+    k_bucket_lists_one<<<1, 1024, smem, st>>>(n, l1, ws.chunk, (int)nsb, ws.hs, ws.bstart, ws.blist);
+    RLU_CUDA_TRY(cudaGetLastError());
+    note_launch(3);
+    return RLU_OK;
+  }
   RLU_CUDA_TRY(cudaMemsetAsync(ws.bcnt, 0, sizeof(int32_t) * (nsb + 1), st));
   k_bucket_count<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, l1, ws.chunk, ws.hs, ws.bcnt);
   k_scan_counts<<<1, 1024, 0, st>>>(nsb, ws.bcnt, ws.bstart);
