@@ -429,9 +429,11 @@ int launch_assemble(const AssembleArgs& a, cudaStream_t st) {
                                                                           reinterpret_cast<TO*>(a.U));
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch(3);
-  // L = L_y L_b: float-float (or FP64) by default; FP32 accumulation in the
-  // BF16 forms, whose error is set by the BF16 representation of A and W
-  // (~1e-3 of ||A||), far above an FP32 product's
+  // L = L_y L_b: FP64 in the FP64 mode; FP32 accumulation over the k terms in
+  // the others, whose L is FP32: that rounding (about sqrt(k) units of 2^-24
+  // per entry) moves ||L U - P A Q|| / ||A|| far less than the FP32 sketch and
+  // the FP32 input do (dense FP32 8192^2: 3.2e-6 with an FP32 product or a
+  // float-float one)
   int rc;
   if (a.fp32_product && !std::is_same<T, double>::value)
     rc = gemm_simt<T, T, TO, float>(st, m, k, k, LyP, k, 1, Lb, k, 1, reinterpret_cast<TO*>(a.L), k, 1);

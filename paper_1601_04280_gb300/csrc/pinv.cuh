@@ -39,7 +39,7 @@ struct AssembleArgs {
   void* U;                // k x n output
   int64_t* p;
   int64_t* q;
-  int fp32_product;  // L = L_y L_b with FP32 accumulation (the BF16 forms) instead of float-float
+  int fp32_product;  // L = L_y L_b with FP32 accumulation (FP32 and BF16 forms) instead of float-float
 };
 
 int launch_gram(const PinvArgs& a, cudaStream_t st);
