@@ -394,7 +394,7 @@ def main():
             slot_step(slot)
 
     from concurrent.futures import ThreadPoolExecutor
-    pipe_steps = 2 * e2e_steps
+    pipe_steps = 4 * e2e_steps  # a longer window: two host threads make this figure noisier
     with ThreadPoolExecutor(2) as ex:
         list(ex.map(lambda sl: run_slot(sl, 1), slots))  # warm the second handle
         barrier()

@@ -35,7 +35,7 @@ __global__ void k_extract_Lk(int64_t m, int l, int k, const double* __restrict__
 constexpr int kNb = 32;
 
 __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S, double* __restrict__ Rinv,
-                                                  unsigned int* bar, unsigned int* status) {
+                                                  unsigned int* bar, unsigned int* status, int tri_smem) {
   // FP64 on this part has long latency as well as low throughput, so every
   // sequential chain below is spread over threads: one thread per element in
   // the diagonal factor, one warp per column (lanes = rows) in the triangular
@@ -135,32 +135,51 @@ __global__ void __launch_bounds__(256) k_chol_inv(int k, double* __restrict__ S,
     }
   }
   // R^{-1} column by column, FP64: column j solves R x = e_j from the bottom
-  // up, one warp per column; the working vector lives in this warp's part of
-  // shared memory.  R's columns are first copied, transposed, into the free
-  // strictly lower triangle of S (S[t][i] = R[i][t], i < t), so that the
-  // update with column t reads contiguous memory.
+  // up, one warp per column, the working vector w in this warp's part of
+  // shared memory.  R's columns, each scaled by 1 / R[t][t], are first written
+  // into the free strictly lower triangle of S (S[t][i] = R[i][t] / R[t][t],
+  // i < t), so that a step of the solve is one FMA per entry on the dependent
+  // chain, w_i -= S[t][i] w_t, and x_t = w_t / R[t][t] is taken at the end.
+  // A CTA that owns columns first copies the rows it reads into shared memory
+  // (packed: row t at t (t - 1) / 2) when tri_smem is set.
   if (!grid_barrier(bar, ++epoch, status)) return;
   for (int64_t e = gtid; e < (int64_t)k * k; e += gthreads) {
     const int t = (int)(e / k), i = (int)(e - (int64_t)t * k);
-    if (i < t) S[(int64_t)t * k + i] = S[(int64_t)i * k + t];
+    if (i < t) S[(int64_t)t * k + i] = S[(int64_t)i * k + t] * (1.0 / S[(int64_t)t * k + t]);
   }
   if (!grid_barrier(bar, ++epoch, status)) return;
   extern __shared__ __align__(16) unsigned char chol_smem[];
   double* rdg = reinterpret_cast<double*>(chol_smem);                     // k: 1 / R[i][i]
   double* xw = rdg + k + (size_t)warp * k;                                 // k per warp
+  double* tri = rdg + (size_t)(NW + 1) * k;                                // packed scaled rows
   for (int i = tid; i < k; i += blockDim.x) rdg[i] = 1.0 / S[(int64_t)i * k + i];
+  int T = 0;  // rows this CTA reads: up to its last column
+  for (int64_t j = (int64_t)blockIdx.x * NW; j < k; j += nwarps) T = (int)min((int64_t)k, j + NW);
+  if (tri_smem)
+    for (int t = warp; t < T; t += NW)
+      for (int i = lane; i < t; i += 32) tri[(size_t)t * (t - 1) / 2 + i] = S[(int64_t)t * k + i];
   __syncthreads();
   for (int64_t j = gwarp; j < k; j += nwarps) {
     for (int i = lane; i <= j; i += 32) xw[i] = (i == j) ? 1.0 : 0.0;
     __syncwarp();
-    for (int t = (int)j; t >= 0; --t) {
-      const double xt = xw[t] * rdg[t];  // every lane, same value
-      const double* rt = S + (int64_t)t * k;               // rt[i] = R[i][t], i < t
-      for (int i = lane; i < t; i += 32) xw[i] = fma(-xt, rt[i], xw[i]);
-      if (lane == 0) xw[t] = xt;
-      __syncwarp();
+    // two loops so that the row loads of the global-memory one are known not
+    // to alias w (and can be issued ahead of the chain)
+    if (tri_smem) {
+      for (int t = (int)j; t > 0; --t) {
+        const double wt = xw[t];  // final: every step above t has been applied
+        const double* rt = tri + (size_t)t * (t - 1) / 2;
+        for (int i = lane; i < t; i += 32) xw[i] = fma(-wt, rt[i], xw[i]);
+        __syncwarp();
+      }
+    } else {
+      for (int t = (int)j; t > 0; --t) {
+        const double wt = xw[t];
+        const double* __restrict__ rt = S + (int64_t)t * k;
+        for (int i = lane; i < t; i += 32) xw[i] = fma(-wt, __ldcg(rt + i), xw[i]);
+        __syncwarp();
+      }
     }
-    for (int i = lane; i < k; i += 32) Rinv[(int64_t)i * k + j] = (i <= j) ? xw[i] : 0.0;
+    for (int i = lane; i < k; i += 32) Rinv[(int64_t)i * k + j] = (i <= j) ? xw[i] * rdg[i] : 0.0;
     __syncwarp();
   }
 }
@@ -328,7 +347,12 @@ int launch_gram(const PinvArgs& a, cudaStream_t st) {
 int launch_chol(const PinvArgs& a, cudaStream_t st) {
   const int k = a.k;
   RLU_CUDA_TRY(cudaMemsetAsync(a.bar, 0, sizeof(unsigned int), st));
-  const size_t smem = (size_t)9 * k * sizeof(double);  // 1/diag(R) and one k-vector per warp (R^{-1} columns)
+  // 1/diag(R) and one k-vector per warp (R^{-1} columns), and the scaled
+  // triangle of R when it fits
+  const size_t base = (size_t)9 * k * sizeof(double);
+  const size_t trib = (size_t)k * (k - 1) / 2 * sizeof(double);
+  int tri_smem = base + trib <= 200 * 1024 ? 1 : 0;
+  const size_t smem = base + (tri_smem ? trib : 0);
   if (int rc_ = allow_dynamic_smem((const void*)k_chol_inv, smem)) return rc_;
   int per_sm = 0;
   RLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_inv, 256, smem));
@@ -339,7 +363,7 @@ int launch_chol(const PinvArgs& a, cudaStream_t st) {
   int kk = k;
   unsigned int* bar = a.bar;
   unsigned int* status = a.status;
-  void* args[] = {&kk, &Sm, &Ri, &bar, &status};
+  void* args[] = {&kk, &Sm, &Ri, &bar, &status, &tri_smem};
   RLU_CUDA_TRY(launch_cooperative((void*)k_chol_inv, G, 256, args, smem, st));
   note_launch();
   return RLU_OK;
