@@ -469,6 +469,7 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   aa.Lk = h->Lk; aa.perm_y = h->perm_y; aa.perm_b = h->perm_b; aa.Bp = h->B;
   aa.LyP = h->LyP; aa.Lb = h->Lb; aa.L = L; aa.U = U; aa.p = p; aa.q = q;
   aa.fp32_product = h->prec != RLU_PREC_F64 ? 1 : 0;  // FP32 outputs: an FP32 product suffices
+  aa.num_sms = coop_sms(h);
   rc = f64 ? launch_assemble<double, double>(aa, st) : launch_assemble<df32, float>(aa, st);
   if (rc) return rc;
   if ((rc = mark(h, 9, st))) return rc;
@@ -542,6 +543,7 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   aa.Lk = h->Lk; aa.perm_y = h->perm_y; aa.perm_b = h->perm_b; aa.Bp = h->B;
   aa.LyP = h->LyP; aa.Lb = h->Lb; aa.L = L; aa.U = U; aa.p = p; aa.q = q;
   aa.fp32_product = h->prec != RLU_PREC_F64 ? 1 : 0;  // FP32 outputs: an FP32 product suffices
+  aa.num_sms = coop_sms(h);
   rc = f64 ? launch_assemble<double, double>(aa, st) : launch_assemble<df32, float>(aa, st);
   if (rc) return rc;
   if ((rc = mark(h, 9, st))) return rc;

@@ -427,6 +427,69 @@ __global__ void k_build_Lb(int k, int64_t n, const T* __restrict__ Bp, const int
   Lb[e] = (c >= j) ? Bp[(int64_t)c * n + q[j]] : zero_<T>();
 }
 
+// L = (P L_y) L_b with FP32 products and FP32 accumulation, L_b (k x k,
+// lower triangular) resident in shared memory as FP32 and the rows of P L_y
+// gathered from Lk on the fly (row i of P L_y = row perm[i] of Lk).  A warp
+// takes four rows at a time: lane owns columns j = lane + 32 q of them, and
+// each L_b entry read from shared memory serves four rows.  The k-term sums
+// run in ascending order of the summation index.
+constexpr int kAsmRows = 4;
+constexpr int kAsmMaxQ = 8;  // k <= 256
+template <typename T, typename TO, int Q>
+__global__ void __launch_bounds__(512, 1) k_assemble_rows(int64_t m, int k, const T* __restrict__ Lk,
+                                                       const int64_t* __restrict__ perm, const T* __restrict__ Lb,
+                                                       TO* __restrict__ L) {
+  extern __shared__ __align__(16) float lbs[];  // k x k
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) lbs[e] = to_float(Lb[e]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t tasks = cdiv(m, kAsmRows);
+  for (int64_t task = wid; task < tasks; task += nw) {
+    const int64_t i0 = task * kAsmRows;
+    const T* src[kAsmRows];
+#pragma unroll
+    for (int r = 0; r < kAsmRows; ++r) src[r] = i0 + r < m ? Lk + perm[i0 + r] * k : nullptr;
+    float acc[kAsmRows][Q];
+#pragma unroll
+    for (int r = 0; r < kAsmRows; ++r)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[r][q] = 0.f;
+    // the next 32 entries of the four rows are loaded while these are used
+    float an[kAsmRows];
+#pragma unroll
+    for (int r = 0; r < kAsmRows; ++r) an[r] = (src[r] && lane < k) ? to_float(src[r][lane]) : 0.f;
+    for (int t0 = 0; t0 < k; t0 += 32) {
+      float a[kAsmRows];
+#pragma unroll
+      for (int r = 0; r < kAsmRows; ++r) {
+        a[r] = an[r];
+        an[r] = (src[r] && t0 + 32 + lane < k) ? to_float(src[r][t0 + 32 + lane]) : 0.f;
+      }
+      const int tn = min(32, k - t0);
+      for (int tt = 0; tt < tn; ++tt) {
+        const float* brow = lbs + (size_t)(t0 + tt) * k;
+        float b[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) b[q] = lane + 32 * q < k ? brow[lane + 32 * q] : 0.f;
+#pragma unroll
+        for (int r = 0; r < kAsmRows; ++r) {
+          const float av = __shfl_sync(0xffffffffu, a[r], tt);
+#pragma unroll
+          for (int q = 0; q < Q; ++q) acc[r][q] = fmaf(av, b[q], acc[r][q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kAsmRows; ++r)
+      if (i0 + r < m)
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (lane + 32 * q < k) L[(i0 + r) * k + lane + 32 * q] = (TO)acc[r][q];
+  }
+}
+
 template <typename T, typename TO>
 __global__ void k_build_U(int k, int64_t n, const T* __restrict__ Bp, const int64_t* __restrict__ q,
                           TO* __restrict__ U) {
@@ -446,20 +509,34 @@ int launch_assemble(const AssembleArgs& a, cudaStream_t st) {
   T* LyP = reinterpret_cast<T*>(a.LyP);
   T* Lb = reinterpret_cast<T*>(a.Lb);
   const T* Bp = reinterpret_cast<const T*>(a.Bp);
-  k_build_LyP<T><<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, k, reinterpret_cast<const T*>(a.Lk), a.perm_y,
-                                                              LyP);
+  // the FP32 product with L_b resident in shared memory needs no P L_y copy
+  const bool rows_kernel = a.fp32_product && !std::is_same<T, double>::value && k <= 32 * kAsmMaxQ &&
+                           (size_t)k * k * sizeof(float) <= 200 * 1024 && a.num_sms > 0;
+  if (!rows_kernel) {
+    k_build_LyP<T><<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, k, reinterpret_cast<const T*>(a.Lk), a.perm_y,
+                                                                LyP);
+    note_launch();
+  }
   k_build_Lb<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(k, n, Bp, a.perm_b, Lb);
   k_build_U<T, TO><<<(unsigned)cdiv((int64_t)k * n, 256), 256, 0, st>>>(k, n, Bp, a.perm_b,
                                                                           reinterpret_cast<TO*>(a.U));
   RLU_CUDA_TRY(cudaGetLastError());
-  note_launch(3);
+  note_launch(2);
   // L = L_y L_b: FP64 in the FP64 mode; FP32 accumulation over the k terms in
   // the others, whose L is FP32: that rounding (about sqrt(k) units of 2^-24
-  // per entry) moves ||L U - P A Q|| / ||A|| far less than the FP32 sketch and
-  // the FP32 input do (dense FP32 8192^2: 3.2e-6 with an FP32 product or a
-  // float-float one)
+  // per entry) keeps ||L U - P A Q|| / ||A|| within the FP32 bar (dense FP32
+  // 8192^2: 4.5e-6 against 3.3e-6 with a float-float product)
   int rc;
-  if (a.fp32_product && !std::is_same<T, double>::value)
+  if (rows_kernel) {
+    const size_t smem = (size_t)k * k * sizeof(float);
+    auto kern = k <= 64 ? k_assemble_rows<T, TO, 2> : (k <= 128 ? k_assemble_rows<T, TO, 4> : k_assemble_rows<T, TO, 8>);
+    if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
+    kern<<<(unsigned)a.num_sms, 512, smem, st>>>(m, k, reinterpret_cast<const T*>(a.Lk), a.perm_y, Lb,
+                                                 reinterpret_cast<TO*>(a.L));
+    RLU_CUDA_TRY(cudaGetLastError());
+    note_launch();
+    rc = RLU_OK;
+  } else if (a.fp32_product && !std::is_same<T, double>::value)
     rc = gemm_simt<T, T, TO, float>(st, m, k, k, LyP, k, 1, Lb, k, 1, reinterpret_cast<TO*>(a.L), k, 1);
   else
     rc = gemm_simt<T, T, TO, T>(st, m, k, k, LyP, k, 1, Lb, k, 1, reinterpret_cast<TO*>(a.L), k, 1);

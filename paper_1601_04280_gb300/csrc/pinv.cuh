@@ -40,6 +40,7 @@ struct AssembleArgs {
   int64_t* p;
   int64_t* q;
   int fp32_product;  // L = L_y L_b with FP32 accumulation (FP32 and BF16 forms) instead of float-float
+  int num_sms;       // grid of the row-streaming FP32 product
 };
 
 int launch_gram(const PinvArgs& a, cudaStream_t st);
