@@ -15,11 +15,13 @@
 // projection of dA onto range(L_y); W's rounding is amplified by cond(L_y),
 // so W keeps 24 bits.
 //
-// Warp roles (192 threads): warp 0 = TMA producer for the W planes, warp 1 =
-// TMEM owner and single-thread MMA issuer, warps 2..5 = converters of A into
-// the K-major swizzled BF16 layout, then the epilogue (TMEM -> registers ->
-// FP32 split-K partials in global memory).  A k-block is 64 rows of A; two
-// pipeline stages.  Every mbarrier wait is bounded; on timeout the kernel
+// Warp roles (320 threads): warp 0 = TMA producer for the W planes, warp 1 =
+// TMEM owner and single-thread MMA issuer, warps 2..9 = two groups of four
+// converters of A into the K-major swizzled BF16 layout (group g takes the
+// k-blocks kb = g mod 2, so the global loads of two k-blocks are in flight at
+// once), then the epilogue (TMEM -> registers -> FP32 split-K partials in
+// global memory, each group half of the columns).  A k-block is 64 rows of A;
+// two to four pipeline stages.  Every mbarrier wait is bounded; on timeout the kernel
 // raises FLAG_TIMEOUT, drains and frees its tensor memory, and returns.
 #pragma once
 #include <cuda.h>
@@ -29,7 +31,8 @@
 namespace rlu {
 namespace tc {
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
+constexpr int kConvGroups = 2;
 constexpr int kBM = 128;        // columns of A per CTA (MMA M)
 constexpr int kBK = 64;         // rows of A per k-block (one 128-byte swizzle atom of BF16)
 constexpr int kMaxStages = 4;  // shared-memory ring depth (the host picks 2..4 by tile size)
@@ -269,10 +272,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_commit(&accum_full);
     }
   } else {
-    // ---- converters (warps 2..5): A rows kb*64.. into K-major swizzled BF16 ----
-    const int t = threadIdx.x - 64;  // 0..127: row of the tile = column j0 + t of A
+    // ---- converters (warps 2..9): A rows kb*64.. into K-major swizzled BF16 ----
+    const int grp = (warp - 2) >> 2;       // 0 or 1: k-blocks kb = grp mod 2
+    const int t = (threadIdx.x - 64) & 127;  // row of the tile = column j0 + t of A
     const int64_t j = j0 + t;
-    for (int kb = 0; kb < nkb; ++kb) {
+    for (int kb = grp; kb < nkb; kb += kConvGroups) {
       const int s = kb % nst;
       if (kb >= nst && !mbar_wait(&empty[s], ((kb / nst) - 1) & 1)) { s_fail = 1; break; }
       if (s_fail) break;
@@ -305,7 +309,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
       const int64_t jj = j0 + quarter * 32 + lane;
       float* out = part + (int64_t)blockIdx.y * k * n;
-      for (int c0 = 0; c0 < npad; c0 += 16) {
+      const int nch = npad / 16, half = (nch + 1) / 2;  // 16-column chunks: group 0 the first half
+      const int cb = grp == 0 ? 0 : half * 16, ce = grp == 0 ? half * 16 : npad;
+      for (int c0 = cb; c0 < ce; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
