@@ -276,29 +276,37 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int grp = (warp - 2) >> 2;       // 0 or 1: k-blocks kb = grp mod 2
     const int t = (threadIdx.x - 64) & 127;  // row of the tile = column j0 + t of A
     const int64_t j = j0 + t;
+    // the 64 values of a k-block are loaded before waiting for its stage, so
+    // the loads are in flight while the tensor cores finish the stage's
+    // previous k-block
+    TA vals[kBK];
+    auto load_kb = [&](int kb) {
+      const int64_t k0 = kbeg + (int64_t)kb * kBK;
+#pragma unroll
+      for (int e = 0; e < kBK; ++e) {
+        const int64_t row = k0 + e;
+        vals[e] = (row < kend && j < n) ? A[row * lda + j] : (TA)0.f;
+      }
+    };
+    if (grp < nkb) load_kb(grp);
     for (int kb = grp; kb < nkb; kb += kConvGroups) {
       const int s = kb % nst;
       if (kb >= nst && !mbar_wait(&empty[s], ((kb / nst) - 1) & 1)) { s_fail = 1; break; }
       if (s_fail) break;
-      const int64_t k0 = kbeg + (int64_t)kb * kBK;
       unsigned char* A1 = stageA(s, 0);
       unsigned char* A2 = stageA(s, P - 1);
 #pragma unroll
       for (int c8 = 0; c8 < kBK / 8; ++c8) {
         __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int64_t row = k0 + c8 * 8 + e;
-          TA a = (TA)0.f;
-          if (row < kend && j < n) a = A[row * lda + j];
-          ALoader<TA>::split(a, h[e], l[e]);
-        }
+        for (int e = 0; e < 8; ++e) ALoader<TA>::split(vals[c8 * 8 + e], h[e], l[e]);
         const uint32_t off = sw128_off(t, c8 * 8);
         *reinterpret_cast<uint4*>(A1 + off) = *reinterpret_cast<const uint4*>(h);
         if (P > 1) *reinterpret_cast<uint4*>(A2 + off) = *reinterpret_cast<const uint4*>(l);
       }
       fence_proxy_async();
       mbar_arrive(&full_a[s]);
+      if (kb + kConvGroups < nkb) load_kb(kb + kConvGroups);
     }
     // ---- epilogue: TMEM -> FP32 partials part[y][c][j] ----
     const bool ok = mbar_wait(&accum_full, 0);
