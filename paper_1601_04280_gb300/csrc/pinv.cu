@@ -553,9 +553,11 @@ template int launch_assemble<df32, float>(const AssembleArgs&, cudaStream_t);
 // B = W A (first version: SIMT, FP32 or FP64 accumulate)
 // ---------------------------------------------------------------------------
 int bgemm_simt_splits(int64_t m, int64_t n, int k, int num_sms) {
+  // enough slices of the m-long contraction for two CTAs per SM, each at least
+  // 64 rows deep
   const int64_t tiles = cdiv(k, 64) * cdiv(n, 64);
   int64_t S = cdiv(2 * (int64_t)num_sms, tiles);
-  S = min64(S, max64(1, m / 256));
+  S = min64(S, max64(1, m / 64));
   return (int)max64(1, S);
 }
 
