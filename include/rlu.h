@@ -59,14 +59,20 @@ typedef enum {
 /* Storage type of A's values. */
 typedef enum { RLU_F64 = 0, RLU_F32 = 1, RLU_BF16 = 2 } rlu_dtype;
 
-/* Arithmetic of the path.  In every mode the pivoted LU of the sketch and the
- * Gram / Cholesky / triangular solve that form L_y^+ run in FP64.
- *   RLU_PREC_F64:         sketch, B = L_y^+ P A, LU of B and L in FP64; outputs f64.
- *   RLU_PREC_F32:         sketch and LU of B in FP32, B = L_y^+ P A with FP32
- *                         accuracy (three-pass TF32 split); outputs f32.
- *   RLU_PREC_BF16:        B from one BF16 pass (L_y^+ rounded to BF16, FP32 accumulate).
+/* Arithmetic of the path.  In every mode the pivoted LU of the sketch, the
+ * Cholesky factor of the Gram matrix L_y^T L_y and its inverse run in FP64.
+ *   RLU_PREC_F64:         every step in FP64; outputs f64.
+ *   RLU_PREC_F32:         sketch in FP32; the Gram matrix, L_y^+ and the LU of B
+ *                         in float-float (about 48 significant bits); B = L_y^+ P A
+ *                         on the tensor cores with FP32 accuracy (L_y^+ as three
+ *                         BF16 planes, FP32 A as two BF16 pieces, FP32
+ *                         accumulation over at most 512 rows of A and float-float
+ *                         across them); L = L_y L_b in FP32; outputs f32.
+ *   RLU_PREC_BF16:        as RLU_PREC_F32, but B from one BF16 pass (L_y^+
+ *                         rounded to BF16, FP32 accumulate over 8192-row slices).
  *   RLU_PREC_BF16_REFINE: B from L_y^+ split into BF16 hi + lo parts (two
- *                         passes, FP32 accumulate): the one-step refinement of B. */
+ *                         passes, FP32 accumulate over 2048-row slices): the
+ *                         one-step refinement of B. */
 typedef enum { RLU_PREC_F64 = 0, RLU_PREC_F32 = 1, RLU_PREC_BF16 = 2, RLU_PREC_BF16_REFINE = 3 } rlu_prec;
 
 /* Create a handle for m x n inputs, output rank k, FJL width l and CountSketch
