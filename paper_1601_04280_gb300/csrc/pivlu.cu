@@ -51,6 +51,21 @@ __device__ __forceinline__ bool cand_better(unsigned long long ka, int pa, unsig
   return ka > kb || (ka == kb && pa < pb);
 }
 
+// Lane holding the warp's best candidate (largest key, then smallest
+// position) among the lanes with `valid`, or -1 if none: hardware max / min
+// reductions on the two halves of the key and then on the position, in place
+// of a shuffle tree (positions are distinct, so the winner is unique).
+__device__ __forceinline__ int warp_best_lane(unsigned long long key, int pos, bool valid) {
+  const unsigned int khi = valid ? (unsigned int)(key >> 32) : 0u;
+  const unsigned int mhi = __reduce_max_sync(0xffffffffu, khi);
+  const bool c1 = valid && khi == mhi;
+  const unsigned int mlo = __reduce_max_sync(0xffffffffu, c1 ? (unsigned int)key : 0u);
+  const bool c2 = c1 && (unsigned int)key == mlo;
+  const unsigned int mp = __reduce_min_sync(0xffffffffu, c2 ? (unsigned int)pos : 0xffffffffu);
+  const unsigned int ball = __ballot_sync(0xffffffffu, c2 && (unsigned int)pos == mp);
+  return ball ? __ffs((int)ball) - 1 : -1;
+}
+
 template <typename T> __device__ __forceinline__ T recip(T x) { return one_<T>() / x; }
 // FP64: Newton's reciprocal (a few dependent FMAs on the slow FP64 pipe instead
 // of a full division), with the sign restored.
@@ -195,13 +210,14 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
             }
           }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
-          int op = __shfl_xor_sync(0xffffffffu, bp, o);
-          int oc = __shfl_xor_sync(0xffffffffu, bc, o);
-          int ow = __shfl_xor_sync(0xffffffffu, bw, o);
-          if (cand_better(ov, op, bv, bp) || (ov == bv && op == bp && oc > bc)) { bv = ov; bp = op; bc = oc; bw = ow; }
+        const int best = warp_best_lane(bv, bp, bc >= 0);
+        if (best >= 0) {
+          bv = __shfl_sync(0xffffffffu, bv, best);
+          bp = __shfl_sync(0xffffffffu, bp, best);
+          bc = __shfl_sync(0xffffffffu, bc, best);
+          bw = __shfl_sync(0xffffffffu, bw, best);
+        } else {
+          bc = -1;
         }
       }
       if (!ok || bc < 0) {  // timed out, or no row left (cannot happen with steps <= rows)
@@ -246,16 +262,20 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
     // from each worker thread's rows, reduced over the workers; the result
     // (local row or -1) lands in s_rstar, s_ckey, s_cpos.
     auto reduce_cand = [&](unsigned long long bv, int bp, int br) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long ov = __shfl_down_sync(0xffffffffu, bv, o);
-        int op = __shfl_down_sync(0xffffffffu, bp, o);
-        int orr = __shfl_down_sync(0xffffffffu, br, o);
-        if (cand_better(ov, op, bv, bp)) { bv = ov; bp = op; br = orr; }
+      const int best = warp_best_lane(bv, bp, br >= 0);
+      unsigned long long wv = 0ull;
+      int wp = 0x7fffffff, wr = -1;
+      if (best >= 0) {
+        wv = __shfl_sync(0xffffffffu, bv, best);
+        wp = __shfl_sync(0xffffffffu, bp, best);
+        wr = __shfl_sync(0xffffffffu, br, best);
       }
-      if (lane == 0) { red_v[wk] = bv; red_p[wk] = bp; red_r[wk] = br; }
+      if (lane == 0) { red_v[wk] = wv; red_p[wk] = wp; red_r[wk] = wr; }
       bar_sync(3, NTW);
       if (tw == 0) {
+        bv = red_v[0];
+        bp = red_p[0];
+        br = red_r[0];
         for (int w = 1; w < NWK; ++w)
           if (cand_better(red_v[w], red_p[w], bv, bp)) { bv = red_v[w]; bp = red_p[w]; br = red_r[w]; }
         s_rstar = br;
