@@ -55,7 +55,7 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
 # of the current kernels (profiles/top_kernels_dense_f32_8192.md: k_pivoted_lu of Y);
 # a workload without a capture of its current dominant kernel reports null.
-MEASURED_TRAFFIC = {("dense_f32_8192x8192_k200", "panel_lu"): 14484480 + 512}
+MEASURED_TRAFFIC = {("dense_f32_8192x8192_k200", "panel_lu"): 14491392 + 768}
 
 # FP64 vector peak: 152 SMs x 2 FP64 FMA/clk/SM (1/64 of the 128 FP32 FMA/clk/SM)
 # x 2 flop x 2.07 GHz max clock = 1.259 TFLOP/s.
