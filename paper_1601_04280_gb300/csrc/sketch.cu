@@ -757,8 +757,9 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_dense_tma(const TA* __restrict
 // entries in one access and its lanes run for about the same number of
 // entries.  A bucket is still summed by one thread in ascending column order,
 // so the sums are the same as with plain lists.  Lists that do not fit that
-// layout (a bucket longer than 255 entries, or too much padding) are kept as
-// plain 16-bit lists; for n >= 32768 they are read through L1.
+// layout (a bucket longer than 255 entries, or too much padding: not expected
+// at the at most 32 entries per bucket on average that the host allows) are
+// kept as plain 16-bit lists; for n >= 32768 they are read through L1.
 // ---------------------------------------------------------------------------
 constexpr int kRowSlotsMax = 4;
 
@@ -1374,6 +1375,9 @@ static RowsShape rows_shape(int64_t m, int64_t n, int l1, size_t es, size_t sv, 
   const size_t budget = 225 * 1024 - rows_lists16_bytes(n, l1);
   const size_t rowb = (size_t)n * es;
   if (!aligned || rowb % 16 != 0 || n < 1 || rows_lists16_bytes(n, l1) >= 225 * 1024) return {0, 0};
+  // whole-row bucket lists hold n / l1 entries per bucket on average; beyond
+  // 32 the column chunks keep the lists (and their insertion sort) short
+  if (n > 32 * (int64_t)l1) return {0, 0};
   int pb_cap = (int)(m / (2 * (int64_t)(num_sms > 0 ? num_sms : 1)));
   pb_cap = pb_cap < 1 ? 1 : (pb_cap > 8 ? 8 : pb_cap);
   const size_t pair = (size_t)2 * l1 * sv, fixed = (size_t)l1 * sv;

@@ -143,12 +143,12 @@ def test_sketch_Y_bf16(rg):
 
 
 # Shapes that reach each way the dense sketch reads A: whole rows with the
-# lists sorted and transposed per warp (the cases above), whole rows with plain
-# 16-bit lists (a bucket longer than 255 entries), whole rows with the lists
-# read through L1 (n >= 32768), and column chunks (rows too long for shared
-# memory).  Same bar as the FP32 cases above.
+# lists sorted and transposed per warp (the cases above), whole rows with the
+# lists read through L1 (n >= 32768), and column chunks (rows too long for
+# shared memory, or more than 32 entries per bucket on average).  Same bar as
+# the FP32 cases above.
 SKETCH_LAYOUT_CASES = [
-    ("f32", 50, 20000, 32, 16),     # ~625 entries per bucket: plain lists
+    ("f32", 50, 20000, 32, 16),     # ~625 entries per bucket: column chunks
     ("bf16", 60, 40000, 2000, 50),  # n >= 32768: lists through L1
     ("f32", 64, 60000, 960, 60),    # 240 KB rows: column chunks
     ("f32", 13, 4096, 1600, 12),    # odd row count, batches of one pair
