@@ -1,6 +1,6 @@
 """Summarize an ncu launch list (CSV of gpu__time_duration.sum) per kernel of this library.
 
-usage: python -m paper_1601_04280_gb300.ncu_summary gpurun_out/launches.csv "<title>" > profiles/<name>.md
+usage: python -m paper_1601_04280_gb300.ncu_summary launches.csv "<title>" > profiles/<name>.md
 """
 import collections
 import csv
