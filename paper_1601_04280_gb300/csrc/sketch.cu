@@ -6,14 +6,18 @@
 //    projection (Sec. 2.1), all from Philox4x64-10 with key (seed, "RANDLU").
 //  * bucket lists: for each column chunk and bucket b, the columns j of the
 //    chunk with h(j) = b in ascending order, so the CountSketch is a
-//    deterministic gather-sum in ascending column order.
-//  * k_sketch_dense: one pass over dense row-major A.  Per group of R rows a
-//    CTA stages column chunks of A in shared memory, each thread sums the
-//    buckets it owns in registers, then every row pair goes through one
-//    complex mixed-radix Stockham FFT in shared memory (two real rows packed
-//    as real and imaginary parts), the Hartley outputs Re X - Im X of the l
-//    selected frequencies are scaled by 1/sqrt(l1) and written to Y.  Y1
-//    never reaches global memory.
+//    deterministic gather-sum in ascending column order (one chunk = whole
+//    rows when they fit the whole-row kernel).
+//  * k_sketch_rows: one pass over dense row-major A whose rows fit in shared
+//    memory, a bulk copy per row; each row's bucket sums go straight into the
+//    FFT input of its row pair (two real rows packed as real and imaginary
+//    parts), batches of row pairs go through a complex mixed-radix Stockham
+//    FFT in shared memory, and the Hartley outputs Re X - Im X of the l
+//    selected frequencies are scaled by 1/sqrt(l1) and written to Y.
+//  * k_sketch_dense_tma / k_sketch_dense: the same over column chunks of R-row
+//    groups (rows too long for shared memory; rows that cannot be bulk-copied),
+//    each thread summing the buckets it owns in registers.
+//  Y1 never reaches global memory.
 #include <cstdio>
 
 #include "common.cuh"
