@@ -54,3 +54,25 @@ def test_fp64_and_csr_products():
     nnz = 12345
     works = bench.stage_work("csr", c, 8 * nnz, nnz, "f32")
     assert works["bgemm"][0] == 2.0 * c.k * nnz
+
+
+def test_reference_arm_json_line():
+    """The reference arm (the oracle on the host cores) prints one JSON line
+    with the contract's keys, on the small dense FP64 workload."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                          "dense_f64_1024x1024_k20", "--steps", "1", "--warmup", "3"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["config"]["workload"] == "dense_f64_1024x1024_k20"
