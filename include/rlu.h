@@ -262,6 +262,30 @@ int rlu_debug_stage_ms(rlu_t h, float* ms, int max_stages, int* count);
 /* Number of CUDA kernels this library has launched in this process so far. */
 int rlu_debug_launch_count(int64_t* out);
 
+/* Test hook, needs no GPU: the status code that the library reports for a
+ * set of device flag bits (bit 0 a timed-out wait, bit 1 a non-finite value,
+ * bit 2 an exactly zero pivot, bit 3 a malformed CSR structure), the same
+ * mapping that every entry point and the device-side status writers use.
+ * Errors: RLU_EINVAL (null status). */
+int rlu_debug_status_of_flags(uint32_t flags, int* status);
+
+/* Test hook: run one of the library's bounded device waits on a condition
+ * that never comes true and report the status it leaves.  which = 0: the grid
+ * barrier of the cooperative kernels (two CTAs wait for an arrival no CTA
+ * makes); which = 1: the mbarrier wait of the tensor-core pipeline (a barrier
+ * nothing arrives at).  Each wait gives up after about a second, sets the
+ * timeout flag and returns, so *status receives RLU_ETIMEOUT and the context
+ * stays usable.  Synchronous; allocates 8 bytes of device memory.
+ * Errors: RLU_EINVAL, RLU_ENOMEM, RLU_ECUDA. */
+int rlu_debug_wait_timeout(int which, int* status);
+
+/* Measurement hook: fused multiply-add throughput of the current GPU in
+ * TFLOP/s (2 flop per FMA), which = 0 for FP64, 1 for FP32, from a kernel of
+ * eight independent FMA chains per thread, 2048 threads per SM, best of three
+ * timed launches of about 20 ms each.  Synchronous.
+ * Errors: RLU_EINVAL, RLU_ENOMEM, RLU_ECUDA. */
+int rlu_debug_alu_peak(int which, double* tflops);
+
 /* Test hook: the device FP64 reciprocal used on the Cholesky's dependent chain
  * (Newton's iteration seeded by the FP32 reciprocal approximation), applied to
  * n host values x (x > 0), results to host out.  Synchronous.
@@ -269,16 +293,17 @@ int rlu_debug_launch_count(int64_t* out);
 int rlu_debug_recip(const double* x, double* out, int64_t n);
 
 /* ---- sketch without allocation ----
- * No counterpart in the paper: this entry point exists for callers that
- * cannot allocate device memory on their call path — a serving loop that
- * must not call cudaMalloc (it synchronizes the whole device and stalls other
- * streams), a host process whose device memory is already reserved by another
- * framework's pool, or an embedded caller with a fixed memory map.
+ * The paper has no counterpart to this entry point: it exists for callers
+ * that cannot allocate device memory on their call path — a serving loop
+ * that must not call cudaMalloc (it synchronizes the whole device and stalls
+ * every other stream), a process whose device memory already belongs to
+ * another framework's pool, or an embedded caller with a fixed memory map.
  *
- * rlu_sketch_dense_noalloc computes the sketch of step 2 of Algorithm 1,
- *   Y = A S D H R / sqrt(l1)   (m x l, row-major f64, device, written by the call),
- * with S, D, R drawn from `seed` exactly as rlu_create(m, n, k, l, l1, seed)
- * draws them (so Y equals the sketch a handle computes for the same inputs).
+ * rlu_sketch_dense_noalloc computes the m x l sketch
+ *   Y = A S D H R / sqrt(l1)   (row-major f64, device, written by the call),
+ * with S (hash and signs), D (signs) and R (the kept Hartley outputs) drawn
+ * from `seed` exactly as rlu_create(m, n, k, l, l1, seed) draws them, so Y
+ * equals the sketch that a handle computes for the same inputs.
  * A: device, m x n row-major of `dtype` (RLU_F64 sums in FP64, RLU_F32 and
  * RLU_BF16 in FP32), leading dimension lda >= n.
  * It allocates nothing: its scratch (hash and sign arrays, per-chunk bucket
@@ -292,8 +317,10 @@ int rlu_debug_recip(const double* x, double* out, int64_t n);
  * capture.  All calls on one device share the array and it keeps the last
  * call's contents (each call re-initializes what it needs); calls on the same
  * device whose GPU work overlaps race on it and must be serialized.
- * Asynchronous on `stream`: `status_dev` (device, one int32) receives RLU_OK
- * or RLU_ENONFINITE when the work completes.
+ * Asynchronous on `stream`: when the work completes, `status_dev` (device,
+ * one int32) receives RLU_OK, RLU_ETIMEOUT (a bounded wait of the sketch's
+ * copy pipeline gave up: Y is incomplete) or RLU_ENONFINITE (A holds NaN or
+ * Inf, or a bucket sum overflowed).
  * Errors at call time: RLU_EINVAL, RLU_ETOOLARGE, RLU_ECUDA. */
 #define RLU_NOALLOC_MAX_N 65536
 #define RLU_NOALLOC_MAX_L1 4096

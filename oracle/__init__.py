@@ -7,5 +7,6 @@ from .rlu import (KEY_TAG, STATUS_OK, STATUS_WRANK, SketchParams, LUResult,
                   OracleResult, sketch_params, sem_matrix, countsketch,
                   hartley_columns, fjl, lu_partial_pivot, unit_lower,
                   pinv_householder, factor, relative_residual, check_sizes,
-                  second_projection, factor_two_sketch)
+                  second_projection, factor_two_sketch,
+                  bucket_of_word, sign_of_word)
 from .philox import philox4x64_10, mulhilo64, stream_blocks

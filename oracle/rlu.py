@@ -58,6 +58,17 @@ class SketchParams:
     R_keys: np.ndarray = field(repr=False, default=None)  # (l1,) uint64
 
 
+def bucket_of_word(w, l1):
+    """Bucket in [0, l1) of a uniform 64-bit word: floor(w * l1 / 2^64),
+    exact in Python integers (the multiply-high form of a uniform draw)."""
+    return (int(w) * int(l1)) >> 64
+
+
+def sign_of_word(w):
+    """Random sign of a uniform 64-bit word: -1 when its top bit is set."""
+    return -1.0 if int(w) >= 2 ** 63 else 1.0
+
+
 def sketch_params(n, l1, l, seed):
     """Draw h, s, d and R for one factorization (step 1 of Algorithm 1).
 
@@ -77,13 +88,11 @@ def sketch_params(n, l1, l, seed):
     if not (1 <= l <= l1):
         raise ValueError("need 1 <= l <= l1")
     key = (np.uint64(seed & 0xFFFFFFFFFFFFFFFF), np.uint64(KEY_TAG))
-    top = np.uint64(1) << np.uint64(63)
     b0 = stream_blocks(key, 0, n)
-    # floor(w0 * l1 / 2^64) computed exactly with Python integers
-    h = np.array([(int(w) * l1) >> 64 for w in b0[:, 0]], dtype=np.int64)
-    s = np.where(b0[:, 1] >= top, -1.0, 1.0)
+    h = np.array([bucket_of_word(w, l1) for w in b0[:, 0]], dtype=np.int64)
+    s = np.array([sign_of_word(w) for w in b0[:, 1]], dtype=np.float64)
     b1 = stream_blocks(key, 1, l1)
-    d = np.where(b1[:, 0] >= top, -1.0, 1.0)
+    d = np.array([sign_of_word(w) for w in b1[:, 0]], dtype=np.float64)
     b2 = stream_blocks(key, 2, l1)
     keys = b2[:, 0]
     order = sorted(range(l1), key=lambda b: (int(keys[b]), b))

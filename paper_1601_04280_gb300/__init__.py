@@ -30,7 +30,8 @@ C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_
              "rlu_debug_timing", "rlu_debug_stage_ms", "rlu_debug_launch_count", "rlu_sketch_dense_noalloc",
              "rlu_csr_workspace_bytes", "rlu_set_csr_workspace", "rlu_graph_capture_dense", "rlu_graph_launch",
              "rlu_graph_destroy", "rlu_copy_block_async", "rlu_set_max_ctas",
-             "rlu_debug_recip", "rlu_set_second_sketch")
+             "rlu_debug_recip", "rlu_set_second_sketch", "rlu_debug_status_of_flags", "rlu_debug_wait_timeout",
+             "rlu_debug_alu_peak")
 
 #: stage names reported by rlu_debug_stage_ms, in order
 STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
@@ -82,6 +83,9 @@ def load(reload=False):
         "rlu_set_max_ctas": ([vp, i32], c.c_int),
         "rlu_debug_recip": ([vp, vp, i64], c.c_int),
         "rlu_set_second_sketch": ([vp, i32, i32, u64], c.c_int),
+        "rlu_debug_status_of_flags": ([c.c_uint32, c.POINTER(c.c_int)], c.c_int),
+        "rlu_debug_wait_timeout": ([c.c_int, c.POINTER(c.c_int)], c.c_int),
+        "rlu_debug_alu_peak": ([c.c_int, c.POINTER(c.c_double)], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -204,6 +208,27 @@ def rlu_debug_recip(x):
     out = np.empty_like(x)
     _check(load().rlu_debug_recip(x.ctypes.data, out.ctypes.data, x.size), "rlu_debug_recip")
     return out
+
+
+def rlu_debug_status_of_flags(flags):
+    """Status code the library reports for device flag bits (no GPU needed)."""
+    out = ctypes.c_int()
+    _check(load().rlu_debug_status_of_flags(int(flags), ctypes.byref(out)), "rlu_debug_status_of_flags")
+    return out.value
+
+
+def rlu_debug_wait_timeout(which):
+    """Run a bounded device wait that can never complete; returns its status."""
+    out = ctypes.c_int()
+    _check(load().rlu_debug_wait_timeout(int(which), ctypes.byref(out)), "rlu_debug_wait_timeout")
+    return out.value
+
+
+def rlu_debug_alu_peak(which):
+    """FP64 (which=0) or FP32 (which=1) FMA throughput of the current GPU, TFLOP/s."""
+    out = ctypes.c_double()
+    _check(load().rlu_debug_alu_peak(int(which), ctypes.byref(out)), "rlu_debug_alu_peak")
+    return out.value
 
 
 def rlu_debug_launch_count():

@@ -229,28 +229,14 @@ bool sizes_ok(int64_t m, int64_t n, int k, int l, int l1) {
 // CTAs for the grid-synchronised kernels of this handle.
 int coop_sms(const rlu_ctx* h) { return h->max_ctas > 0 && h->max_ctas < h->num_sms ? h->max_ctas : h->num_sms; }
 
-int map_flags(unsigned int f) {
-  if (f & FLAG_TIMEOUT) return RLU_ETIMEOUT;
-  if (f & FLAG_BAD_CSR) return RLU_EBADCSR;
-  if (f & FLAG_NONFINITE) return RLU_ENONFINITE;
-  if (f & FLAG_ZERO_PIVOT) return RLU_WRANK;
-  return RLU_OK;
-}
+int map_flags(unsigned int f) { return status_of_flags(f); }
 
 __global__ void k_debug_recip(int64_t n, const double* x, double* out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = rcp_newton(x[i]);
 }
 
-__global__ void k_status_code(const unsigned int* flags, int32_t* out) {
-  unsigned int f = *flags;
-  int code = RLU_OK;
-  if (f & FLAG_TIMEOUT) code = RLU_ETIMEOUT;
-  else if (f & FLAG_BAD_CSR) code = RLU_EBADCSR;
-  else if (f & FLAG_NONFINITE) code = RLU_ENONFINITE;
-  else if (f & FLAG_ZERO_PIVOT) code = RLU_WRANK;
-  *out = code;
-}
+__global__ void k_status_code(const unsigned int* flags, int32_t* out) { *out = status_of_flags(*flags); }
 
 bool prec_dtype_ok(int prec, int dtype) {
   switch (prec) {
@@ -991,6 +977,12 @@ int rlu_debug_stage_ms(rlu_t h, float* ms, int max_stages, int* count) {
   int cnt = max_stages < kNumStages ? max_stages : kNumStages;
   for (int i = 0; i < cnt; ++i) RLU_CUDA_TRY(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
   *count = cnt;
+  return RLU_OK;
+}
+
+int rlu_debug_status_of_flags(uint32_t flags, int* status) {
+  if (!status) return RLU_EINVAL;
+  *status = status_of_flags(flags);
   return RLU_OK;
 }
 

@@ -107,6 +107,15 @@ __global__ void k_split_w_rows(int64_t m, int k, int64_t ldw, const float* __res
   W3[e] = __float2bfloat16_rn(r2);
 }
 
+// B[c][j] = sum over splits of part[s][c][j], float-float, fixed order.
+__global__ void k_sum_parts(int64_t kn, int S, const float* __restrict__ part, df32* __restrict__ B) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= kn) return;
+  df32 acc = df_make(0.f, 0.f);
+  for (int s = 0; s < S; ++s) acc = acc + df_make(part[(int64_t)s * kn + e], 0.f);
+  B[e] = acc;
+}
+
 template <typename TA>
 static int launch_cfg(const TcWs& w, int wplanes, const TA* A, int64_t lda, int64_t m, int64_t n, int k,
                       int64_t kps, int splits, unsigned int* status, cudaStream_t st) {
@@ -151,7 +160,7 @@ int launch_bgemm_tc(const TcWs& w, const float* W, const void* A, int64_t lda, i
   else
     return RLU_EINVAL;
   if (rc) return rc;
-  tc::k_sum_parts<<<(unsigned)cdiv((int64_t)k * n, 256), 256, 0, st>>>((int64_t)k * n, splits, w.part, B);
+  k_sum_parts<<<(unsigned)cdiv((int64_t)k * n, 256), 256, 0, st>>>((int64_t)k * n, splits, w.part, B);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
   return RLU_OK;

@@ -18,6 +18,18 @@ enum : unsigned int {
   FLAG_BAD_CSR = 1u << 3,    // CSR structure invalid (row pointers or column range)
 };
 
+// Status code of a set of flag bits, in order of severity: a timed-out wait
+// leaves outputs unwritten, so it outranks everything; then a malformed CSR,
+// a non-finite input, and last the rank warning.  The one mapping used by the
+// host read-back and by every kernel that writes a status code to the device.
+__host__ __device__ __forceinline__ int status_of_flags(unsigned int f) {
+  if (f & FLAG_TIMEOUT) return RLU_ETIMEOUT;
+  if (f & FLAG_BAD_CSR) return RLU_EBADCSR;
+  if (f & FLAG_NONFINITE) return RLU_ENONFINITE;
+  if (f & FLAG_ZERO_PIVOT) return RLU_WRANK;
+  return RLU_OK;
+}
+
 // Spin limit for every device wait: about a second at GB300 clocks.
 constexpr long long kSpinLimitCycles = 2000000000ll;
 

@@ -339,15 +339,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0 && s_fail) set_flag(status, FLAG_TIMEOUT);
 }
 
-// B[c][j] = sum over splits of part[s][c][j], float-float, fixed order.
-__global__ void k_sum_parts(int64_t kn, int S, const float* __restrict__ part, df32* __restrict__ B) {
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= kn) return;
-  df32 acc = df_make(0.f, 0.f);
-  for (int s = 0; s < S; ++s) acc = acc + df_make(part[(int64_t)s * kn + e], 0.f);
-  B[e] = acc;
-}
-
 // W (k x m, FP64 accurate values in float-float or double) -> three BF16 planes.
 template <typename TW>
 __global__ void k_split_w(int64_t km, const TW* __restrict__ W, __nv_bfloat16* __restrict__ W1,

@@ -73,10 +73,9 @@ int scratch_address(void** out) {
   return RLU_OK;
 }
 
-__global__ void k_noalloc_status(const unsigned int* flags, int32_t* out) {
-  const unsigned int f = *flags;
-  *out = (f & FLAG_NONFINITE) ? RLU_ENONFINITE : RLU_OK;
-}
+// The same flag-to-status mapping as every other entry point: a timed-out
+// wait (Y partly unwritten) reports RLU_ETIMEOUT ahead of a non-finite input.
+__global__ void k_noalloc_status(const unsigned int* flags, int32_t* out) { *out = status_of_flags(*flags); }
 
 }  // namespace
 }  // namespace rlu

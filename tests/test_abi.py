@@ -53,3 +53,19 @@ def test_strerror(lib):
     for code in (0, 1, 2, 3, 4, 5, 6, 100):
         assert rg.strerror(code)
     assert rg.strerror(12345) == "unknown status"
+
+
+def test_every_flag_bit_reaches_the_status_word(lib):
+    """Each device flag bit gives its own status code, and a set of bits gives
+    the most severe one: a timed-out wait (outputs unwritten) before a
+    malformed CSR, a non-finite input, and the rank warning.  This is the one
+    mapping of the host read-back and of the device-side status writers
+    (including the allocation-free sketch)."""
+    single = {1: rg.RLU_ETIMEOUT, 2: rg.RLU_ENONFINITE, 4: rg.RLU_WRANK, 8: rg.RLU_EBADCSR}
+    for bit, code in single.items():
+        assert rg.rlu_debug_status_of_flags(bit) == code
+    assert rg.rlu_debug_status_of_flags(0) == rg.RLU_OK
+    order = [1, 8, 2, 4]  # most severe first
+    for flags in range(1, 16):
+        first = next(b for b in order if flags & b)
+        assert rg.rlu_debug_status_of_flags(flags) == single[first], flags

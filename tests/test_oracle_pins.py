@@ -62,6 +62,58 @@ def test_philox_matches_numpy(key):
 
 
 # ---------------------------------------------------------------------------
+# Step 1's mapping from Philox words to h, s, d and R, restated from its
+# specification with numpy's own Philox stepping through each stream
+# ---------------------------------------------------------------------------
+def numpy_stream(key, stream, count):
+    """Blocks (i, stream, 0, 0), i < count, from numpy's Philox: started one
+    below counter (0, stream, 0, 0) (a 256-bit little-endian integer, so the
+    decrement borrows across words), it increments before each block."""
+    before = ((stream << 64) - 1) % (1 << 256)
+    words = [(before >> (64 * i)) & (2**64 - 1) for i in range(4)]
+    bg = np.random.Philox(key=[0, 0])
+    st = bg.state
+    st["state"]["counter"] = np.array(words, dtype=np.uint64)
+    st["state"]["key"] = np.array(key, dtype=np.uint64)
+    st["buffer_pos"] = 4
+    bg.state = st
+    return bg.random_raw(4 * count).reshape(count, 4)
+
+
+@pytest.mark.parametrize("n,l1,l,seed", [(1000, 240, 30, 1), (3000, 1600, 220, 2001), (500, 4000, 520, 2**63 + 5),
+                                         (64, 7, 7, 0)])
+def test_sketch_params_from_numpy_philox(n, l1, l, seed):
+    """h(j) = floor(w0 l1 / 2^64), s(j) = -1 iff w1 >= 2^63 on stream 0;
+    d(b) = -1 iff w0 >= 2^63 on stream 1; R = the l indices b of smallest
+    (w0, b) on stream 2, in that order.  Words from numpy's generator, the
+    mapping written out here with Python integers."""
+    key = [seed % 2**64, oracle.KEY_TAG]
+    p = oracle.sketch_params(n, l1, l, seed)
+    b0 = numpy_stream(key, 0, n)
+    assert [int(x) for x in p.h] == [(int(w) * l1) >> 64 for w in b0[:, 0]]
+    assert [int(x) for x in p.s] == [-1 if int(w) >> 63 else 1 for w in b0[:, 1]]
+    b1 = numpy_stream(key, 1, l1)
+    assert [int(x) for x in p.d] == [-1 if int(w) >> 63 else 1 for w in b1[:, 0]]
+    b2 = numpy_stream(key, 2, l1)
+    ranked = sorted(range(l1), key=lambda b: (int(b2[b, 0]), b))
+    assert [int(x) for x in p.R] == ranked[:l]
+
+
+def test_word_mapping_boundaries():
+    """The edges of the word-to-bucket and word-to-sign maps."""
+    for l1 in (7, 240, 1600, 4000, 16384):
+        assert oracle.bucket_of_word(0, l1) == 0
+        assert oracle.bucket_of_word(2**64 - 1, l1) == l1 - 1
+        for b in (1, l1 // 2, l1 - 1):
+            first = -(-(b << 64) // l1)  # smallest word of bucket b: ceil(b 2^64 / l1)
+            assert oracle.bucket_of_word(first, l1) == b
+            assert oracle.bucket_of_word(first - 1, l1) == b - 1
+    assert oracle.sign_of_word(2**63) == -1.0
+    assert oracle.sign_of_word(2**63 - 1) == 1.0
+    assert oracle.sign_of_word(0) == 1.0 and oracle.sign_of_word(2**64 - 1) == -1.0
+
+
+# ---------------------------------------------------------------------------
 # Sparse embedding matrix (Sec. 2.2)
 # ---------------------------------------------------------------------------
 def test_sketch_params_ranges_and_selection():
@@ -354,3 +406,28 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
     r = oracle.factor(A, 5, 8, 48, seed=4)
     e = oracle.relative_residual(A, r.L, r.U, r.p, r.q)
     assert not np.isclose(e, projector_error(A, r.Y[:, 3:8]), rtol=1e-6)
+
+
+def test_planted_word_mapping_mistakes_fail_the_pin(monkeypatch):
+    """h from w1 instead of w0, the sign from the wrong word, and a sign test
+    shifted by one word value each break test_sketch_params_from_numpy_philox
+    or test_word_mapping_boundaries."""
+    n, l1, l, seed = 300, 240, 30, 9
+    key = [seed, oracle.KEY_TAG]
+    b0 = numpy_stream(key, 0, n)
+    good_h = [(int(w) * l1) >> 64 for w in b0[:, 0]]
+    good_s = [-1 if int(w) >> 63 else 1 for w in b0[:, 1]]
+    real = oracle.rlu.stream_blocks
+
+    def swapped(key_, stream, count):  # words 0 and 1 exchanged
+        b = real(key_, stream, count).copy()
+        b[:, [0, 1]] = b[:, [1, 0]]
+        return b
+    monkeypatch.setattr(oracle.rlu, "stream_blocks", swapped)
+    p = oracle.sketch_params(n, l1, l, seed)
+    monkeypatch.undo()
+    assert [int(x) for x in p.h] != good_h and [int(x) for x in p.s] != good_s
+    # a strict '>' in the sign test moves the word 2^63 to the wrong side
+    monkeypatch.setattr(oracle.rlu, "sign_of_word", lambda w: -1.0 if int(w) > 2 ** 63 else 1.0)
+    assert oracle.rlu.sign_of_word(2**63) != -1.0
+    monkeypatch.undo()

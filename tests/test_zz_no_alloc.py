@@ -46,18 +46,27 @@ def test_noalloc_sketch_matches_handle_path_on_two_calls():
     rg.load(reload=True)
     g = torch.Generator().manual_seed(5)
     cases = [
-        # (m, n, l, l1, seed, dtype, prec of the handle path)
-        (300, 5000, 30, 240, 11, torch.float32, "f32"),
-        (257, 3000, 64, 1600, 12, torch.float64, "f64"),
+        # (m, n, l, l1, seed, dtype, prec of the handle path, row stride)
+        # whole rows in shared memory:
+        (300, 5000, 30, 240, 11, torch.float32, "f32", None),
+        (257, 3000, 64, 1600, 12, torch.float64, "f64", None),
+        # column chunks through the fixed scratch's per-chunk counters and lists:
+        # n = the maximum, more than 32 entries per bucket (64 chunks x 1600 buckets)
+        (40, 65536, 32, 1600, 13, torch.float32, "f32", None),
+        # rows too long for shared memory at the maximum l1 (30 chunks x 4096 buckets)
+        (24, 60000, 16, 4096, 14, torch.bfloat16, "f32", None),
+        # a row stride that is not a multiple of 16 bytes: the register-staged kernel
+        (50, 3000, 20, 240, 15, torch.float32, "f32", 3001),
     ]
     inputs, refs = [], []
-    for m, n, l, l1, seed, dt, prec in cases:
-        A = torch.randn((m, n), generator=g, dtype=torch.float64).to(dt).cuda()
+    for m, n, l, l1, seed, dt, prec, lda in cases:
+        full = torch.randn((m, lda or n), generator=g, dtype=torch.float64).to(dt).cuda()
+        A = full[:, :n]
         inputs.append(A)
         refs.append(_sketch_via_handle(rg, A, l, l1, seed, prec))
     # two calls in a row, then compare both with the handle path
     outs = []
-    for (m, n, l, l1, seed, dt, prec), A in zip(cases, inputs):
+    for (m, n, l, l1, seed, dt, prec, lda), A in zip(cases, inputs):
         rc, Y, st = _sketch_noalloc(rg, A, l, l1, seed)
         assert rc == rg.RLU_OK, rg.strerror(rc)
         outs.append((Y, st))
