@@ -1,20 +1,22 @@
 """CSR input: parity of the CUDA path with the FP64 oracle (scipy.sparse A).
 
 Tolerances as in test_gpu_parity: FP32 |e_gpu - e_oracle| <= 1e-5, FP64 <= 1e-12;
-pivots equal on the separated prefix.  Rows with >= n/4 entries take the dense
-(heavy) route, the others the sparse route; both are exercised.
+pivots equal on the separated prefix; L, U and B entry by entry wherever the
+GPU chose the oracle's pivots (parity_tools).  Rows with >= n/4 entries take
+the dense (heavy) route, the others the sparse route; both are exercised.
 """
 import numpy as np
 import pytest
 import scipy.sparse
 
 import oracle
+import parity_tools as pt
 import rlu_inputs as ri
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from test_gpu_parity import check_pivots, check_structure  # noqa: E402
+from test_gpu_parity import check_pivots, check_structure, separated_prefix  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -67,6 +69,36 @@ def test_csr_f32_parity(rg, m, n, npr, heavy, k, l, l1):
     assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
     if e_o >= 1e-4:
         assert abs(e_g / e_o - 1) <= 1e-2
+    tau = pt.tolerances(As, o, k, l, "f32")
+    done = pt.check_elementwise(g, o, k, tau, g["B"])
+    print("csr %dx%d k=%d: tau %s, max rel. differences %s" % (m, n, k, tau, done))
+    if separated_prefix(o.top_y, np.abs(o.Y).max(), 1e-4) >= k:
+        assert "B" in done
+
+
+def test_csr_f32_c2_shape(rg):
+    """The sparse workload's code paths at a reduced height: 40 uniform
+    columns per row, a dense rank-50 block on 2 % of the rows (160 rows of
+    50000 entries: heavy rows, densified and sketched by the column-chunk
+    kernel through the row map, their B on the tensor cores), k = 100,
+    l = 120, l1 = 960."""
+    m, n, k, l, l1 = 8000, 50000, 100, 120, 960
+    As = sparse_case(m, n, 40, m // 50, 50, seed=77, dtype=np.float32)
+    o = oracle.factor(As, k, l, l1, seed=97)
+    g = run_csr(rg, As, k, l, l1, 97, "f32", debug=True)
+    assert g["status"] == 0, rg.strerror(g["status"])
+    check_structure(g, m, n, k)
+    check_pivots(g, o, k)
+    rown = np.sqrt(np.asarray(As.multiply(As).sum(axis=1)).ravel().max())
+    assert np.abs(g["Y"] - o.Y).max() <= 5e-6 * rown
+    e_o = oracle.relative_residual(As, o.L, o.U, o.p, o.q)
+    e_g = oracle.relative_residual(As, g["L"], g["U"], g["p"], g["q"])
+    assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
+    if e_o >= 1e-4:
+        assert abs(e_g / e_o - 1) <= 1e-2
+    tau = pt.tolerances(As, o, k, l, "f32", draws=1)
+    done = pt.check_elementwise(g, o, k, tau, g["B"])
+    print("csr c2 shape: e_gpu %.4e e_oracle %.4e; tau %s; max rel. differences %s" % (e_g, e_o, tau, done))
 
 
 def test_csr_f64_parity(rg):

@@ -10,6 +10,10 @@ Tolerances
     1e-2.  Y element-wise within 5e-6 * max row norm: FP32 sums of n terms carry
     a relative error of a few n*u_32 in the worst case and ~sqrt(n)*u_32
     typically (u_32 = 6e-8).
+  * factors, entry by entry (parity_tools): L (in A's row order), U and B
+    against the oracle's wherever the GPU chose the oracle's pivots, within
+    10x the oracle's own response to a perturbation the size of the mode's
+    rounding (FP32 sketch; B within FP32, 16-bit or 8-bit W; FP32 L product).
   * pivots: equal on every step before the first step whose two best
     candidates, in the oracle, differ by less than 1e-4 of the largest entry
     of the factored matrix (Y for the row pivots, B for the column pivots):
@@ -20,6 +24,7 @@ import numpy as np
 import pytest
 
 import oracle
+import parity_tools as pt
 import rlu_inputs as ri
 
 torch = pytest.importorskip("torch")
@@ -212,6 +217,12 @@ def test_dense_f32_parity(rg, m, n, k, l, l1, rank, noise):
     assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
     if e_o >= 1e-4:
         assert abs(e_g / e_o - 1) <= 1e-2
+    # these inputs have separated pivots in every step of both LUs: all three
+    # factors are compared entry by entry
+    tau = pt.tolerances(A.astype(np.float64), o, k, l, "f32")
+    done = pt.check_elementwise(g, o, k, tau, g["B"])
+    print("f32 %dx%d k=%d: tau %s, max rel. differences %s" % (m, n, k, tau, done))
+    assert set(done) == {"B", "L", "U"}, done
 
 
 @pytest.fixture(scope="module")
@@ -226,23 +237,30 @@ def bf16_case():
     return A, (m, n, k, l, l1), o, e_o, kappa
 
 
-# Precision forms on BF16 input.  W is carried in BF16 planes: three planes
-# (24 significant bits, RLU_PREC_F32), two (hi + lo, 16 bits: the one-step
-# refinement) or one (8 bits).  An entrywise relative error eps in W moves
-# L U = L_y (W A) Q by at most eps * ||L_y|| ||W|| ||A|| = eps * kappa(L_y) ||A||
-# (W = L_y^+, so ||L_y|| ||W|| = kappa(L_y)), hence |e_gpu - e_oracle| <=
-# eps * kappa(L_y) with eps = 2^-(bits+1); the FP32 sketch and accumulation add
-# far less (the FP32 bar of 1e-5 covers them).
-@pytest.mark.parametrize("prec,bits", [("f32", 24), ("bf16_refine", 16), ("bf16", 8)])
-def test_dense_bf16_precision_forms(rg, bf16_case, prec, bits):
+# Precision forms on BF16 input: the error of each form against the oracle's
+# error on the same (BF16-rounded) matrix, as ratios.  W is carried in BF16
+# planes: three (24 significant bits, RLU_PREC_F32), two (hi + lo, 16 bits:
+# the one-step refinement of B) or one (8 bits).  RLU_PREC_F32 must match the
+# oracle within the FP32 bars; the refinement must restore the oracle's error
+# to within 5 %; one plane may raise it, by at most the ratio measured on
+# GB300 for this matrix (1.044 with kappa(L_y) = 31.5; the refinement
+# measured 1.0000) plus a margin of 0.10.
+E_RATIO_BAR = {"f32": 1.01, "bf16_refine": 1.05, "bf16": 1.15}
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16_refine", "bf16"])
+def test_dense_bf16_precision_forms(rg, bf16_case, prec):
     A, (m, n, k, l, l1), o, e_o, kappa = bf16_case
     g = run(rg, A, k, l, l1, 93, prec, torch.bfloat16)
     assert g["status"] == 0
     check_structure(g, m, n, k)
     e_g = oracle.relative_residual(A.astype(np.float64), g["L"], g["U"], g["p"], g["q"])
-    tol = max(1e-5, 2.0 ** -(bits + 1) * kappa)
-    assert abs(e_g - e_o) <= tol, (prec, e_g, e_o, kappa, tol)
+    ratio = e_g / e_o
+    print("%s: kappa(L_y) %.1f, e_gpu %.4e, e_oracle %.4e, ratio %.4f, bar %.2f" % (
+        prec, kappa, e_g, e_o, ratio, E_RATIO_BAR[prec]))
+    assert ratio <= E_RATIO_BAR[prec], (prec, e_g, e_o, kappa)
     if prec == "f32":
+        assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
         check_pivots(g, o, k)
     else:
         # the sketch (hence the row pivots) does not depend on the W planes
@@ -250,18 +268,76 @@ def test_dense_bf16_precision_forms(rg, bf16_case, prec, bits):
         assert np.array_equal(g["p"][:sy], o.p[:sy])
 
 
+@pytest.fixture(scope="module")
+def bf16_gauss_case():
+    """BF16-stored Gaussian rank-60 product plus noise: pivots separated in
+    every step of both LUs, so the factors compare entry by entry."""
+    m, n, k, l, l1 = 3000, 2000, 60, 80, 640
+    A = ri.round_to_bf16(ri.dense_low_rank_plus_noise(m, n, 60, 1e-3, seed=4243))[0]
+    o = oracle.factor(A.astype(np.float64), k, l, l1, seed=94)
+    return A, (m, n, k, l, l1), o
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16_refine", "bf16"])
+def test_dense_bf16_elementwise(rg, bf16_gauss_case, prec):
+    A, (m, n, k, l, l1), o = bf16_gauss_case
+    g = run(rg, A, k, l, l1, 94, prec, torch.bfloat16, debug=True)
+    assert g["status"] == 0
+    tau = pt.tolerances(A.astype(np.float64), o, k, l, prec)
+    done = pt.check_elementwise(g, o, k, tau, g["B"])
+    print("%s: tau %s, max rel. differences %s" % (prec, tau, done))
+    # B is always comparable (the row pivots come from the FP32 sketch); with
+    # one BF16 plane of W the column pivots may move, and L, U with them
+    assert "B" in done
+    if prec != "bf16":
+        assert set(done) == {"B", "L", "U"}, done
+
+
 def test_dense_f32_8192_full_size(rg):
     """The dense FP32 workload at full size, in the configuration the bench times."""
     w = ri.DENSE_F32_8K
     A = ri.make_dense(w)
     o = oracle.factor(A.astype(np.float64), w.k, w.l, w.l1, w.sketch_seed)
-    g = run(rg, A, w.k, w.l, w.l1, w.sketch_seed, "f32", torch.float32)
+    g = run(rg, A, w.k, w.l, w.l1, w.sketch_seed, "f32", torch.float32, debug=True)
     assert g["status"] == 0
     check_structure(g, w.m, w.n, w.k)
     check_pivots(g, o, w.k)
     e_o = oracle.relative_residual(A, o.L, o.U, o.p, o.q)
     e_g = oracle.relative_residual(A, g["L"], g["U"], g["p"], g["q"])
     assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
+    tau = pt.tolerances(A.astype(np.float64), o, w.k, w.l, "f32", draws=1)
+    done = pt.check_elementwise(g, o, w.k, tau, g["B"])
+    print("dense f32 8192^2: e_gpu %.3e e_oracle %.3e; tau %s; max rel. differences %s" % (e_g, e_o, tau, done))
+    assert "B" in done
+
+
+def test_dense_bf16_c3_shape(rg):
+    """The BF16 precision form's code paths at a reduced size of its workload:
+    the global-memory panel LU (rows per CTA x 520 columns exceed shared
+    memory), the k > 226 product L = L_y L_b, a 4000-point FFT, the
+    refinement with 2048-row splits.  Same 1/i^2 spectrum (rank-2048
+    truncation), rounded to BF16."""
+    w = ri.DENSE_BF16_32K
+    m, n = 16384, 4096
+    A = ri.make_dense(w, m=m, n=n)
+    A64 = A.astype(np.float64)
+    o = oracle.factor(A64, w.k, w.l, w.l1, w.sketch_seed)
+    g = run(rg, A, w.k, w.l, w.l1, w.sketch_seed, "bf16_refine", torch.bfloat16, debug=True)
+    assert g["status"] == 0
+    check_structure(g, m, n, w.k)
+    rown = np.linalg.norm(A64, axis=1).max()
+    assert np.abs(g["Y"] - o.Y).max() <= 5e-6 * rown
+    sy = separated_prefix(o.top_y, np.abs(o.Y).max(), 1e-4)
+    assert np.array_equal(g["p"][:sy], o.p[:sy])
+    e_o = oracle.relative_residual(A64, o.L, o.U, o.p, o.q)
+    e_g = oracle.relative_residual(A64, g["L"], g["U"], g["p"], g["q"])
+    tau = pt.tolerances(A64, o, w.k, w.l, "bf16_refine", draws=1)
+    done = pt.check_elementwise(g, o, w.k, tau, g["B"])
+    print("bf16 %dx%d k=%d refine: e_gpu %.4e e_oracle %.4e ratio %.4f; separated steps %d; tau %s; compared %s"
+          % (m, n, w.k, e_g, e_o, e_g / e_o, sy, tau, done))
+    assert e_g / e_o <= E_RATIO_BAR["bf16_refine"], (e_g, e_o)
+
+
 
 
 def test_exact_rank_recovery_f64(rg):
