@@ -8,5 +8,6 @@ from .rlu import (KEY_TAG, STATUS_OK, STATUS_WRANK, SketchParams, LUResult,
                   hartley_columns, fjl, lu_partial_pivot, unit_lower,
                   pinv_householder, factor, relative_residual, check_sizes,
                   second_projection, factor_two_sketch,
-                  bucket_of_word, sign_of_word)
+                  bucket_of_word, sign_of_word, phase_of_word,
+                  TRANSFORMS, hadamard_columns, srft_columns, transform_matrix)
 from .philox import philox4x64_10, mulhilo64, stream_blocks

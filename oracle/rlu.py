@@ -49,6 +49,10 @@ STATUS_WRANK = 100  # an exact zero pivot was met; the factors are still valid
 # ---------------------------------------------------------------------------
 # Step 1: the random structures
 # ---------------------------------------------------------------------------
+#: the FFT-based projections of step 2 (transform of the l1 bucket sums)
+TRANSFORMS = ("hartley", "srht", "srft")
+
+
 @dataclass
 class SketchParams:
     h: np.ndarray  # (n,) int64, bucket of column j, in [0, l1)
@@ -56,6 +60,7 @@ class SketchParams:
     d: np.ndarray  # (l1,) float64, random sign of Hartley input b, +-1
     R: np.ndarray  # (l,) int64, kept frequencies, in key order
     R_keys: np.ndarray = field(repr=False, default=None)  # (l1,) uint64
+    theta: np.ndarray = field(repr=False, default=None)  # (l1,) phases of the complex D (srft)
 
 
 def bucket_of_word(w, l1):
@@ -97,7 +102,16 @@ def sketch_params(n, l1, l, seed):
     keys = b2[:, 0]
     order = sorted(range(l1), key=lambda b: (int(keys[b]), b))
     R = np.array(order[:l], dtype=np.int64)
-    return SketchParams(h=h, s=s, d=d, R=R, R_keys=keys)
+    # stream 3, b < l1: the phase of the complex unit-modulus D of the SRFT
+    b3 = stream_blocks(key, 3, l1)
+    theta = np.array([phase_of_word(w) for w in b3[:, 0]], dtype=np.float64)
+    return SketchParams(h=h, s=s, d=d, R=R, R_keys=keys, theta=theta)
+
+
+def phase_of_word(w):
+    """A uniform phase in [0, 2 pi) from a 64-bit word: 2 pi u with u the top
+    53 bits of w over 2^53 (exact in FP64, so u < 1)."""
+    return 2.0 * np.pi * ((int(w) >> 11) * 2.0 ** -53)
 
 
 def sem_matrix(params, l1):
@@ -140,14 +154,66 @@ def hartley_columns(l1, freqs):
     return np.cos(ang) + np.sin(ang)
 
 
-def fjl(Y1, params, l1):
-    """Y = Y1 D H[:, R] / sqrt(l1): signs, Hartley transform, subsample.
+def hadamard_columns(l1, cols):
+    """Columns `cols` of the l1 x l1 Walsh-Hadamard matrix in Sylvester order,
+    H[b, c] = (-1)^popcount(b & c), l1 a power of two (the SRHT of Sec. 4)."""
+    if l1 & (l1 - 1):
+        raise ValueError("the Walsh-Hadamard transform needs l1 a power of two")
+    b = np.arange(l1, dtype=np.int64)[:, None]
+    x = b & np.asarray(cols, dtype=np.int64)[None, :]
+    par = np.zeros_like(x)
+    while np.any(x):
+        par ^= x & 1
+        x >>= 1
+    return 1.0 - 2.0 * par
+
+
+def srft_columns(l1, theta, freqs):
+    """The real form of the complex SRFT of Sec. 2.1 (Pi = D F S with D
+    diagonal of unit-modulus entries exp(i theta_b) and F the DFT): for each
+    kept frequency f, the real and imaginary parts of exp(i theta_b) exp(-2 pi
+    i b f / l1), interleaved: columns (cos phi, sin phi), phi_b = theta_b -
+    2 pi (b f mod l1) / l1.  An l1 x 2 len(freqs) array."""
+    b = np.arange(l1, dtype=np.int64)[:, None]
+    t = (b * np.asarray(freqs, dtype=np.int64)[None, :]) % l1
+    phi = theta[:, None] - 2.0 * np.pi * t.astype(np.float64) / l1
+    out = np.empty((l1, 2 * len(freqs)))
+    out[:, 0::2] = np.cos(phi)
+    out[:, 1::2] = np.sin(phi)
+    return out
+
+
+def transform_matrix(params, l1, l, transform="hartley"):
+    """The l1 x l matrix M of step 2's FFT-based projection, Y = Y1 M.
+
+      hartley: D H R / sqrt(l1) with D = diag(d) (+-1), H the real Hartley
+               kernel cas(2 pi b f / l1) (the default reading for real data);
+      srht:    D W R / sqrt(l1) with W the Walsh-Hadamard matrix (l1 a power
+               of two);
+      srft:    the complex D F R with D = diag(exp(i theta)), realified: the
+               first l/2 kept frequencies give the real and imaginary parts as
+               two columns each, scaled by sqrt(2 / l1) (l even).
+    Every variant keeps the l columns of R in key order.
+    """
+    if transform == "hartley":
+        return params.d[:, None] * hartley_columns(l1, params.R) / np.sqrt(l1)
+    if transform == "srht":
+        return params.d[:, None] * hadamard_columns(l1, params.R) / np.sqrt(l1)
+    if transform == "srft":
+        if l % 2:
+            raise ValueError("the realified SRFT needs an even l")
+        return srft_columns(l1, params.theta, params.R[: l // 2]) * np.sqrt(2.0 / l1)
+    raise ValueError("unknown transform %r" % (transform,))
+
+
+def fjl(Y1, params, l1, transform="hartley"):
+    """Y = Y1 M with M = transform_matrix(...): signs (or phases), the
+    transform, the subsample.
 
     Direct O(l1 * l) sum per row (Lemma 2.1 states the fast-transform cost; the
     oracle deliberately uses the plain definition instead).
     """
-    M = params.d[:, None] * hartley_columns(l1, params.R) / np.sqrt(l1)
-    return Y1 @ M
+    return Y1 @ transform_matrix(params, l1, len(params.R), transform)
 
 
 # ---------------------------------------------------------------------------
@@ -263,15 +329,16 @@ def check_sizes(m, n, k, l, l1):
         raise ValueError("need l <= m and k <= min(m, n)")
 
 
-def factor(A, k, l, l1, seed):
-    """Sparse randomized LU of A (dense ndarray or scipy.sparse), all FP64."""
+def factor(A, k, l, l1, seed, transform="hartley"):
+    """Sparse randomized LU of A (dense ndarray or scipy.sparse), all FP64.
+    `transform` selects step 2's FFT-based projection (transform_matrix)."""
     m, n = A.shape
     check_sizes(m, n, k, l, l1)
     status = STATUS_OK
     # step 1
     params = sketch_params(n, l1, l, seed)
     # step 2
-    Y = fjl(countsketch(A, params, l1), params, l1)
+    Y = fjl(countsketch(A, params, l1), params, l1, transform)
     # step 3: l elimination steps on the m x l sketch, then truncate to k
     ly = lu_partial_pivot(Y, steps=l)
     if ly.zero_pivot:
