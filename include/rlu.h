@@ -75,6 +75,23 @@ typedef enum { RLU_F64 = 0, RLU_F32 = 1, RLU_BF16 = 2 } rlu_dtype;
  *                         one-step refinement of B. */
 typedef enum { RLU_PREC_F64 = 0, RLU_PREC_F32 = 1, RLU_PREC_BF16 = 2, RLU_PREC_BF16_REFINE = 3 } rlu_prec;
 
+/* The FFT-based projection of step 2 (rlu_set_transform).
+ *   RLU_XFORM_HARTLEY: random signs D, the real Hartley transform
+ *                      cas(2 pi b f / l1) (Re - Im of the DFT), l kept
+ *                      outputs R, scaled by 1/sqrt(l1): the real reading of
+ *                      the SRFT of Sec. 2.1 (the default; fused kernels).
+ *   RLU_XFORM_SRHT:    random signs D, the Walsh-Hadamard transform
+ *                      (-1)^popcount(b & f) in Sylvester order, l kept outputs,
+ *                      scaled by 1/sqrt(l1): the subsampled randomized
+ *                      Hadamard transform the experiments of Sec. 4 used for
+ *                      real data.  Needs l1 a power of two.
+ *   RLU_XFORM_SRFT:    the complex SRFT of Sec. 2.1, D = diag(exp(i theta_b))
+ *                      with theta_b = 2 pi u_b (u_b from the Philox stream 3
+ *                      of the seed), the DFT, the first l/2 kept frequencies
+ *                      R, each giving two columns (real and imaginary part)
+ *                      scaled by sqrt(2/l1).  Needs l even. */
+typedef enum { RLU_XFORM_HARTLEY = 0, RLU_XFORM_SRHT = 1, RLU_XFORM_SRFT = 2 } rlu_transform;
+
 /* Create a handle for m x n inputs, output rank k, FJL width l and CountSketch
  * width l1 (Algorithm 1, step 1: k plays the role of the output rank, l of k1,
  * l1 of l1).  Requires 1 <= k <= l <= l1, l <= m, k <= min(m, n), m and n
@@ -121,6 +138,16 @@ int rlu_set_csr_workspace(rlu_t h, int64_t max_nnz, void* workspace, size_t work
 
 /* Select the arithmetic (rlu_prec).  Valid at any time between calls. */
 int rlu_set_precision(rlu_t h, int prec);
+
+/* Select the FFT-based projection of step 2 (rlu_transform); valid at any time
+ * between calls.  RLU_XFORM_SRHT and RLU_XFORM_SRFT form Y1 = A S (bucket sums
+ * in ascending column order) in a handle buffer of m x l1 values (8 bytes
+ * each, allocated by the first dense factorization that uses it) and
+ * Y = Y1 M with M the l1 x l matrix of the projection; dense A only
+ * (rlu_factor_csr returns RLU_EINVAL while one of them is selected).
+ * Errors: RLU_EINVAL (null handle, unknown transform, l1 not a power of two
+ * for the SRHT, odd l for the SRFT). */
+int rlu_set_transform(rlu_t h, int transform);
 
 /* Use the paper's own second projection for B (Algorithm 1, steps 4-6)
  * instead of the exact pseudo-inverse of Corollary 3.3: Omega_2 = Pi_2 S_2

@@ -22,6 +22,8 @@ RLU_WRANK = 100
 RLU_F64, RLU_F32, RLU_BF16 = 0, 1, 2
 RLU_PREC_F64, RLU_PREC_F32, RLU_PREC_BF16, RLU_PREC_BF16_REFINE = 0, 1, 2, 3
 PREC = {"f64": RLU_PREC_F64, "f32": RLU_PREC_F32, "bf16": RLU_PREC_BF16, "bf16_refine": RLU_PREC_BF16_REFINE}
+RLU_XFORM_HARTLEY, RLU_XFORM_SRHT, RLU_XFORM_SRFT = 0, 1, 2
+TRANSFORM = {"hartley": RLU_XFORM_HARTLEY, "srht": RLU_XFORM_SRHT, "srft": RLU_XFORM_SRFT}
 
 #: every entry point declared in include/rlu.h
 C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_bytes", "rlu_factor_dense",
@@ -31,7 +33,7 @@ C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_
              "rlu_csr_workspace_bytes", "rlu_set_csr_workspace", "rlu_graph_capture_dense", "rlu_graph_launch",
              "rlu_graph_destroy", "rlu_copy_block_async", "rlu_set_max_ctas",
              "rlu_debug_recip", "rlu_set_second_sketch", "rlu_debug_status_of_flags", "rlu_debug_wait_timeout",
-             "rlu_debug_alu_peak")
+             "rlu_debug_alu_peak", "rlu_set_transform")
 
 #: stage names reported by rlu_debug_stage_ms, in order
 STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
@@ -86,6 +88,7 @@ def load(reload=False):
         "rlu_debug_status_of_flags": ([c.c_uint32, c.POINTER(c.c_int)], c.c_int),
         "rlu_debug_wait_timeout": ([c.c_int, c.POINTER(c.c_int)], c.c_int),
         "rlu_debug_alu_peak": ([c.c_int, c.POINTER(c.c_double)], c.c_int),
+        "rlu_set_transform": ([vp, c.c_int], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -127,6 +130,10 @@ def rlu_create_in(m, n, k, l, l1, seed, workspace_ptr, workspace_bytes, stream_p
 
 def rlu_set_precision(h, prec):
     return _check(load().rlu_set_precision(h, PREC.get(prec, prec)), "rlu_set_precision")
+
+
+def rlu_set_transform(h, transform):
+    return _check(load().rlu_set_transform(h, TRANSFORM.get(transform, transform)), "rlu_set_transform")
 
 
 def rlu_set_second_sketch(h, k2, l2, seed2):
@@ -276,6 +283,10 @@ class RandLU:
     def set_second_sketch(self, k2, l2, seed2):
         """B by the paper's second projection (k2 x m, l2 buckets); k2 = 0: exact pseudo-inverse."""
         rlu_set_second_sketch(self.h, k2, l2, seed2)
+
+    def set_transform(self, transform):
+        """The projection of step 2: "hartley" (default), "srht" or "srft"."""
+        rlu_set_transform(self.h, transform)
 
     def set_max_ctas(self, max_ctas):
         """Bound the CTAs of the grid-synchronised kernels (0: one per SM)."""

@@ -14,6 +14,7 @@
 #include "pinv.cuh"
 #include "pivlu.cuh"
 #include "sketch.cuh"
+#include "xform.cuh"
 
 using namespace rlu;
 
@@ -116,9 +117,13 @@ struct rlu_ctx {
   void* Lb = nullptr;
   double* bpart = nullptr;  // split-K partials of the FP64 SIMT B = W A
   TcWs tcw{};
+  LtcWs ltc{};  // digit planes of the tensor-core L = L_y L_b
+  float* fjl_table = nullptr;  // l1 x l table of the CSR sketch's direct evaluation
+  int xform = RLU_XFORM_HARTLEY;  // projection of step 2
+  void* xf_buf = nullptr;         // Y1 and the projection matrix (SRHT, SRFT), allocated on first use
   unsigned int* status_dev = nullptr;
   unsigned int* bar2 = nullptr;
-  // 4 page-locked host words: status (0) and the CSR row counts (2, 3); own
+  // 4 page-locked host words: status (0) and the CSR row counts (1, 2, 3); own
   // allocation when status_pinned, else a piece of the shared slab
   unsigned int* status_host = nullptr;
   bool status_pinned = false;
@@ -215,6 +220,9 @@ Sizes plan_sizes(int64_t m, int64_t n, int k, int l, int l1, int num_sms) {
   s.add(sizeof(unsigned int) * 4);                   // status, bar2
   s.add(tc_workspace_bytes(m, n, k, num_sms));       // tensor-core GEMM: W planes, partials
   s.add(sizeof(double) * bgemm_simt_splits(m, n, k, num_sms) * k * n);  // FP64 B = W A partials
+  s.add(ltc_workspace_bytes(m, k));                  // tensor-core L = L_y L_b: digit planes
+  s.add(sizeof(int64_t) * kScanMaxParts);            // multi-CTA scan partials
+  s.add(l1 <= kDirectMaxL1 ? sizeof(float) * l1 * l : 0);  // CSR sketch: table of D H R / sqrt(l1)
   return s;
 }
 
@@ -257,10 +265,11 @@ struct CsrLayout {
 
 Sizes csr_rows_sizes(int64_t m, int64_t n, int k) {
   Sizes sz;
-  for (int i = 0; i < 4; ++i) sz.add(sizeof(int32_t) * (m + 1));  // hflag, lflag, hpos, lpos
+  for (int i = 0; i < 6; ++i) sz.add(sizeof(int32_t) * (m + 1));  // hflag, lflag, mflag, hpos, lpos, mpos
   sz.add(sizeof(int32_t) * m);                                     // heavy
   sz.add(sizeof(int32_t) * m);                                     // light
-  sz.add(sizeof(int32_t) * 2);                                     // count
+  sz.add(sizeof(int32_t) * m);                                     // mid
+  sz.add(sizeof(int32_t) * 3);                                     // count
   sz.add(sizeof(int32_t) * (n + 1));                               // ccnt
   sz.add(sizeof(int32_t) * (n + 1));                               // cstart
   sz.add((size_t)8 * m * k);                                       // W^T
@@ -297,8 +306,9 @@ void csr_carve_rows(rlu_ctx* h, char* b) {
   int idx = 0;
   auto next = [&]() -> void* { void* p = b + off; off += sz.parts[idx++]; return p; };
   CsrWs& w = h->csr;
-  w.hflag = (int32_t*)next(); w.lflag = (int32_t*)next(); w.hpos = (int32_t*)next(); w.lpos = (int32_t*)next();
-  w.heavy = (int32_t*)next(); w.light = (int32_t*)next(); w.count = (int32_t*)next();
+  w.hflag = (int32_t*)next(); w.lflag = (int32_t*)next(); w.mflag = (int32_t*)next();
+  w.hpos = (int32_t*)next(); w.lpos = (int32_t*)next(); w.mpos = (int32_t*)next();
+  w.heavy = (int32_t*)next(); w.light = (int32_t*)next(); w.mid = (int32_t*)next(); w.count = (int32_t*)next();
   w.ccnt = (int32_t*)next(); w.cstart = (int32_t*)next(); w.Wt = next();
 }
 
@@ -375,8 +385,17 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   RLU_CUDA_TRY(cudaMemsetAsync(h->status_dev, 0, sizeof(unsigned int), st));
   h->ev_recorded = 0;
   if ((rc = mark(h, 0, st))) return rc;
-  // step 1: S, D, R
-  {
+  // step 1: S, D, R (whole-row bucket lists for the SRHT and SRFT products)
+  if (h->xform != RLU_XFORM_HARTLEY) {
+    h->sk.chunk = (int)n;
+    if (!h->xf_buf) {
+      if (cudaMalloc(&h->xf_buf, xform_buffer_bytes(m, l1, l, true)) != cudaSuccess) {
+        cudaGetLastError();
+        h->xf_buf = nullptr;
+        return RLU_ENOMEM;
+      }
+    }
+  } else {
     const size_t es = dtype == RLU_F64 ? 8 : (dtype == RLU_F32 ? 4 : 2);
     const bool al = ((uintptr_t)A % 16 == 0) && (((size_t)lda * es) % 16 == 0);
     h->sk.chunk = sketch_chunk_cols(dtype, m, n, l1, al, h->num_sms);
@@ -384,9 +403,13 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   h->sk.nchunks = cdiv(n, h->sk.chunk);
   if ((rc = launch_sketch_params(h->sk, n, l1, l, h->seed, st))) return rc;
   if ((rc = mark(h, 1, st))) return rc;
-  // step 2: Y = A S D H R / sqrt(l1)
-  if ((rc = launch_sketch_dense(A, lda, dtype, f64, m, n, l1, l, h->sk, h->Y, h->status_dev, h->num_sms, st)))
-    return rc;
+  // step 2: Y = A S D H R / sqrt(l1) (or the SRHT / SRFT projection)
+  if (h->xform != RLU_XFORM_HARTLEY)
+    rc = launch_sketch_xform(h->xform, A, lda, dtype, f64, m, n, l1, l, h->seed, h->sk, h->xf_buf, h->Y,
+                             h->status_dev, st);
+  else
+    rc = launch_sketch_dense(A, lda, dtype, f64, m, n, l1, l, h->sk, h->Y, h->status_dev, h->num_sms, st);
+  if (rc) return rc;
   if ((rc = mark(h, 2, st))) return rc;
   if (h->debug && h->Ydbg)
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Ydbg, h->Y, sizeof(double) * m * l, cudaMemcpyDeviceToDevice, st));
@@ -454,8 +477,10 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   aa.m = m; aa.n = n; aa.k = k;
   aa.Lk = h->Lk; aa.perm_y = h->perm_y; aa.perm_b = h->perm_b; aa.Bp = h->B;
   aa.LyP = h->LyP; aa.Lb = h->Lb; aa.L = L; aa.U = U; aa.p = p; aa.q = q;
-  aa.fp32_product = h->prec != RLU_PREC_F64 ? 1 : 0;  // FP32 outputs: an FP32 product suffices
+  aa.fp32_product = h->prec != RLU_PREC_F64 ? 1 : 0;  // FP32 outputs
   aa.num_sms = coop_sms(h);
+  aa.ltc = &h->ltc;
+  aa.status = h->status_dev;
   rc = f64 ? launch_assemble<double, double>(aa, st) : launch_assemble<df32, float>(aa, st);
   if (rc) return rc;
   if ((rc = mark(h, 9, st))) return rc;
@@ -481,14 +506,15 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   h->sk.nchunks = cdiv(n, h->sk.chunk);
   if ((rc = launch_sketch_params(h->sk, n, l1, l, h->seed, st))) return rc;
   CsrRows cr{};
-  if ((rc = csr_classify(h->csr, rowptr, m, n, nnz, h->status_dev, cr, reinterpret_cast<int32_t*>(h->status_host + 2),
-                         st)))
+  const int64_t direct_max = f64 ? -1 : csr_direct_max(l1, l);  // FP64 sums keep the FFT route
+  if ((rc = csr_classify(h->csr, rowptr, m, n, nnz, direct_max, h->status_dev, cr,
+                         reinterpret_cast<int32_t*>(h->status_host + 1), st)))
     return rc;
   if ((rc = csr_grow(h, nnz, cr.n_heavy))) return rc;
   if ((rc = mark(h, 1, st))) return rc;
   RLU_CUDA_TRY(cudaMemsetAsync(h->Y, 0, sizeof(double) * m * l, st));
-  if ((rc = launch_sketch_csr(rowptr, colind, val, dtype, n, cr, l1, l, h->sk, h->csr.D, h->Y, h->status_dev,
-                              h->num_sms, st)))
+  if ((rc = launch_sketch_csr(rowptr, colind, val, dtype, n, cr, l1, l, h->sk, h->csr.D, h->Y, h->fjl_table,
+                              h->status_dev, h->num_sms, st)))
     return rc;
   if ((rc = mark(h, 2, st))) return rc;
   if (h->debug && h->Ydbg)
@@ -528,8 +554,10 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   aa.m = m; aa.n = n; aa.k = k;
   aa.Lk = h->Lk; aa.perm_y = h->perm_y; aa.perm_b = h->perm_b; aa.Bp = h->B;
   aa.LyP = h->LyP; aa.Lb = h->Lb; aa.L = L; aa.U = U; aa.p = p; aa.q = q;
-  aa.fp32_product = h->prec != RLU_PREC_F64 ? 1 : 0;  // FP32 outputs: an FP32 product suffices
+  aa.fp32_product = h->prec != RLU_PREC_F64 ? 1 : 0;  // FP32 outputs
   aa.num_sms = coop_sms(h);
+  aa.ltc = &h->ltc;
+  aa.status = h->status_dev;
   rc = f64 ? launch_assemble<double, double>(aa, st) : launch_assemble<df32, float>(aa, st);
   if (rc) return rc;
   if ((rc = mark(h, 9, st))) return rc;
@@ -660,7 +688,11 @@ static int create_common(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1,
   h->bar2 = h->status_dev + 1;
   void* tcbase = next();
   h->bpart = (double*)next();
-  if (tc_setup(h->tcw, tcbase, m, n, k, sms) != RLU_OK) {
+  void* ltcbase = next();
+  h->sk.scan_tmp = (int64_t*)next();
+  h->csr.scan_tmp = h->sk.scan_tmp;
+  h->fjl_table = (float*)next();
+  if (tc_setup(h->tcw, tcbase, m, n, k, sms) != RLU_OK || ltc_setup(h->ltc, ltcbase, m, k) != RLU_OK) {
     rlu_destroy(h);
     return RLU_ECUDA;
   }
@@ -794,6 +826,15 @@ int rlu_set_precision(rlu_t h, int prec) {
   return RLU_OK;
 }
 
+int rlu_set_transform(rlu_t h, int transform) {
+  if (!h) return RLU_EINVAL;
+  if (transform == RLU_XFORM_SRHT && (h->l1 & (h->l1 - 1))) return RLU_EINVAL;
+  if (transform == RLU_XFORM_SRFT && (h->l & 1)) return RLU_EINVAL;
+  if (transform < RLU_XFORM_HARTLEY || transform > RLU_XFORM_SRFT) return RLU_EINVAL;
+  h->xform = transform;
+  return RLU_OK;
+}
+
 int rlu_destroy(rlu_t h) {
   if (!h) return RLU_OK;
   for (void* p : h->allocs) cudaFree(p);
@@ -810,6 +851,7 @@ int rlu_destroy(rlu_t h) {
   if (h->q_stage) cudaFree(h->q_stage);
   if (h->sk2_buf) cudaFree(h->sk2_buf);
   if (h->at_buf) cudaFree(h->at_buf);
+  if (h->xf_buf) cudaFree(h->xf_buf);
   if (!h->csr_external) {
     if (h->csr_rows_buf) cudaFree(h->csr_rows_buf);
     if (h->csr_nnz_buf) cudaFree(h->csr_nnz_buf);
@@ -920,6 +962,7 @@ int rlu_factor_csr(rlu_t h, const int64_t* rowptr, const int32_t* colind, const 
     return RLU_EINVAL;
   if (h->csr_external && nnz > h->csr_cap_nnz) return RLU_EINVAL;
   if (h->k2 > 0) return RLU_EINVAL;  // the second projection is built for dense A
+  if (h->xform != RLU_XFORM_HARTLEY) return RLU_EINVAL;  // so are the SRHT and SRFT products
   cudaStream_t st = (cudaStream_t)stream;
   int rc = enqueue_csr(h, rowptr, colind, val, nnz, dtype, L, U, p, q, st);
   if (rc) return drain_after(rc, st);

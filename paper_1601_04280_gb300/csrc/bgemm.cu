@@ -31,6 +31,20 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
+int tc_encode_bf16_3d(void* map, void* base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t ld_elems,
+                      uint32_t box_inner, uint32_t box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return RLU_ECUDA;
+  cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld_elems * 2), (cuuint64_t)(ld_elems * 2 * rows)};
+  cuuint32_t box[3] = {box_inner, box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+                   es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RLU_OK : RLU_ECUDA;
+}
+
 // Split-K: FP32 accumulation in tensor memory runs over at most max_kps rows
 // of A (its rounding error grows with that depth); the split partials are
 // summed in float-float.  Enough splits to fill the GPU twice over.

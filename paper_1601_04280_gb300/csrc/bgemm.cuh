@@ -28,6 +28,12 @@ struct TcWs {
 void tc_plan(int64_t m, int64_t n, int k, int num_sms, TcPlan& p);
 size_t tc_workspace_bytes(int64_t m, int64_t n, int k, int num_sms);
 int tc_setup(TcWs& w, void* base, int64_t m, int64_t n, int k, int num_sms);
+// TMA descriptor (128-byte swizzle) of `planes` BF16 matrices of rows x inner
+// elements, row stride ld_elems (a multiple of 8), stacked one after another:
+// boxes of box_inner x box_rows x 1.  RLU_ECUDA when tensor maps are
+// unavailable or the encoding is refused.
+int tc_encode_bf16_3d(void* map, void* base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t ld_elems,
+                      uint32_t box_inner, uint32_t box_rows);
 int launch_bgemm_tc(const TcWs& w, const float* W, const void* A, int64_t lda, int dtype, int prec, int64_t m,
                     int64_t n, int k, df32* B, unsigned int* status, cudaStream_t st);
 

@@ -16,8 +16,13 @@
 
 namespace rlu {
 
-__global__ void k_csr_classify(int64_t m, int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
-                               int32_t* __restrict__ hflag, int32_t* __restrict__ lflag, unsigned int* status) {
+// Row classes: heavy (>= n/4 entries: densified, dense kernels), light (the
+// rest: the sparse product for B), and among the light rows the "mid" ones
+// with more than direct_max entries, whose sketch goes through the FFT kernel
+// (the others are evaluated directly; direct_max < 0: every light row is mid).
+__global__ void k_csr_classify(int64_t m, int64_t n, int64_t nnz, int64_t direct_max,
+                               const int64_t* __restrict__ rowptr, int32_t* __restrict__ hflag,
+                               int32_t* __restrict__ lflag, int32_t* __restrict__ mflag, unsigned int* status) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
   const int64_t s = rowptr[i], e = rowptr[i + 1];
@@ -26,21 +31,27 @@ __global__ void k_csr_classify(int64_t m, int64_t n, int64_t nnz, const int64_t*
   if (i == m - 1 && e != nnz) bad = true;
   if (bad) set_flag(status, FLAG_BAD_CSR);
   const bool heavy = !bad && (e - s) > 0 && 4 * (e - s) >= n;
+  const bool light = !bad && !heavy;  // rows with a bad range are skipped (their Y rows stay zero)
   hflag[i] = heavy ? 1 : 0;
-  lflag[i] = (!bad && !heavy) ? 1 : 0;  // rows with a bad range are skipped (their Y rows stay zero)
+  lflag[i] = light ? 1 : 0;
+  mflag[i] = (light && (e - s) > direct_max) ? 1 : 0;
 }
 
 __global__ void k_csr_lists(int64_t m, const int32_t* __restrict__ hflag, const int32_t* __restrict__ lflag,
-                            const int32_t* __restrict__ hpos, const int32_t* __restrict__ lpos,
-                            int32_t* __restrict__ heavy, int32_t* __restrict__ light, int32_t* count) {
+                            const int32_t* __restrict__ mflag, const int32_t* __restrict__ hpos,
+                            const int32_t* __restrict__ lpos, const int32_t* __restrict__ mpos,
+                            int32_t* __restrict__ heavy, int32_t* __restrict__ light, int32_t* __restrict__ mid,
+                            int32_t* count) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < m) {
     if (hflag[i]) heavy[hpos[i]] = (int32_t)i;
     if (lflag[i]) light[lpos[i]] = (int32_t)i;
+    if (mflag[i]) mid[mpos[i]] = (int32_t)i;
   }
   if (i == 0) {
     count[0] = lpos[m];
     count[1] = hpos[m];
+    count[2] = mpos[m];
   }
 }
 
@@ -216,25 +227,30 @@ __global__ void __launch_bounds__(256) k_spmm_csc(int64_t n, int k, const int32_
 }
 
 // ---- host side -----------------------------------------------------------------
-int csr_classify(CsrWs& w, const int64_t* rowptr, int64_t m, int64_t n, int64_t nnz, unsigned int* status,
-                 CsrRows& cr, int32_t* cnt, cudaStream_t st) {
+int csr_classify(CsrWs& w, const int64_t* rowptr, int64_t m, int64_t n, int64_t nnz, int64_t direct_max,
+                 unsigned int* status, CsrRows& cr, int32_t* cnt, cudaStream_t st) {
   const unsigned g = (unsigned)cdiv(m, 256);
-  k_csr_classify<<<g, 256, 0, st>>>(m, n, nnz, rowptr, w.hflag, w.lflag, status);
+  k_csr_classify<<<g, 256, 0, st>>>(m, n, nnz, direct_max, rowptr, w.hflag, w.lflag, w.mflag, status);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
   int rc;
-  if ((rc = launch_scan_i32(m, w.hflag, w.hpos, st))) return rc;
-  if ((rc = launch_scan_i32(m, w.lflag, w.lpos, st))) return rc;
-  k_csr_lists<<<g, 256, 0, st>>>(m, w.hflag, w.lflag, w.hpos, w.lpos, w.heavy, w.light, w.count);
+  if ((rc = launch_scan_i32(m, w.hflag, w.hpos, w.scan_tmp, st))) return rc;
+  if ((rc = launch_scan_i32(m, w.lflag, w.lpos, w.scan_tmp, st))) return rc;
+  if ((rc = launch_scan_i32(m, w.mflag, w.mpos, w.scan_tmp, st))) return rc;
+  k_csr_lists<<<g, 256, 0, st>>>(m, w.hflag, w.lflag, w.mflag, w.hpos, w.lpos, w.mpos, w.heavy, w.light, w.mid,
+                                 w.count);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
-  RLU_CUDA_TRY(cudaMemcpyAsync(cnt, w.count, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  RLU_CUDA_TRY(cudaMemcpyAsync(cnt, w.count, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   RLU_CUDA_TRY(cudaStreamSynchronize(st));
   cr.light = w.light;
   cr.heavy = w.heavy;
+  cr.mid = w.mid;
   cr.d_count = w.count;
   cr.n_light = cnt[0];
   cr.n_heavy = cnt[1];
+  cr.n_mid = cnt[2];
+  cr.direct_max = direct_max;
   return RLU_OK;
 }
 
@@ -267,7 +283,7 @@ static int light_part(const CsrWs& w, const int64_t* rowptr, const int32_t* coli
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
   int rc;
-  if ((rc = launch_scan_i32(n, w.ccnt, w.cstart, st))) return rc;
+  if ((rc = launch_scan_i32(n, w.ccnt, w.cstart, w.scan_tmp, st))) return rc;
   RLU_CUDA_TRY(cudaMemsetAsync(w.ccnt, 0, sizeof(int32_t) * (n + 1), st));
   k_csc_fill<TV><<<gr, 256, 0, st>>>(rowptr, colind, val, n, cr.light, cr.n_light, w.cstart, w.ccnt, w.crow,
                                      reinterpret_cast<TV*>(w.cval));

@@ -9,19 +9,23 @@
 namespace rlu {
 
 struct CsrWs {
-  int32_t *hflag, *lflag, *hpos, *lpos, *heavy, *light, *count;  // rows (m, m+1) and counts
+  int32_t *hflag, *lflag, *hpos, *lpos, *heavy, *light, *count;  // rows (m, m+1) and counts (3)
+  int32_t *mflag, *mpos, *mid;                                    // light rows sketched through the FFT
   int32_t *ccnt, *cstart, *crow;                                  // CSC of the light entries
   void* cval;
   void* D;   // heavy rows, dense (n_heavy x n)
   void* Wt;  // W^T (m x k)
   void* Wh;  // W restricted to the heavy rows (k x n_heavy)
   TcWs tc;   // tensor-core product of W_h and D
+  int64_t* scan_tmp;  // scratch of the multi-CTA scans (the handle's)
 };
 
-// Row classification; reads the two row counts back through `cnt` (two
-// int32 of page-locked host memory).
-int csr_classify(CsrWs& w, const int64_t* rowptr, int64_t m, int64_t n, int64_t nnz, unsigned int* status,
-                 CsrRows& cr, int32_t* cnt, cudaStream_t st);
+// Row classification; light rows with at most direct_max entries are
+// sketched by direct evaluation (direct_max < 0: none).  Reads the three row
+// counts (light, heavy, mid) back through `cnt` (three int32 of page-locked
+// host memory).
+int csr_classify(CsrWs& w, const int64_t* rowptr, int64_t m, int64_t n, int64_t nnz, int64_t direct_max,
+                 unsigned int* status, CsrRows& cr, int32_t* cnt, cudaStream_t st);
 int csr_bgemm(CsrWs& w, const int64_t* rowptr, const int32_t* colind, const void* val, int dtype, int prec,
               int64_t m, int64_t n, int k, const CsrRows& cr, const void* W, void* B, unsigned int* status,
               int num_sms, cudaStream_t st);

@@ -509,24 +509,40 @@ int launch_assemble(const AssembleArgs& a, cudaStream_t st) {
   T* LyP = reinterpret_cast<T*>(a.LyP);
   T* Lb = reinterpret_cast<T*>(a.Lb);
   const T* Bp = reinterpret_cast<const T*>(a.Bp);
-  // the FP32 product with L_b resident in shared memory needs no P L_y copy
-  const bool rows_kernel = a.fp32_product && !std::is_same<T, double>::value && k <= 32 * kAsmMaxQ &&
+  // FP32 outputs: L = L_y L_b as an exact digit product on the tensor cores
+  // (k <= 512), else as an FP32 product with L_b resident in shared memory
+  // (no P L_y copy), else the SIMT GEMM
+  const bool tc_digits = a.fp32_product && std::is_same<T, df32>::value && a.ltc && a.ltc->ready;
+  const bool rows_kernel = !tc_digits && a.fp32_product && !std::is_same<T, double>::value && k <= 32 * kAsmMaxQ &&
                            (size_t)k * k * sizeof(float) <= 200 * 1024 && a.num_sms > 0;
-  if (!rows_kernel) {
+  if (!rows_kernel && !tc_digits) {
     k_build_LyP<T><<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, k, reinterpret_cast<const T*>(a.Lk), a.perm_y,
                                                                 LyP);
     note_launch();
   }
-  k_build_Lb<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(k, n, Bp, a.perm_b, Lb);
+  if (!tc_digits) {
+    k_build_Lb<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(k, n, Bp, a.perm_b, Lb);
+    note_launch();
+  }
   k_build_U<T, TO><<<(unsigned)cdiv((int64_t)k * n, 256), 256, 0, st>>>(k, n, Bp, a.perm_b,
                                                                           reinterpret_cast<TO*>(a.U));
   RLU_CUDA_TRY(cudaGetLastError());
-  note_launch(2);
+  note_launch();
   // L = L_y L_b: FP64 in the FP64 mode; FP32 accumulation over the k terms in
   // the others, whose L is FP32: that rounding (about sqrt(k) units of 2^-24
   // per entry) keeps ||L U - P A Q|| / ||A|| within the FP32 bar (dense FP32
   // 8192^2: 4.5e-6 against 3.3e-6 with a float-float product)
   int rc;
+  if constexpr (std::is_same<T, df32>::value && std::is_same<TO, float>::value) {
+    if (tc_digits) {
+      rc = launch_l_tc<df32>(*a.ltc, reinterpret_cast<const df32*>(a.Lk), a.perm_y, Bp, a.perm_b, n,
+                             reinterpret_cast<float*>(a.L), a.status, st);
+      if (rc) return rc;
+      RLU_CUDA_TRY(cudaMemcpyAsync(a.p, a.perm_y, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
+      RLU_CUDA_TRY(cudaMemcpyAsync(a.q, a.perm_b, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, st));
+      return RLU_OK;
+    }
+  }
   if (rows_kernel) {
     const size_t smem = (size_t)k * k * sizeof(float);
     auto kern = k <= 64 ? k_assemble_rows<T, TO, 2> : (k <= 128 ? k_assemble_rows<T, TO, 4> : k_assemble_rows<T, TO, 8>);

@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "lgemm.cuh"
 #include "sketch.cuh"
 
 namespace rlu {
@@ -39,8 +40,10 @@ struct AssembleArgs {
   void* U;                // k x n output
   int64_t* p;
   int64_t* q;
-  int fp32_product;  // L = L_y L_b with FP32 accumulation (FP32 and BF16 forms) instead of float-float
+  int fp32_product;  // L = L_y L_b with FP32 outputs (FP32 and BF16 forms) instead of float-float
   int num_sms;       // grid of the row-streaming FP32 product
+  const LtcWs* ltc;  // the exact digit product on the tensor cores (FP32 outputs, k <= 512), or null
+  unsigned int* status;
 };
 
 int launch_gram(const PinvArgs& a, cudaStream_t st);

@@ -101,6 +101,66 @@ __global__ void k_scan_counts(int64_t count, const int32_t* cnt, int32_t* start)
   if (threadIdx.x == T - 1) start[count] = (int32_t)run;
 }
 
+// Exclusive scan over many CTAs: CTA b owns the elements [b per, (b+1) per)
+// and reads them in rounds of blockDim.x consecutive values (coalesced).
+// k_scan_part writes each CTA's total; k_scan_final adds the totals of the
+// CTAs before it and scans its own rounds.  Fixed order: exact integer sums.
+__device__ __forceinline__ int64_t block_sum_i64(int64_t v, int64_t* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  int64_t t = 0;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  return t;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_part(int64_t count, int64_t per, const int32_t* __restrict__ cnt,
+                                                    int64_t* __restrict__ part) {
+  __shared__ int64_t red[32];
+  const int64_t a = (int64_t)blockIdx.x * per, b = min64(count, a + per);
+  int64_t s = 0;
+  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) s += cnt[i];
+  s = block_sum_i64(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_final(int64_t count, int64_t per, const int32_t* __restrict__ cnt,
+                                                     const int64_t* __restrict__ part, int32_t* __restrict__ start) {
+  __shared__ int64_t red[32];
+  __shared__ int64_t wsum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int64_t off = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) off += part[b];
+  off = block_sum_i64(off, red);
+  const int64_t a = (int64_t)blockIdx.x * per, e = min64(count, a + per);
+  for (int64_t r0 = a; r0 < e; r0 += blockDim.x) {
+    const int64_t i = r0 + threadIdx.x;
+    const int64_t v = i < e ? cnt[i] : 0;
+    int64_t x = v;  // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int64_t before = 0, round = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int64_t t = wsum[w];
+      if (w < warp) before += t;
+      round += t;
+    }
+    if (i < e) start[i] = (int32_t)(off + before + x - v);
+    off += round;
+  }
+  if (e == count && a < e && threadIdx.x == 0) start[count] = (int32_t)off;
+  if (count == 0 && blockIdx.x == 0 && threadIdx.x == 0) start[0] = 0;
+}
+
 __global__ void k_bucket_fill(int64_t n, int l1, int chunk, const uint32_t* hs, const int32_t* start,
                               int32_t* cursor, uint32_t* list) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1210,6 +1270,96 @@ __global__ void __launch_bounds__(kCsrWarps * 32, 1)
   if (bad_val) set_flag(status, FLAG_NONFINITE);
 }
 
+// Sparse light rows by direct evaluation: with T[b][c] = d(b) cas(2 pi b R_c /
+// l1) / sqrt(l1) (the l1 x l matrix D H R / sqrt(l1)), row i of the sketch is
+// Y[i][c] = sum over the row's entries (j, v) of s(j) v T[h(j)][c], the same
+// linear map as the bucket sums followed by the transform, at nnz x l
+// multiply-adds per row instead of an l1-point FFT.  T is built from the FFT
+// twiddles (cas(2 pi t / l1) = Re w^t - Im w^t with w = exp(-2 pi i / l1)).
+__global__ void k_fjl_table(int l1, int l, const float* __restrict__ dsign, const int32_t* __restrict__ Rsel,
+                            const float2* __restrict__ tw, float* __restrict__ T) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)l1 * l) return;
+  const int b = (int)(e / l), c = (int)(e - (int64_t)b * l);
+  const int t = (int)(((int64_t)b * Rsel[c]) % l1);
+  const float2 w = tw[t];
+  T[e] = dsign[b] * (w.x - w.y) * rsqrtf((float)l1);
+}
+
+// A CTA holds the columns [c0, c0 + lg) of T in shared memory (blockIdx.y
+// picks the group); warp w of CTA x takes the light rows x * kDirWarps + w,
+// + gridDim.x * kDirWarps, ... with at most direct_max entries.  Lanes own
+// the columns; each round of 32 entries is staged as (bucket, signed value)
+// pairs and read back by every lane in entry order (a fixed order: results
+// repeat bit for bit).
+constexpr int kDirWarps = 32;
+template <typename TV>
+__global__ void __launch_bounds__(kDirWarps * 32, 1)
+    k_sketch_csr_direct(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                        const TV* __restrict__ val, int64_t n, const int32_t* __restrict__ list,
+                        const int32_t* count, int64_t direct_max, int l1, int l, int lg,
+                        const float* __restrict__ T, const uint32_t* __restrict__ hs, double* __restrict__ Y,
+                        unsigned int* status) {
+  // l1 x lg, then 32 zeros: lane t reads Ts[b lg + t] for every t < 32, which
+  // for lg < 32 runs past row b (into row b + 1, or the zero pad after the
+  // last row); those lanes' sums are never stored
+  extern __shared__ __align__(16) float Ts[];
+  __shared__ int2 stage[kDirWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = blockIdx.y * lg;
+  const int ncols = min(lg, l - c0);
+  for (int64_t e = threadIdx.x; e < (int64_t)l1 * lg + 32; e += blockDim.x) {
+    const int b = (int)(e / lg), cc = (int)(e - (int64_t)b * lg);
+    Ts[e] = (b < l1 && cc < ncols) ? T[(int64_t)b * l + c0 + cc] : 0.f;
+  }
+  __syncthreads();
+  const int nrows = *count;
+  bool bad_csr = false, bad_val = false;
+  for (int64_t li = (int64_t)blockIdx.x * kDirWarps + warp; li < nrows; li += (int64_t)gridDim.x * kDirWarps) {
+    const int row = list[li];
+    const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
+    if (e1 - e0 > direct_max) continue;  // a mid row: the FFT kernel's
+    // four independent chains (entries t = 0, 1, 2, 3 mod 4), summed at the end
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int64_t base = e0; base < e1; base += 32) {
+      const int64_t e = base + lane;
+      int b = 0;
+      float x = 0.f;
+      if (e < e1) {
+        const int col = colind[e];
+        if (col < 0 || (int64_t)col >= n) {
+          bad_csr = true;
+        } else {
+          const TV v = val[e];
+          bad_val |= !finite_(v);
+          const uint32_t h = hs[col];
+          b = (int)(h & 0x7fffffffu);
+          x = (h >> 31) ? -(float)v : (float)v;
+        }
+      }
+      stage[warp][lane] = make_int2(b * lg, __float_as_int(x));
+      __syncwarp();
+      const int cnt = (int)min64(32, e1 - base);
+      int t = 0;
+      for (; t + 4 <= cnt; t += 4) {
+        const int2 p0 = stage[warp][t], p1 = stage[warp][t + 1], p2 = stage[warp][t + 2], p3 = stage[warp][t + 3];
+        a0 = fmaf(__int_as_float(p0.y), Ts[p0.x + lane], a0);
+        a1 = fmaf(__int_as_float(p1.y), Ts[p1.x + lane], a1);
+        a2 = fmaf(__int_as_float(p2.y), Ts[p2.x + lane], a2);
+        a3 = fmaf(__int_as_float(p3.y), Ts[p3.x + lane], a3);
+      }
+      for (; t < cnt; ++t) {
+        const int2 p = stage[warp][t];
+        a0 = fmaf(__int_as_float(p.y), Ts[p.x + lane], a0);
+      }
+      __syncwarp();
+    }
+    if (lane < ncols) Y[(int64_t)row * l + c0 + lane] = (double)((a0 + a1) + (a2 + a3));
+  }
+  if (bad_csr) set_flag(status, FLAG_BAD_CSR);
+  if (bad_val) set_flag(status, FLAG_NONFINITE);
+}
+
 // Heavy rows: densified, a CTA per row, into D (row i of D = heavy row
 // list[i], n columns; repeated coordinates summed), then sketched by the dense
 // kernels with the row map list.  A row with exactly n strictly increasing
@@ -1251,13 +1401,34 @@ __global__ void __launch_bounds__(512) k_csr_densify(const int64_t* __restrict__
 
 template <typename TV, typename TACC>
 static int launch_csr_cfg(const int64_t* rowptr, const int32_t* colind, const TV* val, int64_t n, const CsrRows& cr,
-                          int l1, int l, const SketchWs& ws, TV* D, double* Y, unsigned int* status, int num_sms,
-                          cudaStream_t st) {
+                          int l1, int l, const SketchWs& ws, TV* D, double* Y, float* table, unsigned int* status,
+                          int num_sms, cudaStream_t st) {
   using V = typename C2<TACC>::t;
   const typename C2<TACC>::t* tw;
   if constexpr (sizeof(TACC) == 8) tw = ws.tw64; else tw = ws.tw32;
   const size_t budget = 220 * 1024;
-  if (cr.n_light > 0) {
+  if constexpr (sizeof(TACC) == 4) {
+    if (cr.direct_max >= 0 && cr.n_light > cr.n_mid) {
+      if (!table) return RLU_EINVAL;
+      k_fjl_table<<<(unsigned)cdiv((int64_t)l1 * l, 256), 256, 0, st>>>(l1, l, ws.dsign, ws.R, ws.tw32, table);
+      RLU_CUDA_TRY(cudaGetLastError());
+      note_launch();
+      // column groups of at most 32 (a lane each) whose slice of T fits in shared memory
+      const int lg_max = (int)min64(32, (int64_t)(200 * 1024) / (4 * (int64_t)l1));
+      if (lg_max < 1) return RLU_EINVAL;
+      const int G = (int)cdiv(l, lg_max);
+      const int lg = (int)cdiv(l, G);
+      const size_t smem = (size_t)4 * ((size_t)l1 * lg + 32);  // the table slice and its zero pad
+      auto kern = k_sketch_csr_direct<TV>;
+      if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
+      const int64_t per_group = min64(cdiv(cr.n_light, kDirWarps), max64(1, cdiv((int64_t)num_sms, G)));
+      kern<<<dim3((unsigned)per_group, (unsigned)G), kDirWarps * 32, smem, st>>>(
+          rowptr, colind, val, n, cr.light, cr.d_count, cr.direct_max, l1, l, lg, table, ws.hs, Y, status);
+      RLU_CUDA_TRY(cudaGetLastError());
+      note_launch();
+    }
+  }
+  if (cr.n_mid > 0) {
     auto kern = k_sketch_csr_light<TV, TACC>;
     const size_t fixed = (size_t)l1 * sizeof(V) + (size_t)kCsrWarps * l1 * sizeof(TACC);
     const size_t per_pair = (size_t)2 * l1 * sizeof(V);
@@ -1266,9 +1437,9 @@ static int launch_csr_cfg(const int64_t* rowptr, const int32_t* colind, const TV
     if (pb > kCsrWarps / 2) pb = kCsrWarps / 2;
     const size_t smem = fixed + (size_t)pb * per_pair;
     if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
-    const int64_t groups = cdiv(cr.n_light, kCsrWarps);
+    const int64_t groups = cdiv(cr.n_mid, kCsrWarps);
     const unsigned grid = (unsigned)min64(groups, (int64_t)num_sms);
-    kern<<<grid, kCsrWarps * 32, smem, st>>>(rowptr, colind, val, n, cr.light, cr.d_count, l1, l, ws.hs, ws.dsign,
+    kern<<<grid, kCsrWarps * 32, smem, st>>>(rowptr, colind, val, n, cr.mid, cr.d_count + 2, l1, l, ws.hs, ws.dsign,
                                              ws.R, tw, ws.plan, pb, Y, status);
     RLU_CUDA_TRY(cudaGetLastError());
     note_launch();
@@ -1287,14 +1458,14 @@ static int launch_csr_cfg(const int64_t* rowptr, const int32_t* colind, const TV
 }
 
 int launch_sketch_csr(const int64_t* rowptr, const int32_t* colind, const void* val, int dtype, int64_t n,
-                      const CsrRows& cr, int l1, int l, const SketchWs& ws, void* D, double* Y, unsigned int* status,
-                      int num_sms, cudaStream_t st) {
+                      const CsrRows& cr, int l1, int l, const SketchWs& ws, void* D, double* Y, float* table,
+                      unsigned int* status, int num_sms, cudaStream_t st) {
   if (dtype == RLU_F64)
     return launch_csr_cfg<double, double>(rowptr, colind, (const double*)val, n, cr, l1, l, ws, (double*)D, Y,
-                                          status, num_sms, st);
+                                          table, status, num_sms, st);
   if (dtype == RLU_F32)
-    return launch_csr_cfg<float, float>(rowptr, colind, (const float*)val, n, cr, l1, l, ws, (float*)D, Y, status,
-                                        num_sms, st);
+    return launch_csr_cfg<float, float>(rowptr, colind, (const float*)val, n, cr, l1, l, ws, (float*)D, Y, table,
+                                        status, num_sms, st);
   return RLU_EINVAL;
 }
 
@@ -1339,19 +1510,30 @@ int launch_sketch_params(const SketchWs& ws, int64_t n, int l1, int l, uint64_t 
   }
   RLU_CUDA_TRY(cudaMemsetAsync(ws.bcnt, 0, sizeof(int32_t) * (nsb + 1), st));
   k_bucket_count<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, l1, ws.chunk, ws.hs, ws.bcnt);
-  k_scan_counts<<<1, 1024, 0, st>>>(nsb, ws.bcnt, ws.bstart);
+  note_launch();
+  if (int rc_ = launch_scan_i32(nsb, ws.bcnt, ws.bstart, ws.scan_tmp, st)) return rc_;
   RLU_CUDA_TRY(cudaMemsetAsync(ws.bcnt, 0, sizeof(int32_t) * (nsb + 1), st));
   k_bucket_fill<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, l1, ws.chunk, ws.hs, ws.bstart, ws.bcnt, ws.blist);
   k_bucket_sort<<<(unsigned)cdiv(nsb, 256), 256, 0, st>>>(nsb, ws.bstart, ws.blist);
   RLU_CUDA_TRY(cudaGetLastError());
-  note_launch(6);
+  note_launch(4);
   return RLU_OK;
 }
 
-int launch_scan_i32(int64_t count, const int32_t* cnt, int32_t* start, cudaStream_t st) {
-  k_scan_counts<<<1, 1024, 0, st>>>(count, cnt, start);
+int launch_scan_i32(int64_t count, const int32_t* cnt, int32_t* start, int64_t* tmp, cudaStream_t st) {
+  if (!tmp) {  // no scratch (the allocation-free sketch): one CTA
+    k_scan_counts<<<1, 1024, 0, st>>>(count, cnt, start);
+    RLU_CUDA_TRY(cudaGetLastError());
+    note_launch();
+    return RLU_OK;
+  }
+  // at least 8 rounds of 1024 values per CTA, at most kScanMaxParts CTAs
+  const int64_t per = max64(8192, cdiv(cdiv(max64(count, 1), kScanMaxParts), 1024) * 1024);
+  const int64_t parts = max64(1, cdiv(count, per));
+  k_scan_part<<<(unsigned)parts, 1024, 0, st>>>(count, per, cnt, tmp);
+  k_scan_final<<<(unsigned)parts, 1024, 0, st>>>(count, per, cnt, tmp, start);
   RLU_CUDA_TRY(cudaGetLastError());
-  note_launch();
+  note_launch(2);
   return RLU_OK;
 }
 

@@ -101,6 +101,38 @@ def test_csr_f32_c2_shape(rg):
     print("csr c2 shape: e_gpu %.4e e_oracle %.4e; tau %s; max rel. differences %s" % (e_g, e_o, tau, done))
 
 
+def test_csr_f32_row_classes(rg):
+    """Every route of the CSR sketch in one matrix: rows of 8 entries (direct
+    evaluation against the projection's table), rows of 600 entries (more
+    than the direct bound 4 l1 (log2 l1 + 1) / l = 288 for l1 = 320, l = 40,
+    below n/4: the bucket sums and FFT), rows of 1200 entries (>= n/4:
+    densified).  Same bars as test_csr_f32_parity."""
+    rng = np.random.default_rng(21)
+    m, n, k, l, l1 = 2000, 4000, 30, 40, 320
+    counts = np.where(np.arange(m) % 10 == 3, 600, np.where(np.arange(m) % 50 == 7, 1200, 8))
+    indptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=indptr[1:])
+    cols = np.concatenate([np.sort(rng.choice(n, size=c, replace=False)) for c in counts]).astype(np.int32)
+    U = rng.standard_normal((m, 8))
+    V = rng.standard_normal((8, n))
+    rows = np.repeat(np.arange(m), counts)
+    vals = (np.einsum("ij,ji->i", U[rows], V[:, cols]) + 0.01 * rng.standard_normal(len(cols))).astype(np.float32)
+    As = scipy.sparse.csr_matrix((vals, cols, indptr), shape=(m, n))
+    o = oracle.factor(As, k, l, l1, seed=8)
+    g = run_csr(rg, As, k, l, l1, 8, "f32", debug=True)
+    assert g["status"] == 0, rg.strerror(g["status"])
+    check_structure(g, m, n, k)
+    check_pivots(g, o, k)
+    rown = np.sqrt(np.asarray(As.multiply(As).sum(axis=1)).ravel())
+    # row by row against the row's own norm: each route is checked on its rows
+    assert np.all(np.abs(g["Y"] - o.Y).max(axis=1) <= 5e-6 * rown + 1e-30)
+    e_o = oracle.relative_residual(As, o.L, o.U, o.p, o.q)
+    e_g = oracle.relative_residual(As, g["L"], g["U"], g["p"], g["q"])
+    assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
+    if e_o >= 1e-4:
+        assert abs(e_g / e_o - 1) <= 1e-2
+
+
 def test_csr_f64_parity(rg):
     As = sparse_case(2000, 1500, 10, 30, 5, seed=9, dtype=np.float64)
     o = oracle.factor(As, 25, 32, 256, seed=6)
