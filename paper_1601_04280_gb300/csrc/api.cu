@@ -425,6 +425,11 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   pa.G = h->G; pa.Rinv = h->Rinv; pa.Ginv = h->Ginv;
   pa.W = h->W; pa.w64 = f64 ? 1 : 0;
   pa.bar = h->bar2; pa.status = h->status_dev; pa.num_sms = h->num_sms; pa.coop_ctas = coop_sms(h);
+  // W and its BF16 planes from the tensor-core digit product (FP32 outputs)
+  const bool w_tc = !f64 && h->ltc.ready && h->tcw.ready;
+  pa.ltc = w_tc ? &h->ltc : nullptr;
+  pa.wplanes = w_tc ? h->tcw.wp : nullptr;
+  pa.ldw = h->tcw.plan.ldw;
   if (h->k2 > 0) {
     // steps 4-6 of Algorithm 1: B = (Omega_2 L_1)^+ Omega_2 P A (the timing stage
     // "gram" covers all of it; chol, wform and bgemm then read zero)
@@ -454,7 +459,7 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
     // B = W A: tensor cores (BF16 splits) when available, else SIMT
     if (!f64 && h->tcw.ready)
       rc = launch_bgemm_tc(h->tcw, reinterpret_cast<const float*>(h->W), A, lda, dtype, h->prec, m, n, k,
-                           reinterpret_cast<df32*>(h->B), h->status_dev, st);
+                           reinterpret_cast<df32*>(h->B), h->status_dev, st, w_tc);
     else
       rc = launch_bgemm_simt(h->W, f64 ? 1 : 0, A, lda, dtype, m, n, k, h->B, h->bpart, h->num_sms, st);
     if (rc) return rc;
@@ -529,6 +534,9 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   pa.G = h->G; pa.Rinv = h->Rinv; pa.Ginv = h->Ginv;
   pa.W = h->W; pa.w64 = f64 ? 1 : 0;
   pa.bar = h->bar2; pa.status = h->status_dev; pa.num_sms = h->num_sms; pa.coop_ctas = coop_sms(h);
+  pa.ltc = (!f64 && h->ltc.ready) ? &h->ltc : nullptr;  // W from the digit product; the CSR path splits its own planes
+  pa.wplanes = nullptr;
+  pa.ldw = 0;
   if ((rc = launch_gram(pa, st))) return rc;
   if ((rc = mark(h, 4, st))) return rc;
   if ((rc = launch_chol(pa, st))) return rc;
@@ -692,7 +700,7 @@ static int create_common(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1,
   h->sk.scan_tmp = (int64_t*)next();
   h->csr.scan_tmp = h->sk.scan_tmp;
   h->fjl_table = (float*)next();
-  if (tc_setup(h->tcw, tcbase, m, n, k, sms) != RLU_OK || ltc_setup(h->ltc, ltcbase, m, k) != RLU_OK) {
+  if (tc_setup(h->tcw, tcbase, m, n, k, sms) != RLU_OK || ltc_setup(h->ltc, ltcbase, m, k, sms) != RLU_OK) {
     rlu_destroy(h);
     return RLU_ECUDA;
   }

@@ -152,13 +152,15 @@ static int launch_cfg(const TcWs& w, int wplanes, const TA* A, int64_t lda, int6
 }
 
 int launch_bgemm_tc(const TcWs& w, const float* W, const void* A, int64_t lda, int dtype, int prec, int64_t m,
-                    int64_t n, int k, df32* B, unsigned int* status, cudaStream_t st) {
+                    int64_t n, int k, df32* B, unsigned int* status, cudaStream_t st, bool planes_ready) {
   if (!w.ready) return RLU_EINVAL;
   const TcPlan& p = w.plan;
-  const int64_t tot = (int64_t)k * p.ldw;
-  k_split_w_rows<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(m, k, p.ldw, W, w.wp[0], w.wp[1], w.wp[2]);
-  RLU_CUDA_TRY(cudaGetLastError());
-  note_launch();
+  if (!planes_ready) {
+    const int64_t tot = (int64_t)k * p.ldw;
+    k_split_w_rows<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(m, k, p.ldw, W, w.wp[0], w.wp[1], w.wp[2]);
+    RLU_CUDA_TRY(cudaGetLastError());
+    note_launch();
+  }
   int wplanes = 3;
   if (prec == RLU_PREC_BF16) wplanes = 1;
   if (prec == RLU_PREC_BF16_REFINE) wplanes = 2;

@@ -34,7 +34,8 @@ int tc_setup(TcWs& w, void* base, int64_t m, int64_t n, int k, int num_sms);
 // unavailable or the encoding is refused.
 int tc_encode_bf16_3d(void* map, void* base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t ld_elems,
                       uint32_t box_inner, uint32_t box_rows);
+// planes_ready: W's BF16 planes are already in w.wp (written with W).
 int launch_bgemm_tc(const TcWs& w, const float* W, const void* A, int64_t lda, int dtype, int prec, int64_t m,
-                    int64_t n, int k, df32* B, unsigned int* status, cudaStream_t st);
+                    int64_t n, int k, df32* B, unsigned int* status, cudaStream_t st, bool planes_ready = false);
 
 }  // namespace rlu

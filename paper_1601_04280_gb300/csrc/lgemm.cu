@@ -1,30 +1,35 @@
-// L = L_y L_b on the 5th-generation tensor cores (step 7 of Algorithm 1).
+// Exact digit products on the 5th-generation tensor cores:
+//   L = (P L_y) L_b          (step 7 of Algorithm 1), and
+//   W = G^{-1} L_y^T         (W = L_y^+ P of Corollary 3.3, with G = L_y^T L_y).
 //
-// An exact product of integer digits, in the manner of the error-free
-// splitting of Ozaki, Ogita, Oishi and Rump ("Error-free transformations of
-// matrix multiplication by using fast routines of matrix multiplication and
-// its applications", Numer. Algorithms 59, 2012), carried out with BF16
-// tensor-core products and FP32 accumulation:
+// An error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump
+// ("Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", Numer. Algorithms
+// 59, 2012), carried out with BF16 tensor-core products and FP32 accumulation:
 //
-//   * row i of P L_y is scaled by 2^-a_i and column c of L_b by 2^-b_c
-//     (powers of two: exact) into [-1, 1], and every scaled value x is cut
-//     into four signed digits, x = sum_s d_s 2^(-7 s) + r 2^-28 with
-//     |d_1| <= 128, |d_s| <= 64 for s > 1, |r| <= 1/2.  Digits are integers,
-//     exact in BF16, and a product of two digits is an integer below 2^14.
-//   * level v = s + t (2..5) collects the digit products d_s^A d_t^B; its
-//     sum over the k terms of the contraction stays below 2^24 for k <= 512,
-//     so the FP32 accumulation in tensor memory is exact.  One accumulator
-//     per level: 10 MMAs per 16-deep step.
+//   * every row of each operand is scaled by a power of two (exact) into
+//     [-1, 1], and every scaled value x is cut into D signed digits,
+//     x = sum_s d_s 2^(-7 s) + r 2^(-7 D), |d_1| <= 128, |d_s| <= 64 for s > 1,
+//     |r| <= 1/2.  Digits are integers, exact in BF16; a product of two
+//     digits is an integer below 2^14.
+//   * level v = s + t (2 .. D + 1) collects the products d_s^A d_t^B; its sum
+//     over a contraction of at most kLtcMaxK terms stays below 2^24, so the
+//     FP32 accumulation in tensor memory is exact.  One accumulator per level:
+//     D (D + 1) / 2 MMAs per 16-deep step.
 //   * the epilogue combines the levels, sum_v D_v 2^(-7 v), with TwoSum on
-//     the FP32 pipe, scales by 2^(a_i + b_c) and rounds once to FP32.
-// The only errors are the digits' truncation (2^-29 of the row and column
-// scales) and the dropped levels >= 6, both far below the FP32 rounding of L.
+//     the FP32 pipe, scales by the two powers of two and rounds once to FP32.
+// The errors are the digits' truncation (2^-(7 D + 1) of the row scales) and
+// the dropped levels > D + 1: 2^-29 with four digits (L), 2^-36 with five
+// (W, whose entries cancel by up to cond(L_y) against |G^{-1}| |L_y^T|).
 //
-// Kernel roles (192 threads): warp 0 issues the TMA loads of both digit
-// stacks (128-byte swizzle, K-major), warp 1 owns tensor memory and issues the
-// MMAs, warps 2..5 read the four TMEM lane quarters in the epilogue.  Every
-// mbarrier wait is bounded: on timeout the kernel raises FLAG_TIMEOUT, waits
-// for its own copies in flight, frees its tensor memory and returns.
+// The kernel is persistent: CTA b takes the tiles b, b + gridDim.x, ... (128
+// rows x ntile columns each, column tile fastest).  Warp 0 streams the digit
+// planes of both operands by TMA (128-byte swizzle, K-major) through a ring
+// that runs across tiles; warp 1 owns tensor memory and issues the MMAs into
+// one of two accumulator sets, so that warps 2..5 read the previous tile's
+// accumulators (their four TMEM lane quarters) while the next tile's MMAs
+// run.  Every wait is bounded: on timeout the kernel raises FLAG_TIMEOUT,
+// waits for its own copies in flight, frees its tensor memory and returns.
 #include <cuda.h>
 
 #include "bgemm.cuh"
@@ -34,21 +39,24 @@
 namespace rlu {
 namespace ltc {
 
-constexpr int kDig = 4;                    // digits per operand
-constexpr int kLev = 4;                    // levels 2..5
-constexpr int kBM = 128;                   // rows of L per CTA (MMA M)
+constexpr int kBM = 128;                   // rows per tile (MMA M)
 constexpr int kBK = 64;                    // contraction depth per stage (one swizzle atom of BF16)
-constexpr int kMaxN = 64;                  // columns of L per CTA
 constexpr int kStages = 2;
 constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 256;        // kLev x kMaxN
+constexpr uint32_t kTmemCols = 512;        // two accumulator sets of levels x ntile
 constexpr uint32_t kATile = kBM * kBK * 2;  // one digit plane of the A tile: 16 KB
 
 __host__ __device__ inline uint32_t b_tile_bytes(int ntile) { return (uint32_t)ntile * kBK * 2; }
+template <int D>
 __host__ __device__ inline uint32_t stage_bytes(int ntile) {
-  return (uint32_t)kDig * kATile + (uint32_t)kDig * b_tile_bytes(ntile);
+  return (uint32_t)D * (kATile + b_tile_bytes(ntile));
 }
-inline size_t smem_bytes(int ntile) { return (size_t)kStages * stage_bytes(ntile) + 1024; }
+template <int D>
+inline size_t smem_bytes(int ntile) {
+  return (size_t)kStages * stage_bytes<D>(ntile) + 1024;
+}
+
+enum { kEpiRows = 0, kEpiTransposed = 1 };
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
   asm volatile(
@@ -58,14 +66,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// Four digits of the float-float value (hi + lo) * 2^-e, |value| <= 1 (up to
+// D digits of the float-float value (hi + lo) * 2^-e, |value| <= 1 (up to
 // rounding of the scale choice): each step takes the nearest integer of the
 // leading part, keeps the exact remainder as a float-float pair, and moves up
 // by 2^7.  Every operation is exact in FP32.
-__device__ __forceinline__ void digits4(float hi, float lo, int e, __nv_bfloat16 (&d)[kDig]) {
+template <int D>
+__device__ __forceinline__ void digits(float hi, float lo, int e, __nv_bfloat16 (&d)[D]) {
   float yh = ldexpf(hi, 7 - e), yl = ldexpf(lo, 7 - e);
 #pragma unroll
-  for (int s = 0; s < kDig; ++s) {
+  for (int s = 0; s < D; ++s) {
     const float t = rintf(yh);
     d[s] = __float2bfloat16_rn(t);  // an integer of magnitude <= 128: exact
     const df32 r = two_sum(yh - t, yl);
@@ -81,40 +90,44 @@ __device__ __forceinline__ int scale_exp(float amax) {
   return e;
 }
 
-// Digit planes of P L_y: one warp per row i of L (row perm[i] of Lk).
-__global__ void k_digits_rows(int64_t m, int k, int64_t ldk, const df32* __restrict__ Lk,
-                              const int64_t* __restrict__ perm, __nv_bfloat16* __restrict__ adig,
-                              int32_t* __restrict__ aexp) {
+// Digit planes of the rows of a float-float matrix X (rows x k, row-major):
+// row i of the planes is row perm[i] of X (row i when perm is null), scaled
+// by 2^-exps[i].  One warp per row.
+template <int D>
+__global__ void k_digits_rows(int64_t rows, int k, int64_t ldk, const df32* __restrict__ X,
+                              const int64_t* __restrict__ perm, __nv_bfloat16* __restrict__ dig,
+                              int32_t* __restrict__ exps) {
   const int lane = threadIdx.x & 31;
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (i >= m) return;
-  const df32* src = Lk + perm[i] * k;
+  if (i >= rows) return;
+  const df32* src = X + (perm ? perm[i] : i) * k;
   float amax = 0.f;
   for (int t = lane; t < k; t += 32) amax = fmaxf(amax, fabsf(src[t].hi));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   const int e = scale_exp(amax);
-  if (lane == 0) aexp[i] = e;
-  const int64_t plane = m * ldk;
+  if (lane == 0) exps[i] = e;
+  const int64_t plane = rows * ldk;
   for (int t = lane; t < ldk; t += 32) {
-    __nv_bfloat16 d[kDig];
+    __nv_bfloat16 d[D];
     if (t < k) {
       const df32 v = src[t];
-      digits4(v.hi, v.lo, e, d);
+      digits<D>(v.hi, v.lo, e, d);
     } else {
 #pragma unroll
-      for (int s = 0; s < kDig; ++s) d[s] = __float2bfloat16_rn(0.f);
+      for (int s = 0; s < D; ++s) d[s] = __float2bfloat16_rn(0.f);
     }
 #pragma unroll
-    for (int s = 0; s < kDig; ++s) adig[s * plane + i * ldk + t] = d[s];
+    for (int s = 0; s < D; ++s) dig[s * plane + i * ldk + t] = d[s];
   }
 }
 
 // Digit planes of L_b^T: one warp per column c of L_b, L_b[t][c] = Bp[t][q[c]]
 // for t >= c, zero above the diagonal.
+template <int D>
 __global__ void k_digits_lb(int k, int64_t n, int64_t ldk, const df32* __restrict__ Bp,
-                            const int64_t* __restrict__ q, __nv_bfloat16* __restrict__ bdig,
-                            int32_t* __restrict__ bexp) {
+                            const int64_t* __restrict__ q, __nv_bfloat16* __restrict__ dig,
+                            int32_t* __restrict__ exps) {
   const int lane = threadIdx.x & 31;
   const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (c >= k) return;
@@ -124,49 +137,57 @@ __global__ void k_digits_lb(int k, int64_t n, int64_t ldk, const df32* __restric
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   const int e = scale_exp(amax);
-  if (lane == 0) bexp[c] = e;
+  if (lane == 0) exps[c] = e;
   const int64_t plane = (int64_t)k * ldk;
   for (int t = lane; t < ldk; t += 32) {
-    __nv_bfloat16 d[kDig];
+    __nv_bfloat16 d[D];
     if (t < k && t >= c) {
       const df32 v = Bp[(int64_t)t * n + col];
-      digits4(v.hi, v.lo, e, d);
+      digits<D>(v.hi, v.lo, e, d);
     } else {
 #pragma unroll
-      for (int s = 0; s < kDig; ++s) d[s] = __float2bfloat16_rn(0.f);
+      for (int s = 0; s < D; ++s) d[s] = __float2bfloat16_rn(0.f);
     }
 #pragma unroll
-    for (int s = 0; s < kDig; ++s) bdig[s * plane + (int64_t)c * ldk + t] = d[s];
+    for (int s = 0; s < D; ++s) dig[s * plane + (int64_t)c * ldk + t] = d[s];
   }
 }
 
-// One CTA per (128-row, ntile-column) tile of L; tiles ordered column tile
-// fastest, so the CTAs that share a row tile read it close together in time.
+struct EpiOut {
+  float* out;            // rows: out[row * ldo + col]; transposed: out[col * ldo + row]
+  int64_t ldo;
+  __nv_bfloat16* pl[3];  // transposed only (optional): BF16 planes of out, [col * ldp + row] for row < ldp
+  int64_t ldp;
+};
+
+// C (M x N) = A (M x K) B^T (N x K) from D digit planes of each operand.
+template <int D, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_l_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t m, int k,
-           int ntile, int nt, const int32_t* __restrict__ aexp, const int32_t* __restrict__ bexp,
-           float* __restrict__ L, unsigned int* status) {
+    k_digit_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t M,
+                 int N, int K, int ntile, int nt, int64_t tiles, const int32_t* __restrict__ aexp,
+                 const int32_t* __restrict__ bexp, EpiOut eo, unsigned int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accum_full;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
+  __shared__ volatile int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ni = (int)(blockIdx.x % nt);
-  const int64_t row0 = (int64_t)(blockIdx.x / nt) * kBM;
-  const int col0 = ni * ntile;
-  const int nkb = (k + kBK - 1) / kBK;
-  const uint32_t sb = stage_bytes(ntile), bt = b_tile_bytes(ntile);
+  const int nkb = (K + kBK - 1) / kBK;
+  const uint32_t sb = stage_bytes<D>(ntile), bt = b_tile_bytes(ntile);
+  const uint32_t set_cols = (uint32_t)(D * ntile);  // one accumulator set: D levels of ntile columns
   auto tileA = [&](int s, int d) { return smem + s * sb + d * kATile; };
-  auto tileB = [&](int s, int d) { return smem + s * sb + kDig * kATile + d * bt; };
+  auto tileB = [&](int s, int d) { return smem + s * sb + D * kATile + d * bt; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(&accum_full, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&tfull[b], 1);
+      tc::mbar_init(&tempty[b], 4);  // one arrival per epilogue warp
+    }
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -182,86 +203,109 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = tmem_base;
 
   if (warp == 0) {
-    // ---- TMA producer: the four digit planes of both operands per stage ----
+    // ---- TMA producer: D digit planes of both operands per stage ----
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % kStages;
-        if (kb >= kStages && !tc::mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) { s_fail = 1; break; }
-        if (s_fail) break;
-        tc::mbar_arrive_expect_tx(&full[s], kDig * (kATile + bt));
-        for (int d = 0; d < kDig; ++d) {
-          tma_load_3d(tileA(s, d), &mapA, &full[s], kb * kBK, (int)row0, d);
-          tma_load_3d(tileB(s, d), &mapB, &full[s], kb * kBK, col0, d);
-        }
-        issued = kb + 1;
-      }
-      // every issued load has landed before the CTA may exit
-      for (int kb = issued - kStages < 0 ? 0 : issued - kStages; kb < issued; ++kb)
-        if (!tc::mbar_wait(&full[kb % kStages], (kb / kStages) & 1)) s_fail = 1;
-    }
-  } else if (warp == 1) {
-    // ---- MMA issuer: level v = s + t accumulates in columns (v - 2) * ntile ----
-    if (lane == 0) {
-      const uint32_t idesc = tc::idesc_bf16(kBM, ntile);
-      bool ok = true;
-      for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int s = kb % kStages;
-        if (!tc::mbar_wait(&full[s], (kb / kStages) & 1)) { ok = false; break; }
-        tc::tc_fence_after();
-#pragma unroll
-        for (int kk = 0; kk < kBK / 16; ++kk) {
-          const uint32_t koff = kk * 32;  // 16 BF16 = 32 bytes along K inside the swizzle atom
-          const bool first = (kb == 0 && kk == 0);
-#pragma unroll
-          for (int v = 0; v < kLev; ++v) {
-            const uint32_t dcol = tmem + (uint32_t)(v * ntile);
-#pragma unroll
-            for (int da = 0; da <= v; ++da) {
-              const int db = v - da;  // digit indices (0-based) with da + db = v
-              const uint64_t aD = tc::sw128_desc(tc::smem_u32(tileA(s, da)) + koff);
-              const uint64_t bD = tc::sw128_desc(tc::smem_u32(tileB(s, db)) + koff);
-              tc::mma_bf16(dcol, aD, bD, idesc, (first && da == 0) ? 0u : 1u);
-            }
+      int64_t it = 0;
+      for (int64_t tile = blockIdx.x; tile < tiles && !s_fail; tile += gridDim.x) {
+        const int row0 = (int)((tile / nt) * kBM), col0 = (int)(tile % nt) * ntile;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % kStages);
+          if (it >= kStages && !tc::mbar_wait(&empty[s], (uint32_t)(((it / kStages) - 1) & 1))) {
+            s_fail = 1;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&full[s], D * (kATile + bt));
+          for (int d = 0; d < D; ++d) {
+            tma_load_3d(tileA(s, d), &mapA, &full[s], kb * kBK, row0, d);
+            tma_load_3d(tileB(s, d), &mapB, &full[s], kb * kBK, col0, d);
           }
         }
-        tc::mma_commit(&empty[s]);
+      }
+      // every issued load has landed before the CTA may exit
+      for (int64_t j = it - kStages < 0 ? 0 : it - kStages; j < it; ++j)
+        if (!tc::mbar_wait(&full[j % kStages], (uint32_t)((j / kStages) & 1))) s_fail = 1;
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer: level v (0-based) of set b in columns b * set_cols + v * ntile ----
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16(kBM, ntile);
+      int64_t it = 0, local = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++local) {
+        const int b = (int)(local & 1);
+        if (local >= 2 && !tc::mbar_wait(&tempty[b], (uint32_t)(((local >> 1) - 1) & 1))) { ok = false; break; }
+        tc::tc_fence_after();
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % kStages);
+          if (!tc::mbar_wait(&full[s], (uint32_t)((it / kStages) & 1))) { ok = false; break; }
+          tc::tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint32_t koff = kk * 32;  // 16 BF16 = 32 bytes along K inside the swizzle atom
+            const bool first = (kb == 0 && kk == 0);
+#pragma unroll
+            for (int v = 0; v < D; ++v) {
+              const uint32_t dcol = tmem + (uint32_t)b * set_cols + (uint32_t)(v * ntile);
+#pragma unroll
+              for (int da = 0; da <= v; ++da) {
+                const uint64_t aD = tc::sw128_desc(tc::smem_u32(tileA(s, da)) + koff);
+                const uint64_t bD = tc::sw128_desc(tc::smem_u32(tileB(s, v - da)) + koff);
+                tc::mma_bf16(dcol, aD, bD, idesc, (first && da == 0) ? 0u : 1u);
+              }
+            }
+          }
+          tc::mma_commit(&empty[s]);
+        }
+        if (ok) tc::mma_commit(&tfull[b]);
       }
       if (!ok) s_fail = 1;
-      tc::mma_commit(&accum_full);
     }
   } else {
     // ---- epilogue (warps 2..5): TMEM lane quarter = warp mod 4 ----
-    const bool ok = tc::mbar_wait(&accum_full, 0);
-    tc::tc_fence_after();
-    if (!ok) {
-      s_fail = 1;
-    } else if (!s_fail) {
-      const int quarter = warp & 3;
-      const int64_t row = row0 + quarter * 32 + lane;
-      const int ea = row < m ? aexp[row] : 0;
-      const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int quarter = warp & 3;
+    int64_t local = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
+      const int b = (int)(local & 1);
+      if (!tc::mbar_wait(&tfull[b], (uint32_t)((local >> 1) & 1))) { s_fail = 1; break; }
+      tc::tc_fence_after();
+      const int64_t row = (tile / nt) * kBM + quarter * 32 + lane;
+      const int col0 = (int)(tile % nt) * ntile;
+      const int ea = row < M ? aexp[row] : 0;
+      const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * set_cols;
       for (int c0 = 0; c0 < ntile; c0 += 16) {
-        float v0[16], v1[16], v2[16], v3[16];
-        tc::tmem_ld16(tq + (uint32_t)(0 * ntile + c0), v0);
-        tc::tmem_ld16(tq + (uint32_t)(1 * ntile + c0), v1);
-        tc::tmem_ld16(tq + (uint32_t)(2 * ntile + c0), v2);
-        tc::tmem_ld16(tq + (uint32_t)(3 * ntile + c0), v3);
-        if (row < m) {
+        float v[D][16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int c = col0 + c0 + i;
-            if (c < k) {
-              // D_v are integers below 2^24: their scaled values are exact,
-              // TwoSum keeps the two leading levels exact, the two small ones
-              // enter the correction
-              const df32 sum = two_sum(v0[i] * 0x1p-14f, v1[i] * 0x1p-21f);
-              const float corr = sum.lo + (v2[i] * 0x1p-28f + v3[i] * 0x1p-35f);
-              L[row * k + c] = ldexpf(sum.hi + corr, ea + bexp[c]);
+        for (int lv = 0; lv < D; ++lv) tc::tmem_ld16(tq + (uint32_t)(lv * ntile + c0), v[lv]);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int c = col0 + c0 + i;
+          if (c >= N) continue;
+          // level sums are integers below 2^24: scaled, they are exact; TwoSum
+          // keeps the two leading levels exact, the others enter the correction
+          const df32 sum = two_sum(v[0][i] * 0x1p-14f, v[1][i] * 0x1p-21f);
+          float corr = 0.f;
+#pragma unroll
+          for (int lv = D - 1; lv >= 2; --lv) corr += v[lv][i] * ldexpf(1.f, -7 * (lv + 2));
+          const float r = (row < M) ? ldexpf(sum.hi + (sum.lo + corr), ea + bexp[c]) : 0.f;
+          if (EPI == kEpiRows) {
+            if (row < M) eo.out[row * eo.ldo + c] = r;
+          } else {
+            if (row < M) eo.out[(int64_t)c * eo.ldo + row] = r;
+            if (eo.pl[0] && row < eo.ldp) {
+              const __nv_bfloat16 h1 = __float2bfloat16_rn(r);
+              const float r1 = r - __bfloat162float(h1);
+              const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
+              const int64_t o = (int64_t)c * eo.ldp + row;
+              eo.pl[0][o] = h1;
+              eo.pl[1][o] = h2;
+              eo.pl[2][o] = __float2bfloat16_rn(r1 - __bfloat162float(h2));
             }
           }
         }
       }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[b]);
     }
   }
   tc::tc_fence_before();
@@ -273,68 +317,115 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0 && s_fail) set_flag(status, FLAG_TIMEOUT);
 }
 
+// Columns per tile for N output columns: equal tiles, multiples of 16, at
+// most 512 / (2 D) columns (two accumulator sets of D levels in TMEM).
+inline int tile_cols(int N, int D) {
+  const int maxn = (512 / (2 * D)) / 16 * 16;
+  const int nt = (int)cdiv(N, maxn);
+  return (int)cdiv(cdiv(N, nt), 16) * 16;
+}
+
+template <int D, int EPI>
+int launch_gemm(const void* mapA, const void* mapB, int64_t M, int N, int K, int ntile, const int32_t* aexp,
+                const int32_t* bexp, const EpiOut& eo, unsigned int* status, int num_sms, cudaStream_t st) {
+  const size_t smem = smem_bytes<D>(ntile);
+  auto kern = k_digit_gemm<D, EPI>;
+  if (int rc = allow_dynamic_smem((const void*)kern, smem)) return rc;
+  const int nt = (int)cdiv(N, ntile);
+  const int64_t tiles = cdiv(M, kBM) * nt;
+  const unsigned grid = (unsigned)min64(tiles, (int64_t)num_sms);
+  kern<<<grid, kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap*>(mapA),
+                                     *reinterpret_cast<const CUtensorMap*>(mapB), M, N, K, ntile, nt, tiles, aexp,
+                                     bexp, eo, status);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return RLU_OK;
+}
+
 }  // namespace ltc
 
 namespace {
 constexpr size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 int64_t ltc_ldk(int k) { return cdiv(k, 8) * 8; }
+constexpr int kDigL = 4;  // digits of the L product
+constexpr int kDigW = 5;  // digits of the W product
 }  // namespace
 
 size_t ltc_workspace_bytes(int64_t m, int k) {
   const int64_t ldk = ltc_ldk(k);
-  return a256((size_t)ltc::kDig * m * ldk * 2) + a256((size_t)ltc::kDig * k * ldk * 2) + a256(4 * (size_t)m) +
+  return a256((size_t)kDigW * m * ldk * 2) + a256((size_t)kDigW * k * ldk * 2) + a256(4 * (size_t)m) +
          a256(4 * (size_t)k);
 }
 
-int ltc_setup(LtcWs& w, void* base, int64_t m, int k) {
+int ltc_setup(LtcWs& w, void* base, int64_t m, int k, int num_sms) {
   w.ready = false;
   w.m = m;
   w.k = k;
+  w.num_sms = num_sms;
   w.ldk = ltc_ldk(k);
   unsigned char* b = (unsigned char*)base;
   w.adig = (__nv_bfloat16*)b;
-  b += a256((size_t)ltc::kDig * m * w.ldk * 2);
+  b += a256((size_t)kDigW * m * w.ldk * 2);
   w.bdig = (__nv_bfloat16*)b;
-  b += a256((size_t)ltc::kDig * k * w.ldk * 2);
+  b += a256((size_t)kDigW * k * w.ldk * 2);
   w.aexp = (int32_t*)b;
   b += a256(4 * (size_t)m);
   w.bexp = (int32_t*)b;
-  // columns per CTA: k split into equal tiles of at most 64, each a multiple of 16
-  const int nt = (int)cdiv(k, ltc::kMaxN);
-  w.ntile = (int)cdiv(cdiv(k, nt), 16) * 16;
+  w.ntileL = ltc::tile_cols(k, kDigL);
+  w.ntileW = ltc::tile_cols(k, kDigW);
   if (k > kLtcMaxK) return RLU_OK;
-  if (tc_encode_bf16_3d(w.mapA, w.adig, (uint64_t)w.ldk, (uint64_t)m, ltc::kDig, (uint64_t)w.ldk, ltc::kBK,
-                        ltc::kBM) != RLU_OK ||
-      tc_encode_bf16_3d(w.mapB, w.bdig, (uint64_t)w.ldk, (uint64_t)k, ltc::kDig, (uint64_t)w.ldk, ltc::kBK,
-                        (uint32_t)w.ntile) != RLU_OK) {
+  // the same planes serve both products: four of them for L, five for W
+  const uint64_t ldk = (uint64_t)w.ldk;
+  if (tc_encode_bf16_3d(w.mapAL, w.adig, ldk, (uint64_t)m, kDigL, ldk, ltc::kBK, ltc::kBM) != RLU_OK ||
+      tc_encode_bf16_3d(w.mapBL, w.bdig, ldk, (uint64_t)k, kDigL, ldk, ltc::kBK, (uint32_t)w.ntileL) != RLU_OK ||
+      tc_encode_bf16_3d(w.mapAW, w.adig, ldk, (uint64_t)m, kDigW, ldk, ltc::kBK, ltc::kBM) != RLU_OK ||
+      tc_encode_bf16_3d(w.mapBW, w.bdig, ldk, (uint64_t)k, kDigW, ldk, ltc::kBK, (uint32_t)w.ntileW) != RLU_OK) {
     cudaGetLastError();
-    return RLU_OK;  // no tensor maps: the caller keeps the SIMT product
+    return RLU_OK;  // no tensor maps: the callers keep the SIMT products
   }
   w.ready = true;
   return RLU_OK;
 }
 
-template <>
-int launch_l_tc<df32>(const LtcWs& w, const df32* Lk, const int64_t* perm_y, const df32* Bp, const int64_t* perm_b,
-                      int64_t n, float* L, unsigned int* status, cudaStream_t st) {
+int launch_l_tc(const LtcWs& w, const df32* Lk, const int64_t* perm_y, const df32* Bp, const int64_t* perm_b,
+                int64_t n, float* L, unsigned int* status, cudaStream_t st) {
   if (!w.ready) return RLU_EINVAL;
   const int64_t m = w.m;
   const int k = w.k;
-  ltc::k_digits_rows<<<(unsigned)cdiv(m * 32, 256), 256, 0, st>>>(m, k, w.ldk, Lk, perm_y, w.adig, w.aexp);
+  ltc::k_digits_rows<kDigL><<<(unsigned)cdiv(m * 32, 256), 256, 0, st>>>(m, k, w.ldk, Lk, perm_y, w.adig, w.aexp);
   RLU_CUDA_TRY(cudaGetLastError());
-  ltc::k_digits_lb<<<(unsigned)cdiv((int64_t)k * 32, 256), 256, 0, st>>>(k, n, w.ldk, Bp, perm_b, w.bdig, w.bexp);
+  ltc::k_digits_lb<kDigL><<<(unsigned)cdiv((int64_t)k * 32, 256), 256, 0, st>>>(k, n, w.ldk, Bp, perm_b, w.bdig,
+                                                                                 w.bexp);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch(2);
-  const size_t smem = ltc::smem_bytes(w.ntile);
-  if (int rc = allow_dynamic_smem((const void*)ltc::k_l_tc, smem)) return rc;
-  const int nt = (int)cdiv(k, w.ntile);
-  const int64_t tiles = cdiv(m, ltc::kBM) * nt;
-  ltc::k_l_tc<<<(unsigned)tiles, ltc::kThreads, smem, st>>>(
-      *reinterpret_cast<const CUtensorMap*>(w.mapA), *reinterpret_cast<const CUtensorMap*>(w.mapB), m, k, w.ntile,
-      nt, w.aexp, w.bexp, L, status);
+  ltc::EpiOut eo{};
+  eo.out = L;
+  eo.ldo = k;
+  return ltc::launch_gemm<kDigL, ltc::kEpiRows>(w.mapAL, w.mapBL, m, k, k, w.ntileL, w.aexp, w.bexp, eo, status,
+                                                w.num_sms, st);
+}
+
+int launch_w_tc(const LtcWs& w, const df32* Ginv, const df32* Lk, float* W, __nv_bfloat16* const* planes,
+                int64_t ldp, unsigned int* status, cudaStream_t st) {
+  if (!w.ready) return RLU_EINVAL;
+  const int64_t m = w.m;
+  const int k = w.k;
+  // W^T (m x k) = Lk G^{-T} = Lk G^{-1} (G symmetric): rows of Lk against rows of G^{-1}
+  ltc::k_digits_rows<kDigW><<<(unsigned)cdiv(m * 32, 256), 256, 0, st>>>(m, k, w.ldk, Lk, nullptr, w.adig, w.aexp);
   RLU_CUDA_TRY(cudaGetLastError());
-  note_launch();
-  return RLU_OK;
+  ltc::k_digits_rows<kDigW><<<(unsigned)cdiv((int64_t)k * 32, 256), 256, 0, st>>>(k, k, w.ldk, Ginv, nullptr,
+                                                                                  w.bdig, w.bexp);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch(2);
+  ltc::EpiOut eo{};
+  eo.out = W;
+  eo.ldo = m;
+  if (planes) {
+    for (int q = 0; q < 3; ++q) eo.pl[q] = planes[q];
+    eo.ldp = ldp;
+  }
+  return ltc::launch_gemm<kDigW, ltc::kEpiTransposed>(w.mapAW, w.mapBW, m, k, k, w.ntileW, w.aexp, w.bexp, eo,
+                                                      status, w.num_sms, st);
 }
 
 }  // namespace rlu

@@ -397,6 +397,12 @@ int launch_wform(const PinvArgs& a, cudaStream_t st) {
   k_sum_slices_df<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>((int64_t)k * k, S, a.gram_part, Ginv);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
+  // W = G^{-1} Lk^T: an exact five-digit product on the tensor cores (which
+  // also writes W's BF16 planes for the tensor-core B when given them), else
+  // float-float on the SIMT pipes
+  if (a.ltc && a.ltc->ready)
+    return launch_w_tc(*a.ltc, Ginv, reinterpret_cast<const df32*>(a.Lk), reinterpret_cast<float*>(a.W), a.wplanes,
+                       a.ldw, a.status, st);
   return gemm_simt<df32, df32, float, df32>(st, k, m, k, Ginv, k, 1, reinterpret_cast<const df32*>(a.Lk), 1, k,
                                             reinterpret_cast<float*>(a.W), m, 1);
 }
@@ -535,8 +541,8 @@ int launch_assemble(const AssembleArgs& a, cudaStream_t st) {
   int rc;
   if constexpr (std::is_same<T, df32>::value && std::is_same<TO, float>::value) {
     if (tc_digits) {
-      rc = launch_l_tc<df32>(*a.ltc, reinterpret_cast<const df32*>(a.Lk), a.perm_y, Bp, a.perm_b, n,
-                             reinterpret_cast<float*>(a.L), a.status, st);
+      rc = launch_l_tc(*a.ltc, reinterpret_cast<const df32*>(a.Lk), a.perm_y, Bp, a.perm_b, n,
+                       reinterpret_cast<float*>(a.L), a.status, st);
       if (rc) return rc;
       RLU_CUDA_TRY(cudaMemcpyAsync(a.p, a.perm_y, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
       RLU_CUDA_TRY(cudaMemcpyAsync(a.q, a.perm_b, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, st));

@@ -25,6 +25,9 @@ struct PinvArgs {
   unsigned int* status;
   int num_sms;
   int coop_ctas;  // CTAs of the grid-synchronised Cholesky kernel (<= num_sms)
+  const LtcWs* ltc;              // exact digit products on the tensor cores (or null)
+  __nv_bfloat16* const* wplanes;  // with ltc: also write W's BF16 planes here (3 x k x ldw), or null
+  int64_t ldw;
 };
 
 struct AssembleArgs {
