@@ -21,12 +21,15 @@ struct LtcWs {
   int64_t m;
   int k;
   int64_t ldk;          // row stride of the planes (k rounded up to 8)
+  int64_t ldm;          // row stride of the transposed planes of the Gram product (m rounded up to 8)
   int ntileL, ntileW;   // columns per tile of the L and W products (multiples of 16)
   int num_sms;
   alignas(64) unsigned char mapAL[128];
   alignas(64) unsigned char mapBL[128];
   alignas(64) unsigned char mapAW[128];
   alignas(64) unsigned char mapBW[128];
+  alignas(64) unsigned char mapAG[128];
+  alignas(64) unsigned char mapBG[128];
   bool ready;
 };
 
@@ -43,6 +46,12 @@ int ltc_setup(LtcWs& w, void* base, int64_t m, int k, int num_sms);
 // Lk[perm_y[i]] and L_b[t][c] = Bp[t][perm_b[c]] for t >= c (packed LU of B).
 int launch_l_tc(const LtcWs& w, const df32* Lk, const int64_t* perm_y, const df32* Bp, const int64_t* perm_b,
                 int64_t n, float* L, unsigned int* status, cudaStream_t st);
+
+// G = Lk^T Lk (k x k) as six-digit products of Lk^T's digit planes, split
+// over the m rows: FP64 partials part[s][c][c'] for s < *splits (at most
+// max_splits); their sum is G.
+int launch_gram_tc(const LtcWs& w, const df32* Lk, double* part, int max_splits, int* splits, unsigned int* status,
+                   cudaStream_t st);
 
 // W (k x m, row-major FP32) = G^{-1} Lk^T with G^{-1} (k x k) and Lk (m x k)
 // in float-float; with `planes` (three k x ldp BF16 arrays) also W's split

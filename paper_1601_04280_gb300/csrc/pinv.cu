@@ -327,6 +327,16 @@ int launch_gram(const PinvArgs& a, cudaStream_t st) {
     k_extract_Lk<df32><<<(unsigned)cdiv(m * k, 256), 256, 0, st>>>(m, l, k, a.Y, a.pstep, Lk);
     RLU_CUDA_TRY(cudaGetLastError());
     note_launch();
+    if (a.ltc && a.ltc->ready) {
+      // six-digit products on the tensor cores, FP64 partials per split of the rows
+      int Sg = 0;
+      if ((rc = launch_gram_tc(*a.ltc, Lk, a.gram_part, a.max_gram_splits, &Sg, a.status, st))) return rc;
+      k_sum_slices<double><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>((int64_t)k * k, Sg, a.gram_part,
+                                                                                a.G);
+      RLU_CUDA_TRY(cudaGetLastError());
+      note_launch();
+      return RLU_OK;
+    }
     // G is symmetric: only the tiles on and above the diagonal are computed
     rc = gemm_simt<df32, df32, double, df32>(st, k, k, m, Lk, 1, k, Lk, k, 1, a.gram_part, k, 1, S,
                                              (int64_t)k * k, 1);
