@@ -9,5 +9,6 @@ from .rlu import (KEY_TAG, STATUS_OK, STATUS_WRANK, SketchParams, LUResult,
                   pinv_householder, factor, relative_residual, check_sizes,
                   second_projection, factor_two_sketch,
                   bucket_of_word, sign_of_word, phase_of_word,
-                  TRANSFORMS, hadamard_columns, srft_columns, transform_matrix)
+                  TRANSFORMS, hadamard_columns, srft_columns, transform_matrix,
+                  column_order_greedy)
 from .philox import philox4x64_10, mulhilo64, stream_blocks

@@ -320,6 +320,7 @@ class OracleResult:
     top_b: np.ndarray = None  # (k, 2)
     Y2: np.ndarray = None     # k2 x n, Omega_2 P A (second projection only)
     Z: np.ndarray = None      # k2 x k, Omega_2 L_y (second projection only)
+    ycols: np.ndarray = None  # (l,) column order of the sketch (column pivoting; identity otherwise)
 
 
 def check_sizes(m, n, k, l, l1):
@@ -329,9 +330,38 @@ def check_sizes(m, n, k, l, l1):
         raise ValueError("need l <= m and k <= min(m, n)")
 
 
-def factor(A, k, l, l1, seed, transform="hartley"):
+def column_order_greedy(Y):
+    """Column order of Y by QR with column pivoting (Businger and Golub): at
+    each step the column with the largest norm after removing the span of the
+    columns already chosen; ties to the smallest index (LAPACK geqp3).
+    Written as the greedy pivoted Cholesky of Y^T Y, which makes the same
+    choices in exact arithmetic: the diagonal of the Schur complement holds
+    the squared residual norms."""
+    G = np.array(Y.T @ Y, dtype=np.float64)
+    l = G.shape[0]
+    order = np.arange(l)
+    for j in range(l):
+        d = np.diag(G)[j:]
+        c = j + int(np.argmax(d))
+        if c != j:
+            G[[j, c], :] = G[[c, j], :]
+            G[:, [j, c]] = G[:, [c, j]]
+            order[[j, c]] = order[[c, j]]
+        piv = G[j, j]
+        if piv <= 0.0:
+            break  # the remaining columns lie in the span of the chosen ones
+        r = G[j, j + 1:] / np.sqrt(piv)
+        G[j + 1:, j + 1:] -= np.outer(r, r)
+        G[j + 1:, j] = G[j, j + 1:] = 0.0
+    return order
+
+
+def factor(A, k, l, l1, seed, transform="hartley", column_pivoting=False):
     """Sparse randomized LU of A (dense ndarray or scipy.sparse), all FP64.
-    `transform` selects step 2's FFT-based projection (transform_matrix)."""
+    `transform` selects step 2's FFT-based projection (transform_matrix).
+    `column_pivoting` orders the sketch's columns by QR with column pivoting
+    before the panel LU (a rank-revealing choice of the k columns that span
+    L_y, beyond Algorithm 1): Y := Y[:, column_order_greedy(Y)]."""
     m, n = A.shape
     check_sizes(m, n, k, l, l1)
     status = STATUS_OK
@@ -339,6 +369,10 @@ def factor(A, k, l, l1, seed, transform="hartley"):
     params = sketch_params(n, l1, l, seed)
     # step 2
     Y = fjl(countsketch(A, params, l1), params, l1, transform)
+    ycols = np.arange(l)
+    if column_pivoting:
+        ycols = column_order_greedy(Y)
+        Y = Y[:, ycols]
     # step 3: l elimination steps on the m x l sketch, then truncate to k
     ly = lu_partial_pivot(Y, steps=l)
     if ly.zero_pivot:
@@ -365,7 +399,7 @@ def factor(A, k, l, l1, seed, transform="hartley"):
     L = Ly @ Lb
     return OracleResult(L=L, U=Ub, p=p, q=q, status=status, params=params,
                         Y=Y, Ly=Ly, W=W, B=B, Lb=Lb, Ub=Ub,
-                        gaps_y=ly.gaps, gaps_b=lb.gaps, top_y=ly.top, top_b=lb.top)
+                        gaps_y=ly.gaps, gaps_b=lb.gaps, top_y=ly.top, top_b=lb.top, ycols=ycols)
 
 
 def second_projection(M, params2, l2):
