@@ -165,6 +165,18 @@ int rlu_set_transform(rlu_t h, int transform);
  * Errors: RLU_EINVAL, RLU_ENOMEM, RLU_ECUDA. */
 int rlu_set_second_sketch(rlu_t h, int32_t k2, int32_t l2, uint64_t seed2);
 
+/* Order the sketch's columns before the panel LU (on = 1) by QR with column
+ * pivoting: at each step the column with the largest norm after removing the
+ * span of the columns already chosen (Businger and Golub; computed as the
+ * greedy pivoted Cholesky of Y^T Y with float-float arithmetic), so that L_y
+ * spans the k most independent of the l sketch columns.  A rank-revealing
+ * choice beyond Algorithm 1, whose panel LU takes the columns as they come;
+ * it lets the oversampling l - k lower the error.  Off by default.  The first
+ * call that turns it on allocates the Gram matrix, its split partials and a
+ * copy of Y (m x l) and waits for the device.  rlu_debug_Y then returns the
+ * reordered sketch.  Errors: RLU_EINVAL, RLU_ENOMEM, RLU_ECUDA. */
+int rlu_set_column_pivoting(rlu_t h, int on);
+
 /* Bound the CTAs of the two grid-synchronised kernels of handle h (the
  * pivoted LUs of steps 3 and 6, the Cholesky factor of G) to max_ctas; 0 (the
  * default) gives one CTA per SM.  Results do not depend on it (each kernel's

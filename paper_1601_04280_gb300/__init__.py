@@ -33,7 +33,7 @@ C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_
              "rlu_csr_workspace_bytes", "rlu_set_csr_workspace", "rlu_graph_capture_dense", "rlu_graph_launch",
              "rlu_graph_destroy", "rlu_copy_block_async", "rlu_set_max_ctas",
              "rlu_debug_recip", "rlu_set_second_sketch", "rlu_debug_status_of_flags", "rlu_debug_wait_timeout",
-             "rlu_debug_alu_peak", "rlu_set_transform")
+             "rlu_debug_alu_peak", "rlu_set_transform", "rlu_set_column_pivoting")
 
 #: stage names reported by rlu_debug_stage_ms, in order
 STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
@@ -89,6 +89,7 @@ def load(reload=False):
         "rlu_debug_wait_timeout": ([c.c_int, c.POINTER(c.c_int)], c.c_int),
         "rlu_debug_alu_peak": ([c.c_int, c.POINTER(c.c_double)], c.c_int),
         "rlu_set_transform": ([vp, c.c_int], c.c_int),
+        "rlu_set_column_pivoting": ([vp, c.c_int], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -134,6 +135,10 @@ def rlu_set_precision(h, prec):
 
 def rlu_set_transform(h, transform):
     return _check(load().rlu_set_transform(h, TRANSFORM.get(transform, transform)), "rlu_set_transform")
+
+
+def rlu_set_column_pivoting(h, on):
+    return _check(load().rlu_set_column_pivoting(h, 1 if on else 0), "rlu_set_column_pivoting")
 
 
 def rlu_set_second_sketch(h, k2, l2, seed2):
@@ -287,6 +292,10 @@ class RandLU:
     def set_transform(self, transform):
         """The projection of step 2: "hartley" (default), "srht" or "srft"."""
         rlu_set_transform(self.h, transform)
+
+    def set_column_pivoting(self, on=True):
+        """Order the sketch's columns by QR with column pivoting before the panel LU."""
+        rlu_set_column_pivoting(self.h, on)
 
     def set_max_ctas(self, max_ctas):
         """Bound the CTAs of the grid-synchronised kernels (0: one per SM)."""

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "bgemm.cuh"
+#include "colpiv.cuh"
 #include "common.cuh"
 #include "csr.cuh"
 #include "pinv.cuh"
@@ -119,6 +120,9 @@ struct rlu_ctx {
   TcWs tcw{};
   LtcWs ltc{};  // digit planes of the tensor-core L = L_y L_b
   float* fjl_table = nullptr;  // l1 x l table of the CSR sketch's direct evaluation
+  int colpiv = 0;                 // rank-revealing column order of the sketch
+  void* cp_buf = nullptr;
+  int cp_splits = 0;
   int xform = RLU_XFORM_HARTLEY;  // projection of step 2
   void* xf_buf = nullptr;         // Y1 and the projection matrix (SRHT, SRFT), allocated on first use
   unsigned int* status_dev = nullptr;
@@ -410,6 +414,7 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   else
     rc = launch_sketch_dense(A, lda, dtype, f64, m, n, l1, l, h->sk, h->Y, h->status_dev, h->num_sms, st);
   if (rc) return rc;
+  if (h->colpiv && (rc = launch_column_pivoting(h->Y, m, l, h->cp_buf, h->cp_splits, h->num_sms, st))) return rc;
   if ((rc = mark(h, 2, st))) return rc;
   if (h->debug && h->Ydbg)
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Ydbg, h->Y, sizeof(double) * m * l, cudaMemcpyDeviceToDevice, st));
@@ -521,6 +526,7 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   if ((rc = launch_sketch_csr(rowptr, colind, val, dtype, n, cr, l1, l, h->sk, h->csr.D, h->Y, h->fjl_table,
                               h->status_dev, h->num_sms, st)))
     return rc;
+  if (h->colpiv && (rc = launch_column_pivoting(h->Y, m, l, h->cp_buf, h->cp_splits, h->num_sms, st))) return rc;
   if ((rc = mark(h, 2, st))) return rc;
   if (h->debug && h->Ydbg)
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Ydbg, h->Y, sizeof(double) * m * l, cudaMemcpyDeviceToDevice, st));
@@ -834,6 +840,22 @@ int rlu_set_precision(rlu_t h, int prec) {
   return RLU_OK;
 }
 
+int rlu_set_column_pivoting(rlu_t h, int on) {
+  if (!h) return RLU_EINVAL;
+  if (on && !h->cp_buf) {
+    const int splits = 4 * h->num_sms;
+    if (cudaMalloc(&h->cp_buf, colpiv_buffer_bytes(h->m, h->l, splits)) != cudaSuccess) {
+      cudaGetLastError();
+      h->cp_buf = nullptr;
+      return RLU_ENOMEM;
+    }
+    h->cp_splits = splits;
+    if (cudaDeviceSynchronize() != cudaSuccess) return RLU_ECUDA;
+  }
+  h->colpiv = on ? 1 : 0;
+  return RLU_OK;
+}
+
 int rlu_set_transform(rlu_t h, int transform) {
   if (!h) return RLU_EINVAL;
   if (transform == RLU_XFORM_SRHT && (h->l1 & (h->l1 - 1))) return RLU_EINVAL;
@@ -860,6 +882,7 @@ int rlu_destroy(rlu_t h) {
   if (h->sk2_buf) cudaFree(h->sk2_buf);
   if (h->at_buf) cudaFree(h->at_buf);
   if (h->xf_buf) cudaFree(h->xf_buf);
+  if (h->cp_buf) cudaFree(h->cp_buf);
   if (!h->csr_external) {
     if (h->csr_rows_buf) cudaFree(h->csr_rows_buf);
     if (h->csr_nnz_buf) cudaFree(h->csr_nnz_buf);
