@@ -29,13 +29,13 @@ void note_launch(int count) {
   t_launches += count;
 }
 
-// Page-locked host words (status and CSR counts, 4 per handle) for handles
+// Page-locked host words (status and CSR counts, 8 per handle) for handles
 // built on caller memory: one slab allocated on first use (never freed),
 // handed out from a free list.
 static std::mutex g_slab_mu;
 static unsigned int* g_slab = nullptr;
 static std::vector<unsigned int*> g_slab_free;
-constexpr int kSlabWords = 1 << 14;
+constexpr int kSlabWords = 1 << 15;  // 8 words per handle, 4096 handles
 
 unsigned int* status_slab_take() {
   std::lock_guard<std::mutex> lock(g_slab_mu);
@@ -47,12 +47,12 @@ unsigned int* status_slab_take() {
     }
     g_slab = (unsigned int*)p;
     g_slab_free.reserve(kSlabWords);
-    for (int i = kSlabWords / 4 - 1; i >= 0; --i) g_slab_free.push_back(g_slab + 4 * i);
+    for (int i = kSlabWords / 8 - 1; i >= 0; --i) g_slab_free.push_back(g_slab + 8 * i);
   }
   if (g_slab_free.empty()) return nullptr;
   unsigned int* w = g_slab_free.back();
   g_slab_free.pop_back();
-  w[0] = w[1] = w[2] = w[3] = 0;
+  for (int i = 0; i < 8; ++i) w[i] = 0;
   return w;
 }
 
@@ -127,7 +127,7 @@ struct rlu_ctx {
   void* xf_buf = nullptr;         // Y1 and the projection matrix (SRHT, SRFT), allocated on first use
   unsigned int* status_dev = nullptr;
   unsigned int* bar2 = nullptr;
-  // 4 page-locked host words: status (0) and the CSR row counts (1, 2, 3); own
+  // 8 page-locked host words: status (0) and the CSR counts (4..7); own
   // allocation when status_pinned, else a piece of the shared slab
   unsigned int* status_host = nullptr;
   bool status_pinned = false;
@@ -273,16 +273,22 @@ Sizes csr_rows_sizes(int64_t m, int64_t n, int k) {
   sz.add(sizeof(int32_t) * m);                                     // heavy
   sz.add(sizeof(int32_t) * m);                                     // light
   sz.add(sizeof(int32_t) * m);                                     // mid
-  sz.add(sizeof(int32_t) * 3);                                     // count
+  sz.add(sizeof(int32_t) * 4);                                     // count
   sz.add(sizeof(int32_t) * (n + 1));                               // ccnt
   sz.add(sizeof(int32_t) * (n + 1));                               // cstart
   sz.add((size_t)8 * m * k);                                       // W^T
+  sz.add(sizeof(int32_t) * (m + 1));                               // llen
+  sz.add(sizeof(int32_t) * (m + 1));                               // loff
+  sz.add(sizeof(int32_t) * (256 * kRadixMaxChunks + 1));           // rhist
+  sz.add(sizeof(int32_t) * (256 * kRadixMaxChunks + 1));           // roffs
   return sz;
 }
 
+// two slots of (column int32, row int32, value up to 8 bytes) per light entry
 size_t csr_entry_bytes(int64_t nnz) {
-  const size_t rb = ((sizeof(int32_t) * (size_t)max64(nnz, 1)) + 255) & ~(size_t)255;
-  return rb + (((size_t)8 * max64(nnz, 1) + 255) & ~(size_t)255);
+  const size_t e = (size_t)max64(nnz, 1);
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  return 2 * (up(4 * e) + up(4 * e) + up(8 * e));
 }
 
 size_t csr_heavy_bytes(int64_t nheavy, int64_t n, int k, int num_sms, size_t* dbytes, size_t* wbytes) {
@@ -314,12 +320,20 @@ void csr_carve_rows(rlu_ctx* h, char* b) {
   w.hpos = (int32_t*)next(); w.lpos = (int32_t*)next(); w.mpos = (int32_t*)next();
   w.heavy = (int32_t*)next(); w.light = (int32_t*)next(); w.mid = (int32_t*)next(); w.count = (int32_t*)next();
   w.ccnt = (int32_t*)next(); w.cstart = (int32_t*)next(); w.Wt = next();
+  w.llen = (int32_t*)next(); w.loff = (int32_t*)next(); w.rhist = (int32_t*)next(); w.roffs = (int32_t*)next();
 }
 
 void csr_carve_entries(rlu_ctx* h, char* b, int64_t nnz) {
-  const size_t rb = ((sizeof(int32_t) * (size_t)max64(nnz, 1)) + 255) & ~(size_t)255;
-  h->csr.crow = (int32_t*)b;
-  h->csr.cval = b + rb;
+  const size_t e = (size_t)max64(nnz, 1);
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  for (int s = 0; s < 2; ++s) {
+    h->csr.ekey[s] = (int32_t*)b;
+    b += up(4 * e);
+    h->csr.erow[s] = (int32_t*)b;
+    b += up(4 * e);
+    h->csr.eval[s] = b;
+    b += up(8 * e);
+  }
 }
 
 int csr_rows_alloc(rlu_ctx* h) {
@@ -518,9 +532,9 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   CsrRows cr{};
   const int64_t direct_max = f64 ? -1 : csr_direct_max(l1, l);  // FP64 sums keep the FFT route
   if ((rc = csr_classify(h->csr, rowptr, m, n, nnz, direct_max, h->status_dev, cr,
-                         reinterpret_cast<int32_t*>(h->status_host + 1), st)))
+                         reinterpret_cast<int32_t*>(h->status_host + 4), st)))
     return rc;
-  if ((rc = csr_grow(h, nnz, cr.n_heavy))) return rc;
+  if ((rc = csr_grow(h, cr.n_light_nnz, cr.n_heavy))) return rc;  // entry scratch for the light entries
   if ((rc = mark(h, 1, st))) return rc;
   RLU_CUDA_TRY(cudaMemsetAsync(h->Y, 0, sizeof(double) * m * l, st));
   if ((rc = launch_sketch_csr(rowptr, colind, val, dtype, n, cr, l1, l, h->sk, h->csr.D, h->Y, h->fjl_table,
@@ -711,7 +725,7 @@ static int create_common(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1,
     return RLU_ECUDA;
   }
   if (pinned) {
-    if (cudaMallocHost(&h->status_host, 4 * sizeof(unsigned int)) != cudaSuccess) {
+    if (cudaMallocHost(&h->status_host, 8 * sizeof(unsigned int)) != cudaSuccess) {
       cudaGetLastError();
       rlu_destroy(h);
       return RLU_ENOMEM;

@@ -40,8 +40,8 @@ __global__ void k_csr_classify(int64_t m, int64_t n, int64_t nnz, int64_t direct
 __global__ void k_csr_lists(int64_t m, const int32_t* __restrict__ hflag, const int32_t* __restrict__ lflag,
                             const int32_t* __restrict__ mflag, const int32_t* __restrict__ hpos,
                             const int32_t* __restrict__ lpos, const int32_t* __restrict__ mpos,
-                            int32_t* __restrict__ heavy, int32_t* __restrict__ light, int32_t* __restrict__ mid,
-                            int32_t* count) {
+                            const int32_t* __restrict__ loff, int32_t* __restrict__ heavy,
+                            int32_t* __restrict__ light, int32_t* __restrict__ mid, int32_t* count) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < m) {
     if (hflag[i]) heavy[hpos[i]] = (int32_t)i;
@@ -52,6 +52,7 @@ __global__ void k_csr_lists(int64_t m, const int32_t* __restrict__ hflag, const 
     count[0] = lpos[m];
     count[1] = hpos[m];
     count[2] = mpos[m];
+    count[3] = loff[m];  // light entries
   }
 }
 
@@ -70,96 +71,104 @@ __global__ void k_csc_count(const int64_t* __restrict__ rowptr, const int32_t* _
   }
 }
 
+// ---- light entries sorted by column (stable): CSC with rows ascending ----------
+// The light entries are laid out flat in row order (rows ascending, each row's
+// entries in CSR order), then sorted by column with a stable least-significant-
+// digit radix sort (8-bit digits): per chunk of entries a histogram of the
+// digit, an exclusive scan over (digit, chunk), and a scatter in which every
+// entry lands after all earlier entries of its digit.  Stability keeps each
+// column's entries in row order, so the column sums of the sparse product run
+// in a fixed order without a sort by row.
+
+// lens[i] = number of entries of row i if it is light, else 0
+__global__ void k_light_lens(int64_t m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ lflag,
+                             int32_t* __restrict__ lens) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) lens[i] = lflag[i] ? (int32_t)(rowptr[i + 1] - rowptr[i]) : 0;
+}
+
+// Flat arrays of the light entries: a warp per light row, at offset loff[row].
+// A column index outside [0, n) becomes n (sorted past every column, never read).
 template <typename TV>
-__global__ void k_csc_fill(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                           const TV* __restrict__ val, int64_t n, const int32_t* __restrict__ light, int64_t nlight,
-                           const int32_t* __restrict__ cstart, int32_t* __restrict__ ccur, int32_t* __restrict__ crow,
-                           TV* __restrict__ cval) {
+__global__ void k_light_expand(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                               const TV* __restrict__ val, int64_t n, const int32_t* __restrict__ light,
+                               const int32_t* __restrict__ count, const int32_t* __restrict__ loff,
+                               int32_t* __restrict__ key, int32_t* __restrict__ row, TV* __restrict__ v) {
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
+  const int64_t nlight = count[0];
   for (int64_t r = gw; r < nlight; r += nw) {
-    const int row = light[r];
-    for (int64_t e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
-      const int c = colind[e];
-      if (c >= 0 && (int64_t)c < n) {
-        const int p = cstart[c] + atomicAdd(&ccur[c], 1);
-        crow[p] = row;
-        cval[p] = val[e];
-      }
+    const int rw = light[r];
+    const int64_t s = rowptr[rw], len = rowptr[rw + 1] - s, o = loff[rw];
+    for (int64_t t = lane; t < len; t += 32) {
+      const int c = colind[s + t];
+      key[o + t] = (c >= 0 && (int64_t)c < n) ? c : (int32_t)n;
+      row[o + t] = rw;
+      v[o + t] = val[s + t];
     }
   }
 }
 
-// Sort each column's (row, value) entries by row (then by value bits, so that
-// duplicate coordinates also come out in a fixed order): a warp per column,
-// bitonic sort through shared memory for up to kSortMax entries, insertion
-// sort by one lane beyond that.
-constexpr int kSortMax = 256;
+constexpr int kRadixThreads = 256;
+// chunk b holds entries [b * 256 * it, (b + 1) * 256 * it); hist[d * nchunks + b]
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(int64_t N, int it, int shift, int64_t nchunks,
+                                                               const int32_t* __restrict__ key,
+                                                               int32_t* __restrict__ hist) {
+  __shared__ int cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRadixThreads * it;
+  for (int r = 0; r < it; ++r) {
+    const int64_t e = base + (int64_t)r * kRadixThreads + threadIdx.x;
+    if (e < N) atomicAdd(&cnt[(key[e] >> shift) & 255], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nchunks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter: in each round of 256 entries, an entry's place is the
+// running count of its digit (earlier rounds), plus the counts of its digit in
+// the earlier warps of the round, plus its rank among the earlier lanes of its
+// warp with the same digit.
 template <typename TV>
-__global__ void __launch_bounds__(256) k_csc_sort(int64_t n, const int32_t* __restrict__ cstart,
-                                                  int32_t* __restrict__ crow, TV* __restrict__ cval) {
-  __shared__ unsigned long long keys[8][kSortMax];
-  __shared__ TV vals[8][kSortMax];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * 8 + warp;
-  const int64_t nw = (int64_t)gridDim.x * 8;
-  auto key_of = [](int32_t r, TV v) -> unsigned long long {
-    unsigned int vb;
-    if constexpr (sizeof(TV) == 8) vb = (unsigned int)(__double_as_longlong((double)v) >> 32);
-    else vb = __float_as_uint((float)v);
-    return ((unsigned long long)(uint32_t)r << 32) | vb;
-  };
-  for (int64_t j = gw; j < n; j += nw) {
-    const int a = cstart[j], b = cstart[j + 1], len = b - a;
-    if (len <= 1) continue;
-    if (len <= kSortMax) {
-      int P = 1;
-      while (P < len) P <<= 1;
-      for (int t = lane; t < P; t += 32) {
-        keys[warp][t] = t < len ? key_of(crow[a + t], cval[a + t]) : ~0ull;
-        vals[warp][t] = t < len ? cval[a + t] : TV(0);
-      }
-      __syncwarp();
-      for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-          for (int t = lane; t < P; t += 32) {
-            const int partner = t ^ stride;
-            if (partner > t) {
-              const bool up = (t & size) == 0;
-              const unsigned long long kt = keys[warp][t], kp = keys[warp][partner];
-              if ((kt > kp) == up) {
-                keys[warp][t] = kp;
-                keys[warp][partner] = kt;
-                const TV vt = vals[warp][t];
-                vals[warp][t] = vals[warp][partner];
-                vals[warp][partner] = vt;
-              }
-            }
-          }
-          __syncwarp();
-        }
-      }
-      for (int t = lane; t < len; t += 32) {
-        crow[a + t] = (int32_t)(keys[warp][t] >> 32);
-        cval[a + t] = vals[warp][t];
-      }
-      __syncwarp();
-    } else if (lane == 0) {
-      for (int i = a + 1; i < b; ++i) {
-        const int32_t r = crow[i];
-        const TV v = cval[i];
-        const unsigned long long kv = key_of(r, v);
-        int t = i - 1;
-        while (t >= a && key_of(crow[t], cval[t]) > kv) {
-          crow[t + 1] = crow[t];
-          cval[t + 1] = cval[t];
-          --t;
-        }
-        crow[t + 1] = r;
-        cval[t + 1] = v;
-      }
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
+    int64_t N, int it, int shift, int64_t nchunks, const int32_t* __restrict__ offs, const int32_t* __restrict__ kin,
+    const int32_t* __restrict__ rin, const TV* __restrict__ vin, int32_t* __restrict__ kout, int32_t* __restrict__ rout,
+    TV* __restrict__ vout) {
+  constexpr int NW = kRadixThreads / 32;
+  __shared__ int run[256];
+  __shared__ int wc[NW][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  run[tid] = offs[(int64_t)tid * nchunks + blockIdx.x];
+  for (int w = 0; w < NW; ++w) wc[w][tid] = 0;
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t base = (int64_t)blockIdx.x * kRadixThreads * it;
+  for (int r = 0; r < it; ++r) {
+    const int64_t e = base + (int64_t)r * kRadixThreads + tid;
+    const bool valid = e < N;
+    const int kv = valid ? kin[e] : 0;
+    const int d = valid ? ((kv >> shift) & 255) : 256 + lane;  // lanes without an entry never match
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & lt);
+    if (valid && rank == 0) wc[warp][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      int dest = run[d] + rank;
+      for (int w = 0; w < warp; ++w) dest += wc[w][d];
+      kout[dest] = kv;
+      rout[dest] = rin[e];
+      vout[dest] = vin[e];
     }
+    __syncthreads();
+    int tot = 0;
+    for (int w = 0; w < NW; ++w) {
+      tot += wc[w][tid];
+      wc[w][tid] = 0;
+    }
+    run[tid] += tot;
+    __syncthreads();
   }
 }
 
@@ -237,11 +246,15 @@ int csr_classify(CsrWs& w, const int64_t* rowptr, int64_t m, int64_t n, int64_t 
   if ((rc = launch_scan_i32(m, w.hflag, w.hpos, w.scan_tmp, st))) return rc;
   if ((rc = launch_scan_i32(m, w.lflag, w.lpos, w.scan_tmp, st))) return rc;
   if ((rc = launch_scan_i32(m, w.mflag, w.mpos, w.scan_tmp, st))) return rc;
-  k_csr_lists<<<g, 256, 0, st>>>(m, w.hflag, w.lflag, w.mflag, w.hpos, w.lpos, w.mpos, w.heavy, w.light, w.mid,
-                                 w.count);
+  k_light_lens<<<g, 256, 0, st>>>(m, rowptr, w.lflag, w.llen);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
-  RLU_CUDA_TRY(cudaMemcpyAsync(cnt, w.count, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if ((rc = launch_scan_i32(m, w.llen, w.loff, w.scan_tmp, st))) return rc;
+  k_csr_lists<<<g, 256, 0, st>>>(m, w.hflag, w.lflag, w.mflag, w.hpos, w.lpos, w.mpos, w.loff, w.heavy, w.light,
+                                 w.mid, w.count);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  RLU_CUDA_TRY(cudaMemcpyAsync(cnt, w.count, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   RLU_CUDA_TRY(cudaStreamSynchronize(st));
   cr.light = w.light;
   cr.heavy = w.heavy;
@@ -250,16 +263,18 @@ int csr_classify(CsrWs& w, const int64_t* rowptr, int64_t m, int64_t n, int64_t 
   cr.n_light = cnt[0];
   cr.n_heavy = cnt[1];
   cr.n_mid = cnt[2];
+  cr.n_light_nnz = cnt[3];
   cr.direct_max = direct_max;
   return RLU_OK;
 }
 
 template <typename TV, typename TW, typename TB>
-static int spmm_light_cfg(const CsrWs& w, int64_t n, int k, const TW* Wt, TB* B, int num_sms, cudaStream_t st) {
+static int spmm_light_cfg(const CsrWs& w, const int32_t* crow, const void* cval_, int64_t n, int k, const TW* Wt,
+                          TB* B, int num_sms, cudaStream_t st) {
   const unsigned grid = (unsigned)min64(cdiv(n * 32, 256), (int64_t)num_sms * 8);
-  const TV* cval = reinterpret_cast<const TV*>(w.cval);
+  const TV* cval = reinterpret_cast<const TV*>(cval_);
 #define RLU_SPMM(K)                                                                                     \
-  k_spmm_csc<TV, TW, TB, K><<<grid, 256, 0, st>>>(n, k, w.cstart, w.crow, cval, Wt, B);
+  k_spmm_csc<TV, TW, TB, K><<<grid, 256, 0, st>>>(n, k, w.cstart, crow, cval, Wt, B);
   if (k <= 32) RLU_SPMM(1)
   else if (k <= 64) RLU_SPMM(2)
   else if (k <= 128) RLU_SPMM(4)
@@ -284,26 +299,47 @@ static int light_part(const CsrWs& w, const int64_t* rowptr, const int32_t* coli
   note_launch();
   int rc;
   if ((rc = launch_scan_i32(n, w.ccnt, w.cstart, w.scan_tmp, st))) return rc;
-  RLU_CUDA_TRY(cudaMemsetAsync(w.ccnt, 0, sizeof(int32_t) * (n + 1), st));
-  k_csc_fill<TV><<<gr, 256, 0, st>>>(rowptr, colind, val, n, cr.light, cr.n_light, w.cstart, w.ccnt, w.crow,
-                                     reinterpret_cast<TV*>(w.cval));
+  // the light entries, flat in row order, then sorted by column (stable)
+  const int64_t N = cr.n_light_nnz;
+  int32_t* key[2] = {w.ekey[0], w.ekey[1]};
+  int32_t* row[2] = {w.erow[0], w.erow[1]};
+  TV* vv[2] = {reinterpret_cast<TV*>(w.eval[0]), reinterpret_cast<TV*>(w.eval[1])};
+  k_light_expand<TV><<<gr, 256, 0, st>>>(rowptr, colind, val, n, cr.light, cr.d_count, w.loff, key[0], row[0],
+                                         vv[0]);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
-  k_csc_sort<TV><<<(unsigned)min64(cdiv(n, 8), (int64_t)num_sms * 4), 256, 0, st>>>(n, w.cstart, w.crow,
-                                                                                   reinterpret_cast<TV*>(w.cval));
-  RLU_CUDA_TRY(cudaGetLastError());
-  note_launch();
+  int cur = 0;
+  if (N > 0) {
+    const int it = (int)max64(8, cdiv(cdiv(N, kRadixThreads), kRadixMaxChunks));
+    const int64_t nchunks = cdiv(N, (int64_t)kRadixThreads * it);
+    int bits = 1;
+    while (((int64_t)1 << bits) <= n) ++bits;  // keys run up to n
+    for (int shift = 0; shift < bits; shift += 8) {
+      k_radix_hist<<<(unsigned)nchunks, kRadixThreads, 0, st>>>(N, it, shift, nchunks, key[cur], w.rhist);
+      RLU_CUDA_TRY(cudaGetLastError());
+      note_launch();
+      if ((rc = launch_scan_i32(256 * nchunks, w.rhist, w.roffs, w.scan_tmp, st))) return rc;
+      k_radix_scatter<TV><<<(unsigned)nchunks, kRadixThreads, 0, st>>>(N, it, shift, nchunks, w.roffs, key[cur],
+                                                                       row[cur], vv[cur], key[cur ^ 1],
+                                                                       row[cur ^ 1], vv[cur ^ 1]);
+      RLU_CUDA_TRY(cudaGetLastError());
+      note_launch();
+      cur ^= 1;
+    }
+  }
+  const int32_t* crow = row[cur];
+  const void* cval = vv[cur];
   dim3 tg((unsigned)cdiv(m, 32), (unsigned)cdiv(k, 32));
   if (f64) {
     k_transpose<double><<<tg, dim3(32, 8), 0, st>>>(k, m, (const double*)W, (double*)Wt);
     RLU_CUDA_TRY(cudaGetLastError());
     note_launch();
-    return spmm_light_cfg<TV, double, double>(w, n, k, (const double*)Wt, (double*)B, num_sms, st);
+    return spmm_light_cfg<TV, double, double>(w, crow, cval, n, k, (const double*)Wt, (double*)B, num_sms, st);
   }
   k_transpose<float><<<tg, dim3(32, 8), 0, st>>>(k, m, (const float*)W, (float*)Wt);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
-  return spmm_light_cfg<TV, float, df32>(w, n, k, (const float*)Wt, (df32*)B, num_sms, st);
+  return spmm_light_cfg<TV, float, df32>(w, crow, cval, n, k, (const float*)Wt, (df32*)B, num_sms, st);
 }
 
 int csr_bgemm(CsrWs& w, const int64_t* rowptr, const int32_t* colind, const void* val, int dtype, int prec,

@@ -11,8 +11,12 @@ namespace rlu {
 struct CsrWs {
   int32_t *hflag, *lflag, *hpos, *lpos, *heavy, *light, *count;  // rows (m, m+1) and counts (3)
   int32_t *mflag, *mpos, *mid;                                    // light rows sketched through the FFT
-  int32_t *ccnt, *cstart, *crow;                                  // CSC of the light entries
-  void* cval;
+  int32_t *ccnt, *cstart;                                         // column counts and starts of the light entries
+  int32_t *llen, *loff;                                           // light entries per row and their flat offsets
+  int32_t *rhist, *roffs;                                         // radix sort: digit counts per chunk, offsets
+  int32_t* ekey[2];                                               // light entries, two slots (keys = columns)
+  int32_t* erow[2];
+  void* eval[2];
   void* D;   // heavy rows, dense (n_heavy x n)
   void* Wt;  // W^T (m x k)
   void* Wh;  // W restricted to the heavy rows (k x n_heavy)
@@ -22,8 +26,13 @@ struct CsrWs {
 
 // Row classification; light rows with at most direct_max entries are
 // sketched by direct evaluation (direct_max < 0: none).  Reads the three row
-// counts (light, heavy, mid) back through `cnt` (three int32 of page-locked
-// host memory).
+// counts (light, heavy, mid) and the number of light entries back through
+// `cnt` (four int32 of page-locked host memory).
+// Radix sort of the light entries: at most this many chunks per pass.
+constexpr int64_t kRadixMaxChunks = 4096;
+// Device bytes per light entry: two slots of (column, row, value up to 8 bytes).
+constexpr size_t kCsrEntryBytes = 2 * (4 + 4 + 8);
+
 int csr_classify(CsrWs& w, const int64_t* rowptr, int64_t m, int64_t n, int64_t nnz, int64_t direct_max,
                  unsigned int* status, CsrRows& cr, int32_t* cnt, cudaStream_t st);
 int csr_bgemm(CsrWs& w, const int64_t* rowptr, const int32_t* colind, const void* val, int dtype, int prec,

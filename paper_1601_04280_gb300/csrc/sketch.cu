@@ -1287,12 +1287,15 @@ __global__ void k_fjl_table(int l1, int l, const float* __restrict__ dsign, cons
 }
 
 // A CTA holds the columns [c0, c0 + lg) of T in shared memory (blockIdx.y
-// picks the group); warp w of CTA x takes the light rows x * kDirWarps + w,
-// + gridDim.x * kDirWarps, ... with at most direct_max entries.  Lanes own
-// the columns; each round of 32 entries is staged as (bucket, signed value)
-// pairs and read back by every lane in entry order (a fixed order: results
-// repeat bit for bit).
+// picks the group); warp w of CTA x takes kDirRows light rows at a time
+// (those with at most direct_max entries), so that the dependent loads of
+// four rows (list, row pointers, entries, hash) are in flight together.
+// Lanes own the columns; each round of 32 entries per row is staged as
+// (bucket, signed value) pairs and read back by every lane in entry order, one
+// accumulator per row (a fixed order: results repeat bit for bit).  Staged
+// slots past a row's end hold (0, 0) and add nothing.
 constexpr int kDirWarps = 32;
+constexpr int kDirRows = 4;
 template <typename TV>
 __global__ void __launch_bounds__(kDirWarps * 32, 1)
     k_sketch_csr_direct(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
@@ -1304,7 +1307,7 @@ __global__ void __launch_bounds__(kDirWarps * 32, 1)
   // for lg < 32 runs past row b (into row b + 1, or the zero pad after the
   // last row); those lanes' sums are never stored
   extern __shared__ __align__(16) float Ts[];
-  __shared__ int2 stage[kDirWarps][32];
+  __shared__ int2 stage[kDirWarps][kDirRows][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c0 = blockIdx.y * lg;
   const int ncols = min(lg, l - c0);
@@ -1315,46 +1318,64 @@ __global__ void __launch_bounds__(kDirWarps * 32, 1)
   __syncthreads();
   const int nrows = *count;
   bool bad_csr = false, bad_val = false;
-  for (int64_t li = (int64_t)blockIdx.x * kDirWarps + warp; li < nrows; li += (int64_t)gridDim.x * kDirWarps) {
-    const int row = list[li];
-    const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
-    if (e1 - e0 > direct_max) continue;  // a mid row: the FFT kernel's
-    // four independent chains (entries t = 0, 1, 2, 3 mod 4), summed at the end
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    for (int64_t base = e0; base < e1; base += 32) {
-      const int64_t e = base + lane;
-      int b = 0;
-      float x = 0.f;
-      if (e < e1) {
-        const int col = colind[e];
-        if (col < 0 || (int64_t)col >= n) {
-          bad_csr = true;
+  const int64_t step = (int64_t)gridDim.x * kDirWarps * kDirRows;
+  for (int64_t li0 = ((int64_t)blockIdx.x * kDirWarps + warp) * kDirRows; li0 < nrows; li0 += step) {
+    int row[kDirRows];
+    int64_t e0[kDirRows], len[kDirRows];
+    int64_t len_max = 0;
+#pragma unroll
+    for (int q = 0; q < kDirRows; ++q) {
+      row[q] = li0 + q < nrows ? list[li0 + q] : -1;
+      e0[q] = 0;
+      len[q] = 0;
+      if (row[q] >= 0) {
+        const int64_t a = rowptr[row[q]], z = rowptr[row[q] + 1];
+        if (z - a <= direct_max) {  // longer rows (mid) are the FFT kernel's
+          e0[q] = a;
+          len[q] = z - a;
         } else {
-          const TV v = val[e];
-          bad_val |= !finite_(v);
-          const uint32_t h = hs[col];
-          b = (int)(h & 0x7fffffffu);
-          x = (h >> 31) ? -(float)v : (float)v;
+          row[q] = -1;
         }
       }
-      stage[warp][lane] = make_int2(b * lg, __float_as_int(x));
-      __syncwarp();
-      const int cnt = (int)min64(32, e1 - base);
-      int t = 0;
-      for (; t + 4 <= cnt; t += 4) {
-        const int2 p0 = stage[warp][t], p1 = stage[warp][t + 1], p2 = stage[warp][t + 2], p3 = stage[warp][t + 3];
-        a0 = fmaf(__int_as_float(p0.y), Ts[p0.x + lane], a0);
-        a1 = fmaf(__int_as_float(p1.y), Ts[p1.x + lane], a1);
-        a2 = fmaf(__int_as_float(p2.y), Ts[p2.x + lane], a2);
-        a3 = fmaf(__int_as_float(p3.y), Ts[p3.x + lane], a3);
+      len_max = max(len_max, len[q]);
+    }
+    float acc[kDirRows];
+#pragma unroll
+    for (int q = 0; q < kDirRows; ++q) acc[q] = 0.f;
+    for (int64_t base = 0; base < len_max; base += 32) {
+#pragma unroll
+      for (int q = 0; q < kDirRows; ++q) {
+        int b = 0;
+        float x = 0.f;
+        if (base + lane < len[q]) {
+          const int64_t e = e0[q] + base + lane;
+          const int col = colind[e];
+          if (col < 0 || (int64_t)col >= n) {
+            bad_csr = true;
+          } else {
+            const TV v = val[e];
+            bad_val |= !finite_(v);
+            const uint32_t h = hs[col];
+            b = (int)(h & 0x7fffffffu);
+            x = (h >> 31) ? -(float)v : (float)v;
+          }
+        }
+        stage[warp][q][lane] = make_int2(b * lg, __float_as_int(x));
       }
-      for (; t < cnt; ++t) {
-        const int2 p = stage[warp][t];
-        a0 = fmaf(__int_as_float(p.y), Ts[p.x + lane], a0);
+      __syncwarp();
+      const int cnt = (int)min64(32, len_max - base);
+      for (int t = 0; t < cnt; ++t) {
+#pragma unroll
+        for (int q = 0; q < kDirRows; ++q) {
+          const int2 p = stage[warp][q][t];
+          acc[q] = fmaf(__int_as_float(p.y), Ts[p.x + lane], acc[q]);
+        }
       }
       __syncwarp();
     }
-    if (lane < ncols) Y[(int64_t)row * l + c0 + lane] = (double)((a0 + a1) + (a2 + a3));
+#pragma unroll
+    for (int q = 0; q < kDirRows; ++q)
+      if (row[q] >= 0 && lane < ncols) Y[(int64_t)row[q] * l + c0 + lane] = (double)acc[q];
   }
   if (bad_csr) set_flag(status, FLAG_BAD_CSR);
   if (bad_val) set_flag(status, FLAG_NONFINITE);
@@ -1413,15 +1434,16 @@ static int launch_csr_cfg(const int64_t* rowptr, const int32_t* colind, const TV
       k_fjl_table<<<(unsigned)cdiv((int64_t)l1 * l, 256), 256, 0, st>>>(l1, l, ws.dsign, ws.R, ws.tw32, table);
       RLU_CUDA_TRY(cudaGetLastError());
       note_launch();
-      // column groups of at most 32 (a lane each) whose slice of T fits in shared memory
-      const int lg_max = (int)min64(32, (int64_t)(200 * 1024) / (4 * (int64_t)l1));
+      // column groups of at most 32 (a lane each) whose slice of T fits in shared
+      // memory beside the 32 KB of staged entries
+      const int lg_max = (int)min64(32, ((int64_t)(190 * 1024) - 128) / (4 * (int64_t)l1));
       if (lg_max < 1) return RLU_EINVAL;
       const int G = (int)cdiv(l, lg_max);
       const int lg = (int)cdiv(l, G);
       const size_t smem = (size_t)4 * ((size_t)l1 * lg + 32);  // the table slice and its zero pad
       auto kern = k_sketch_csr_direct<TV>;
       if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
-      const int64_t per_group = min64(cdiv(cr.n_light, kDirWarps), max64(1, cdiv((int64_t)num_sms, G)));
+      const int64_t per_group = min64(cdiv(cr.n_light, (int64_t)kDirWarps * kDirRows), max64(1, cdiv((int64_t)num_sms, G)));
       kern<<<dim3((unsigned)per_group, (unsigned)G), kDirWarps * 32, smem, st>>>(
           rowptr, colind, val, n, cr.light, cr.d_count, cr.direct_max, l1, l, lg, table, ws.hs, Y, status);
       RLU_CUDA_TRY(cudaGetLastError());

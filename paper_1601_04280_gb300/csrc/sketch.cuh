@@ -52,6 +52,7 @@ struct CsrRows {
   int32_t* mid;        // light rows with more than direct_max entries, ascending
   int32_t* d_count;    // device: [n_light, n_heavy, n_mid]
   int64_t n_light, n_heavy, n_mid;  // host copies
+  int64_t n_light_nnz;                // entries of the light rows
   int64_t direct_max;  // < 0: no direct evaluation
 };
 
