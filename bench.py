@@ -685,6 +685,16 @@ def run_serving(args, rank, world, local):
             span_max = float(t.item())
         sat = len(reqs) / span_sat
         runs = {"saturation": serving.summarize(res_sat, span_sat)}
+    # the same trace with dense requests served from captured graphs per size
+    # bucket (m, n rounded up to the bucket ladder, zero-padded; a bucket's
+    # graph is captured the second time its key comes)
+    with serving.Server(pool_bytes, slots=args.slots, coop_ctas=coop, graphs=True, graph_min_uses=2) as gsrv:
+        gsrv.run(warm, open_loop=False)
+        res_g, span_g = gsrv.run(reqs, open_loop=False)
+        runs["saturation_graph_buckets"] = dict(serving.summarize(res_g, span_g), **gsrv.graph_stats,
+                                                buckets_cached=len(gsrv.buckets))
+    with serving.Server(pool_bytes, slots=args.slots, coop_ctas=coop) as srv:
+        srv.run(warm, open_loop=False)
         for frac in (0.5, 0.9):
             set_arrivals(frac * sat)
             res, span = srv.run(reqs, open_loop=True)

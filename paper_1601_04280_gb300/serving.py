@@ -18,15 +18,25 @@ Every kernel's tiling, grid and reduction order depend only on the request's
 own sizes and the SM count, never on what else is running, so a request's
 factors are bit-for-bit the same alone and in the mix.
 
-Repeated exact sizes can use captured launch graphs instead (GraphBucket:
-one capture per size, replayed with the request copied into the bucket's own
-input buffer).
+Dense requests can also be served from captured launch graphs per size
+bucket (Server(graphs=True)): m and n are rounded up to a ladder of sizes
+(bucket_dim), the request is copied into the bucket's zero-padded input
+buffer, and one graph per (bucket sizes, k, l, l1, seed, precision) replays
+the whole factorization.  Zero columns add exact zeros to every sum of the
+sketch and to B, zero rows never win a pivot (ties go to the smaller
+position), and padded positions are never swapped, so the first m rows of L,
+the first n columns of U, p[:m] and q[:n] are the request's factors (up to
+the rounding of sums whose splits depend on the padded sizes).  A bucket's
+memory stays in the pool while it is cached and is evicted, least recently
+used first, when admission needs the room.  GraphBucket serves one exact
+size outside the server.
 
 This module is host-side orchestration only: every step of every
 factorization runs in the library's kernels.
 """
 import collections
 import ctypes
+import math
 import queue
 import threading
 import time
@@ -177,17 +187,66 @@ def footprint(req):
     return sum(_up(b) for _, b in plan_carve(req))
 
 
+def bucket_dim(x, lo=512):
+    """Smallest value >= x of the ladder lo, lo sqrt 2, 2 lo, ... (each rounded
+    up to a multiple of 64): zero padding to it costs at most 50 % per side."""
+    i = 0
+    while True:
+        base = lo << (i // 2)  # powers of two exactly; the half steps rounded up
+        b = base if i % 2 == 0 else int(math.ceil(base * math.sqrt(2.0) / 64.0)) * 64
+        if b >= x:
+            return b
+        i += 1
+
+
+def bucket_key(req):
+    """Graph bucket of a dense request whose A is on the device, or None."""
+    if req.csr is not None or req.A is None or _on_host(req.A):
+        return None
+    return (bucket_dim(req.m), bucket_dim(req.n), req.k, req.l, req.l1, req.seed, req.prec, str(req.A.dtype))
+
+
+def plan_outputs(req):
+    """The pieces of a request served from a graph bucket: its outputs only."""
+    esz = 8 if req.prec == "f64" else 4
+    return [("L", esz * req.m * req.k), ("U", esz * req.k * req.n), ("p", 8 * req.m), ("q", 8 * req.n),
+            ("status", 4)]
+
+
+def plan_bucket(key):
+    """Pool pieces of one graph bucket: handle workspace, padded input, outputs."""
+    mb, nb, k, l, l1, seed, prec, dt = key
+    esz_in = {"torch.float64": 8, "torch.float32": 4, "torch.bfloat16": 2}[dt]
+    esz = 8 if prec == "f64" else 4
+    return [("ws", rlu_workspace_bytes(mb, nb, k, l, l1, prec)), ("A", esz_in * mb * nb), ("L", esz * mb * k),
+            ("U", esz * k * nb), ("p", 8 * mb), ("q", 8 * nb), ("status", 4)]
+
+
+@dataclass
+class _Bucket:
+    key: tuple
+    carve: object
+    h: object = None
+    graph: object = None
+    busy: bool = False
+    last_used: float = 0.0
+    replays: int = 0
+
+
 class Server:
     """Slots x (stream, worker thread) over one device pool."""
 
     def __init__(self, pool_bytes, slots=8, device="cuda", keep_outputs=False, max_bypass=None, return_host=None,
-                 coop_ctas=None):
+                 coop_ctas=None, graphs=False, graph_min_uses=2):
         """return_host: None, or (max_m, max_n, max_k, prec): every request's L, U,
         p, q and status are copied back into page-locked host buffers of the
         slot (sized for those maxima) before the request counts as done.
         coop_ctas: bound on the CTAs of each request's grid-synchronised kernels
         (rlu_set_max_ctas; 0 = one per SM; None = a quarter of the SMs, so that
-        several requests' eliminations run side by side)."""
+        several requests' eliminations run side by side).
+        graphs: serve dense device requests from captured launch graphs per
+        size bucket; a bucket is built (and its graph captured) when its key
+        has come graph_min_uses times, and replayed from then on."""
         import torch
         load()
         self.device = torch.device(device)
@@ -215,6 +274,13 @@ class Server:
                               torch.empty(mm, dtype=torch.int64, pin_memory=True),
                               torch.empty(mn, dtype=torch.int64, pin_memory=True),
                               torch.zeros(1, dtype=torch.int32, pin_memory=True)) for _ in range(slots)]
+        self.graphs = bool(graphs) and self.device.type == "cuda"
+        self.graph_min_uses = max(1, int(graph_min_uses))
+        self.buckets = {}
+        self.key_seen = collections.Counter()
+        self.graph_stats = {"replays": 0, "captures": 0, "evictions": 0, "eager": 0}
+        self.status_host = [torch.zeros(1, dtype=torch.int32, pin_memory=True) for _ in range(slots)] \
+            if cuda else [None] * slots
         self.worker_error = None
         self.threads = [threading.Thread(target=self._worker, args=(s,), daemon=True) for s in range(slots)]
         for t in self.threads:
@@ -236,12 +302,19 @@ class Server:
             job = self.jobs[s].get()
             if job is None:
                 return
-            req, carve, t0 = job
+            req, carve, t0, bucket, ready = job
             try:
-                status, outputs = self._execute(req, carve, stream, sptr, s)
+                if ready is not None:
+                    # device inputs made on the caller's stream are complete
+                    # before this slot's stream reads them
+                    stream.wait_event(ready)
+                if bucket is not None:
+                    status, outputs = self._execute_bucket(req, carve, bucket, stream, sptr, s)
+                else:
+                    status, outputs = self._execute(req, carve, stream, sptr, s)
             except Exception as e:  # reported as a failed request, the loop goes on
                 status, outputs = -1, repr(e)
-            self.done.put((s, req, carve, status, time.perf_counter() - t0, outputs))
+            self.done.put((s, req, carve, status, time.perf_counter() - t0, outputs, bucket))
 
     def _execute(self, req, carve, stream, sptr, slot=0):
         import torch
@@ -316,9 +389,66 @@ class Server:
             stream.synchronize()
         return status, outputs
 
+    def _execute_bucket(self, req, carve, bucket, stream, sptr, slot):
+        """A dense request through its size bucket: copy A into the zero-padded
+        bucket input, replay the bucket's graph (the first use runs eagerly and
+        captures it), copy the request's part of the outputs to its carve."""
+        import torch
+        lib = load()
+        mb, nb, k, l, l1, seed, prec, _ = bucket.key
+        BP = bucket.carve.parts
+        pool = self.pool
+        bptr = lambda name: ctypes.c_void_p(pool.base + BP[name][0])  # noqa: E731
+        ptr = lambda name: ctypes.c_void_p(pool.base + carve.parts[name][0])  # noqa: E731
+        A = req.A
+        esz_in = A.element_size()
+        with torch.cuda.stream(stream):
+            pool.tensor(BP["A"][0], (mb, nb), A.dtype).zero_()
+        rlu_copy_block_async(bptr("A"), nb * esz_in, ctypes.c_void_p(A.data_ptr()), A.stride(0) * esz_in,
+                             req.n * esz_in, req.m, sptr)
+        code = _dtype_code(A)
+        if bucket.h is None:
+            bucket.h = rlu_create_in(mb, nb, k, l, l1, seed, bptr("ws"), BP["ws"][1], sptr)
+            rlu_set_precision(bucket.h, PREC[prec])
+            if self.coop_ctas:
+                rlu_set_max_ctas(bucket.h, self.coop_ctas)
+        if bucket.graph is None:
+            status = lib.rlu_factor_dense(bucket.h, bptr("A"), nb, code, bptr("L"), bptr("U"), bptr("p"), bptr("q"),
+                                          sptr)
+            if status in (RLU_OK, RLU_WRANK):
+                bucket.graph = rlu_graph_capture_dense(bucket.h, bptr("A"), nb, code, bptr("L"), bptr("U"),
+                                                       bptr("p"), bptr("q"), bptr("status"), sptr)
+                self.graph_stats["captures"] += 1
+        else:
+            rlu_graph_launch(bucket.graph, sptr)
+            sh = self.status_host[slot]
+            rlu_copy_block_async(ctypes.c_void_p(sh.data_ptr()), 4, bptr("status"), 4, 4, 1, sptr)
+            stream.synchronize()
+            status = int(sh[0])
+            bucket.replays += 1
+            self.graph_stats["replays"] += 1
+        if status in (RLU_OK, RLU_WRANK):
+            esz = 8 if prec == "f64" else 4
+            # rows 0..m-1 of L and columns 0..n-1 of U, p[:m], q[:n]
+            rlu_copy_block_async(ptr("L"), esz * req.m * k, bptr("L"), esz * req.m * k, esz * req.m * k, 1, sptr)
+            rlu_copy_block_async(ptr("U"), esz * req.n, bptr("U"), esz * nb, esz * req.n, k, sptr)
+            rlu_copy_block_async(ptr("p"), 8 * req.m, bptr("p"), 8 * req.m, 8 * req.m, 1, sptr)
+            rlu_copy_block_async(ptr("q"), 8 * req.n, bptr("q"), 8 * req.n, 8 * req.n, 1, sptr)
+        outputs = None
+        if self.keep_outputs:
+            odt = _out_dtype(req.prec)
+            outputs = (torch.empty((req.m, req.k), dtype=odt, pin_memory=True),
+                       torch.empty((req.k, req.n), dtype=odt, pin_memory=True),
+                       torch.empty(req.m, dtype=torch.int64, pin_memory=True),
+                       torch.empty(req.n, dtype=torch.int64, pin_memory=True))
+            for t, name in zip(outputs, "LUpq"):
+                nbytes = t.numel() * t.element_size()
+                rlu_copy_block_async(ctypes.c_void_p(t.data_ptr()), nbytes, ptr(name), nbytes, nbytes, 1, sptr)
+        stream.synchronize()
+        return status, outputs
+
     # ---- scheduler side -------------------------------------------------------
-    def _try_carve(self, req):
-        parts = plan_carve(req)
+    def _carve_parts(self, parts):
         total = sum(_up(b) for _, b in parts)
         off = self.pool.alloc(total)
         if off is None:
@@ -329,6 +459,52 @@ class Server:
             c.parts[name] = (o, b)
             o += _up(b)
         return c
+
+    def _try_carve(self, req):
+        return self._carve_parts(plan_carve(req))
+
+    def _evict_one(self):
+        """Drop the least recently used idle graph bucket; False if none."""
+        idle = [b for b in self.buckets.values() if not b.busy]
+        if not idle:
+            return False
+        b = min(idle, key=lambda x: x.last_used)
+        if b.graph is not None:
+            rlu_graph_destroy(b.graph)
+        if b.h is not None:
+            rlu_destroy(b.h)
+        self.pool.free(b.carve.off, b.carve.total)
+        del self.buckets[b.key]
+        self.graph_stats["evictions"] += 1
+        return True
+
+    def _admit(self, req):
+        """(carve, bucket) for the request, or None when the pool has no room."""
+        key = bucket_key(req) if self.graphs else None
+        if key is not None:
+            self.key_seen[key] += 1
+            b = self.buckets.get(key)
+            if b is None and self.key_seen[key] >= self.graph_min_uses:
+                bc = self._carve_parts(plan_bucket(key))
+                if bc is not None:
+                    b = _Bucket(key, bc)
+                    self.buckets[key] = b
+            if b is not None and not b.busy:
+                carve = self._carve_parts(plan_outputs(req))
+                if carve is not None:
+                    b.busy = True
+                    b.last_used = time.perf_counter()
+                    return carve, b
+            self.key_seen[key] -= 1  # counted again when it is admitted
+        while True:
+            carve = self._try_carve(req)
+            if carve is not None:
+                if key is not None:
+                    self.key_seen[key] += 1
+                    self.graph_stats["eager"] += 1
+                return carve, None
+            if not self._evict_one():
+                return None
 
     def run(self, requests, open_loop=True):
         """Serve `requests` (t_arrive in seconds from the start; ignored when
@@ -343,6 +519,10 @@ class Server:
         results = {}
         admitted_at = {}
         bypassed = 0
+        import torch
+        # the requests' device tensors may still be in flight on the caller's
+        # stream: every slot stream waits for this point of it
+        ready = torch.cuda.current_stream(self.device).record_event() if self.device.type == "cuda" else None
         t0 = time.perf_counter()
         n_total = len(requests)
         while len(results) < n_total:
@@ -356,10 +536,11 @@ class Server:
                 req = waiting[i]
                 if i > 0 and bypassed >= self.max_bypass:
                     break
-                carve = self._try_carve(req)
-                if carve is None:
+                got = self._admit(req)
+                if got is None:
                     i += 1
                     continue
+                carve, bucket = got
                 del waiting[i]
                 if i > 0:
                     bypassed += 1
@@ -367,7 +548,7 @@ class Server:
                     bypassed = 0
                 s = free_slots.pop()
                 admitted_at[req.rid] = time.perf_counter() - t0
-                self.jobs[s].put((req, carve, t0))
+                self.jobs[s].put((req, carve, t0, bucket, ready))
             # wait for a completion or the next arrival (and look at the workers
             # at least once a second)
             timeout = 1.0
@@ -380,8 +561,10 @@ class Server:
                     raise RuntimeError("a serving worker stopped: %s" % self.worker_error)
                 continue
             while True:
-                s, req, carve, status, t_done, outputs = item
+                s, req, carve, status, t_done, outputs, bucket = item
                 self.pool.free(carve.off, carve.total)
+                if bucket is not None:
+                    bucket.busy = False
                 free_slots.append(s)
                 results[req.rid] = Result(req.rid, status, req.t_arrive if open_loop else 0.0, admitted_at[req.rid],
                                           t_done, s, carve.total, outputs)
@@ -397,6 +580,12 @@ class Server:
             q.put(None)
         for t in self.threads:
             t.join()
+        for b in list(self.buckets.values()):
+            if b.graph is not None:
+                rlu_graph_destroy(b.graph)
+            if b.h is not None:
+                rlu_destroy(b.h)
+        self.buckets.clear()
 
     def __enter__(self):
         return self
@@ -432,6 +621,8 @@ class GraphBucket:
         """Factor A (device tensor of the bucket's shape; None = the buffer as
         it is).  Returns the status code."""
         import torch
+        # A may still be in flight on the caller's stream
+        self.stream.wait_stream(torch.cuda.current_stream(self.stream.device))
         with torch.cuda.stream(self.stream):
             if A is not None:
                 self.A.copy_(A)
@@ -443,6 +634,7 @@ class GraphBucket:
                 return code
             self.graph = rlu_graph_capture_dense(self.handle.h, a, self.A.stride(0), _dtype_code(self.A), L, U, p,
                                                  q, ctypes.c_void_p(self.status.data_ptr()), self.sptr)
+            self.stream.synchronize()
             return code
         rlu_graph_launch(self.graph, self.sptr)
         self.stream.synchronize()

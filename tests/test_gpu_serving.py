@@ -16,7 +16,7 @@ from rlu_inputs import serving as rs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from test_gpu_parity import check_pivots  # noqa: E402
+from test_gpu_parity import check_pivots, separated_prefix  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -176,3 +176,63 @@ def test_csr_workspace_limit_enforced(rg):
     f = h.factor_csr(rowptr, colind, val, check=False)
     assert f.status == rg.RLU_EINVAL     # more entries than the scratch was sized for
     h.close()
+
+
+def test_bucketed_graphs_match_plain(rg):
+    """Graph replay per size bucket: requests whose m, n round up to the same
+    bucket (1024 x 1024 here) share one captured graph; each is copied into
+    the bucket's zero-padded input.  Restricted to the request, the padded
+    factorization has the plain call's sketch and row pivots exactly (zero
+    columns add exact zeros, zero rows never win a pivot, padded positions are
+    never swapped).  B = W A is FP32-accurate and its split over the rows
+    follows the padded m, so B differs by FP32 rounding: the column pivots
+    agree on the steps the oracle separates (its two best candidates more
+    than 1e-4 apart), L and U entry by entry (1e-4 of their largest entry)
+    wherever all column pivots agree, |de| <= 1e-6, and every request within
+    the FP32 bar of the oracle."""
+    from paper_1601_04280_gb300 import serving
+    base = rs.dense_base_pool(2, 1100, "cuda", seed=4300)
+    sizes = [(900, 850), (1000, 990), (1024, 1024), (800, 780), (950, 1010), (1024, 900), (870, 1024), (999, 999)]
+    reqs = [serving.Request(i, m, n, 20, 30, 240, 17, A=base[i % 2][:m, :n]) for i, (m, n) in enumerate(sizes)]
+    assert len({serving.bucket_key(r) for r in reqs}) == 1
+    pool_bytes = 2 * sum(serving.footprint(r) for r in reqs)
+    # one slot: the bucket serves the requests one after another (with more
+    # slots a request that finds its bucket busy runs on the ordinary path)
+    with serving.Server(pool_bytes, slots=1, keep_outputs=True, graphs=True, graph_min_uses=1) as srv:
+        res, _ = srv.run(reqs, open_loop=False)
+        stats = dict(srv.graph_stats)
+    assert stats["captures"] == 1 and stats["replays"] == len(reqs) - 1, stats
+    full_q = 0
+    for r, q in zip(res, reqs):
+        assert r.status in (rg.RLU_OK, rg.RLU_WRANK), (q.rid, r.status, r.outputs)
+        L, U, p, qq, st = alone(rg, q)
+        assert torch.equal(r.outputs[2], p), q.rid
+        A = q.A.cpu().double().numpy()
+        o = oracle.factor(A, q.k, q.l, q.l1, seed=q.seed)
+        sb = separated_prefix(o.top_b, np.abs(o.B).max(), 1e-4)
+        assert torch.equal(r.outputs[3][:sb], qq[:sb]), q.rid
+        if torch.equal(r.outputs[3], qq):
+            full_q += 1
+            assert (r.outputs[0] - L).abs().max() <= 1e-4 * L.abs().max()
+            assert (r.outputs[1] - U).abs().max() <= 1e-4
+        g = [t.double().numpy() if t.is_floating_point() else t.numpy() for t in r.outputs]
+        e_b = oracle.relative_residual(A, *g)
+        e_p = oracle.relative_residual(A, L.double().numpy(), U.double().numpy(), p.numpy(), qq.numpy())
+        e_o = oracle.relative_residual(A, o.L, o.U, o.p, o.q)
+        assert abs(e_b - e_p) <= 1e-6, (q.rid, e_b, e_p)
+        assert abs(e_b - e_o) <= 1e-5, (q.rid, e_b, e_o)
+    print("bucketed: %d of %d requests with every column pivot of the plain call" % (full_q, len(reqs)))
+    assert full_q >= 1
+
+
+def test_bucket_ladder():
+    from paper_1601_04280_gb300 import serving
+    assert serving.bucket_dim(1) == 512 and serving.bucket_dim(512) == 512
+    assert serving.bucket_dim(513) == 768 and serving.bucket_dim(1024) == 1024
+    assert serving.bucket_dim(16384) == 16384
+    prev = 0
+    for x in range(1, 16385, 37):
+        b = serving.bucket_dim(x)
+        assert b >= x and b % 64 == 0 and (b <= 1.5 * x or b == 512)
+        assert b >= prev
+        prev = b

@@ -79,8 +79,10 @@ def test_csr_workspace_grows_with_entries_and_is_bounded():
     small = rg.rlu_csr_workspace_bytes(1000, 800, 20, 1000)
     big = rg.rlu_csr_workspace_bytes(1000, 800, 20, 200000)
     assert big > small
-    # heavy rows hold >= n/4 entries each: the dense copy is bounded by the entries
-    assert big < small + 200000 * (8 + 4 * 8 + 8) + 20 * 1000 * 8 + (1 << 22)
+    # heavy rows hold >= n/4 entries each: the dense copy is bounded by the
+    # entries; the sort of the light entries by column holds two slots of
+    # (column key, row, value) = 4 + 4 + 8 bytes per entry
+    assert big < small + 200000 * (8 + 4 * 8 + 8 + 2 * 16) + 20 * 1000 * 8 + (1 << 22)
     with pytest.raises(rg.RluError):
         rg.rlu_csr_workspace_bytes(1000, 800, 20, -1)
 
