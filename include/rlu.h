@@ -325,6 +325,32 @@ int rlu_debug_wait_timeout(int which, int* status);
  * Errors: RLU_EINVAL, RLU_ENOMEM, RLU_ECUDA. */
 int rlu_debug_alu_peak(int which, double* tflops);
 
+/* Test and measurement hook: how step 3 (P Y = L_Y U_Y, Algorithm 1) runs.
+ * block = 0 (default): blocked in panels of 64, 32 or 16 columns when the
+ * unblocked kernel cannot keep Y in shared memory and l >= 32 (the widest
+ * panel whose rows fit the panel kernel's shared memory, at least two
+ * panels), else one unblocked kernel;
+ * -1: always the unblocked kernel; 16, 32, 64: that panel width.  The blocked
+ * form makes the same pivot choices as the unblocked one wherever rounding
+ * does not decide them (its trailing updates are FP64-accurate products on
+ * the tensor cores, summed in another order).
+ * Errors: RLU_EINVAL (null handle, other values, a width above
+ * rlu_debug_lu_block's maximum or >= l). */
+int rlu_debug_set_lu_block(rlu_t h, int32_t block);
+
+/* Test hook: the result of step 3 of the last factorization — Y (m x l,
+ * row-major FP64, rows in their ORIGINAL order: the row at position t of the
+ * pivoted order holds its multipliers in columns < t and row t of U_Y from
+ * column t on; a row never pivoted holds multipliers in all l columns) and
+ * the row permutation (perm[t] = original row at position t, m entries), to
+ * host buffers.  Synchronous.  Errors: RLU_EINVAL, RLU_ECUDA. */
+int rlu_debug_lu_Y(rlu_t h, double* Y_host, int64_t* perm_host);
+
+/* The block setting of rlu_debug_set_lu_block (return value) and, in
+ * *block_max (may be null), the widest panel this handle's workspace holds
+ * (0: the blocked form is unavailable).  RLU_EINVAL for a null handle. */
+int rlu_debug_lu_block(rlu_t h, int32_t* block_max);
+
 /* Test hook: the device FP64 reciprocal used on the Cholesky's dependent chain
  * (Newton's iteration seeded by the FP32 reciprocal approximation), applied to
  * n host values x (x > 0), results to host out.  Synchronous.

@@ -33,7 +33,8 @@ C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_
              "rlu_csr_workspace_bytes", "rlu_set_csr_workspace", "rlu_graph_capture_dense", "rlu_graph_launch",
              "rlu_graph_destroy", "rlu_copy_block_async", "rlu_set_max_ctas",
              "rlu_debug_recip", "rlu_set_second_sketch", "rlu_debug_status_of_flags", "rlu_debug_wait_timeout",
-             "rlu_debug_alu_peak", "rlu_set_transform", "rlu_set_column_pivoting")
+             "rlu_debug_alu_peak", "rlu_set_transform", "rlu_set_column_pivoting", "rlu_debug_set_lu_block",
+             "rlu_debug_lu_block", "rlu_debug_lu_Y")
 
 #: stage names reported by rlu_debug_stage_ms, in order
 STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
@@ -90,6 +91,9 @@ def load(reload=False):
         "rlu_debug_alu_peak": ([c.c_int, c.POINTER(c.c_double)], c.c_int),
         "rlu_set_transform": ([vp, c.c_int], c.c_int),
         "rlu_set_column_pivoting": ([vp, c.c_int], c.c_int),
+        "rlu_debug_set_lu_block": ([vp, c.c_int32], c.c_int),
+        "rlu_debug_lu_block": ([vp, c.POINTER(c.c_int32)], c.c_int),
+        "rlu_debug_lu_Y": ([vp, vp, vp], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -139,6 +143,19 @@ def rlu_set_transform(h, transform):
 
 def rlu_set_column_pivoting(h, on):
     return _check(load().rlu_set_column_pivoting(h, 1 if on else 0), "rlu_set_column_pivoting")
+
+
+def rlu_debug_set_lu_block(h, block):
+    return _check(load().rlu_debug_set_lu_block(h, int(block)), "rlu_debug_set_lu_block")
+
+
+def rlu_debug_lu_block(h):
+    """(block setting, widest panel the handle holds)."""
+    bmax = ctypes.c_int32(0)
+    rc = load().rlu_debug_lu_block(h, ctypes.byref(bmax))
+    if rc not in (-1, 0, 16, 32, 64):
+        _check(rc, "rlu_debug_lu_block")
+    return rc, int(bmax.value)
 
 
 def rlu_set_second_sketch(h, k2, l2, seed2):
@@ -297,6 +314,10 @@ class RandLU:
         """Order the sketch's columns by QR with column pivoting before the panel LU."""
         rlu_set_column_pivoting(self.h, on)
 
+    def set_lu_block(self, block):
+        """Panel width of the LU of the sketch: 0 automatic, -1 unblocked, 16/32/64."""
+        rlu_debug_set_lu_block(self.h, block)
+
     def set_max_ctas(self, max_ctas):
         """Bound the CTAs of the grid-synchronised kernels (0: one per SM)."""
         rlu_set_max_ctas(self.h, max_ctas)
@@ -387,6 +408,14 @@ class RandLU:
         Y = np.empty((self.m, self.l), np.float64)
         _check(load().rlu_debug_Y(self.h, Y.ctypes.data), "rlu_debug_Y")
         return Y
+
+    def debug_lu_Y(self):
+        """Y after step 3 (rows in original order) and the row permutation."""
+        import numpy as np
+        Y = np.empty((self.m, self.l), np.float64)
+        perm = np.empty(self.m, np.int64)
+        _check(load().rlu_debug_lu_Y(self.h, Y.ctypes.data, perm.ctypes.data), "rlu_debug_lu_Y")
+        return Y, perm
 
     def debug_B(self):
         import numpy as np

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "bgemm.cuh"
+#include "blu.cuh"
 #include "colpiv.cuh"
 #include "common.cuh"
 #include "csr.cuh"
@@ -119,6 +120,8 @@ struct rlu_ctx {
   double* bpart = nullptr;  // split-K partials of the FP64 SIMT B = W A
   TcWs tcw{};
   LtcWs ltc{};  // digit planes of the tensor-core L = L_y L_b
+  BluWs blu{};  // digit planes of the blocked LU's trailing updates
+  int lu_block = 0;  // panel width of the LU of Y: 0 automatic, -1 unblocked
   float* fjl_table = nullptr;  // l1 x l table of the CSR sketch's direct evaluation
   int colpiv = 0;                 // rank-revealing column order of the sketch
   void* cp_buf = nullptr;
@@ -227,6 +230,7 @@ Sizes plan_sizes(int64_t m, int64_t n, int k, int l, int l1, int num_sms) {
   s.add(ltc_workspace_bytes(m, k));                  // tensor-core L = L_y L_b: digit planes
   s.add(sizeof(int64_t) * kScanMaxParts);            // multi-CTA scan partials
   s.add(l1 <= kDirectMaxL1 ? sizeof(float) * l1 * l : 0);  // CSR sketch: table of D H R / sqrt(l1)
+  s.add(blu_workspace_bytes(m, l, num_sms));         // blocked LU of Y: digit planes of the trailing updates
   return s;
 }
 
@@ -434,7 +438,7 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Ydbg, h->Y, sizeof(double) * m * l, cudaMemcpyDeviceToDevice, st));
   // step 3: P Y = L_Y U_Y (FP64, l steps)
   h->pw.perm = h->perm_y;
-  if ((rc = launch_pivoted_lu<double>(h->Y, m, l, l, 1, l, h->pw, h->status_dev, coop_sms(h), st))) return rc;
+  if ((rc = launch_lu_y(h->Y, m, l, h->pw, h->blu, h->lu_block, h->status_dev, coop_sms(h), st))) return rc;
   if ((rc = mark(h, 3, st))) return rc;
   // W = L_y^+ P
   PinvArgs pa{};
@@ -545,7 +549,7 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   if (h->debug && h->Ydbg)
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Ydbg, h->Y, sizeof(double) * m * l, cudaMemcpyDeviceToDevice, st));
   h->pw.perm = h->perm_y;
-  if ((rc = launch_pivoted_lu<double>(h->Y, m, l, l, 1, l, h->pw, h->status_dev, coop_sms(h), st))) return rc;
+  if ((rc = launch_lu_y(h->Y, m, l, h->pw, h->blu, h->lu_block, h->status_dev, coop_sms(h), st))) return rc;
   if ((rc = mark(h, 3, st))) return rc;
   PinvArgs pa{};
   pa.m = m; pa.k = k; pa.l = l;
@@ -720,7 +724,9 @@ static int create_common(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1,
   h->sk.scan_tmp = (int64_t*)next();
   h->csr.scan_tmp = h->sk.scan_tmp;
   h->fjl_table = (float*)next();
-  if (tc_setup(h->tcw, tcbase, m, n, k, sms) != RLU_OK || ltc_setup(h->ltc, ltcbase, m, k, sms) != RLU_OK) {
+  void* blubase = next();
+  if (tc_setup(h->tcw, tcbase, m, n, k, sms) != RLU_OK || ltc_setup(h->ltc, ltcbase, m, k, sms) != RLU_OK ||
+      blu_setup(h->blu, blubase, m, l, sms) != RLU_OK) {
     rlu_destroy(h);
     return RLU_ECUDA;
   }
@@ -852,6 +858,20 @@ int rlu_set_precision(rlu_t h, int prec) {
   if (!h || prec < 0 || prec > 3) return RLU_EINVAL;
   h->prec = prec;
   return RLU_OK;
+}
+
+int rlu_debug_set_lu_block(rlu_t h, int32_t block) {
+  if (!h) return RLU_EINVAL;
+  if (block != -1 && block != 0 && block != 16 && block != 32 && block != 64) return RLU_EINVAL;
+  if (block > 0 && (!h->blu.ready || block > h->blu.bmax || block >= h->l)) return RLU_EINVAL;
+  h->lu_block = block;
+  return RLU_OK;
+}
+
+int rlu_debug_lu_block(rlu_t h, int32_t* block_max) {
+  if (!h) return RLU_EINVAL;
+  if (block_max) *block_max = h->blu.ready ? h->blu.bmax : 0;
+  return h->lu_block;
 }
 
 int rlu_set_column_pivoting(rlu_t h, int on) {
@@ -1135,6 +1155,14 @@ int rlu_debug_Y(rlu_t h, double* Y_host) {
   if (!h || !Y_host || !h->Ydbg) return RLU_EINVAL;
   RLU_CUDA_TRY(cudaDeviceSynchronize());
   RLU_CUDA_TRY(cudaMemcpy(Y_host, h->Ydbg, sizeof(double) * h->m * h->l, cudaMemcpyDeviceToHost));
+  return RLU_OK;
+}
+
+int rlu_debug_lu_Y(rlu_t h, double* Y_host, int64_t* perm_host) {
+  if (!h || !Y_host || !perm_host) return RLU_EINVAL;
+  RLU_CUDA_TRY(cudaDeviceSynchronize());
+  RLU_CUDA_TRY(cudaMemcpy(Y_host, h->Y, sizeof(double) * h->m * h->l, cudaMemcpyDeviceToHost));
+  RLU_CUDA_TRY(cudaMemcpy(perm_host, h->perm_y, sizeof(int64_t) * h->m, cudaMemcpyDeviceToHost));
   return RLU_OK;
 }
 

@@ -1,0 +1,508 @@
+// Blocked partial-pivoted LU of the sketch, P Y = L_Y U_Y (step 3 of
+// Algorithm 1), with the trailing updates on the tensor cores.
+//
+// Right-looking blocked elimination in panels of b columns (b = 16, 32, 64):
+//   1. the panel's b steps run in the persistent pivoted-LU kernel on the
+//      panel columns only (every row; the panel in shared memory), with
+//      LAPACK getf2 semantics: the pivot choices depend only on the panel;
+//   2. U12 = L11^{-1} A12 for the panel's pivot rows (FP64 forward
+//      substitution with the unit lower L11, a warp per trailing column);
+//   3. A22 -= L21 U12 for every row not yet pivoted.  The product runs as an
+//      exact digit product (the error-free splitting of Ozaki, Ogita, Oishi
+//      and Rump, Numer. Algorithms 59, 2012): each row of L21 and each column
+//      of U12 is scaled by a power of two and cut into eight signed 7-bit
+//      digits (56 bits); level v = s + t of the digit products accumulates
+//      exactly in FP32 in its own tensor-memory accumulator (every level sum
+//      stays below 2^22 for b <= 64); the epilogue combines the eight levels
+//      exactly in 64-bit integers, assembles the double from the integer's
+//      bits with the two scales in its exponent (rounded to 53 bits) and
+//      subtracts it from A22: one FP64 operation per element.
+// The only approximations are the digits' rounding (2^-57 of the row and
+// column scales) and the dropped levels beyond the eighth, so the update
+// carries the accuracy of an FP64 product while the slow FP64 pipe does only
+// the panels (b^2/2 multiply-adds per row and panel instead of l^2/2 per
+// row) and one subtraction per updated element.
+//
+// The digit planes are packed per row as [chunk of 16/32 columns][digit]
+// [column in chunk], so one pipeline stage brings all eight digits of a
+// chunk in a few 128-byte-wide TMA boxes and the MMA for digit pair (s, t)
+// addresses its K-slice inside those boxes.
+#include <cuda.h>
+#include <climits>
+
+#include "bgemm.cuh"
+#include "blu.cuh"
+#include "common.cuh"
+#include "gemm_tc.cuh"
+
+namespace rlu {
+namespace blu {
+
+constexpr int kD = 8;            // digits of 7 bits
+constexpr int kBM = 128;         // rows per tile (MMA M)
+constexpr int kNT = 32;          // columns per tile: two sets of 8 levels x 32 columns fill tensor memory
+constexpr int kThreads = 320;    // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int kEpiWarps = 8;
+constexpr int kMaxStages = 4;
+constexpr uint32_t kTmemCols = 512;
+constexpr int32_t kSkip = INT_MIN;
+constexpr int kNoExp = -100000;
+
+__host__ __device__ constexpr int chunk_of(int b) { return b >= 32 ? 32 : 16; }
+inline int width_index(int b) { return b == 64 ? 0 : (b == 32 ? 1 : 2); }
+
+template <int KC>
+__host__ __device__ constexpr uint32_t stage_bytes() {
+  return (uint32_t)(kD * KC / 64) * (uint32_t)(kBM * 128 + kNT * 128);
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(tc::smem_u32(dst)),
+      "l"(map), "r"(tc::smem_u32(bar)), "r"(x), "r"(y), "r"(0)
+      : "memory");
+}
+
+// frexp exponent of a finite nonzero double from its bits (|x| in [2^(e-1), 2^e)),
+// kNoExp for zero, subnormal or non-finite values.
+__device__ __forceinline__ int exp_of(double x) {
+  const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  return (ex == 0 || ex == 0x7ff) ? kNoExp : ex - 1022;
+}
+
+// Eight balanced digits of x 2^-e (|x| < 2^e): X = round(x 2^(56 - e)) as a
+// 64-bit integer from the bits of x, then X = sum_s d_s 128^(7 - s) with
+// d_1..d_7 in [-64, 63] and |d_0| <= 128.  Integer operations only.
+__device__ __forceinline__ void digits8(double x, int e, int (&d)[kD]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  long long X = 0;
+  if (ex != 0 && ex != 0x7ff) {
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = ex - 1075 + 56 - e;  // X = mant 2^sh; sh <= 3 since |x| < 2^e
+    unsigned long long u = 0;
+    if (sh >= 0) u = mant << sh;
+    else if (sh > -64) u = (mant + (1ull << (-sh - 1))) >> (-sh);
+    X = (b >> 63) ? -(long long)u : (long long)u;
+  }
+#pragma unroll
+  for (int s = kD - 1; s >= 1; --s) {
+    int r = (int)(X & 127);
+    r -= (r >= 64) ? 128 : 0;
+    d[s] = r;
+    X = (X - r) >> 7;
+  }
+  d[0] = (int)X;
+}
+
+// An integer-valued float with |f| < 2^22 as an int (exact).
+__device__ __forceinline__ int level_int(float f) { return __float_as_int(f + 12582912.0f) - 0x4B400000; }
+
+// t 2^E as a double, rounded to 53 bits (half away from zero), built from the
+// integer's bits; values outside the normal range take the slow FP64 route.
+__device__ __forceinline__ double i64_scaled(long long t, int E) {
+  if (t == 0) return 0.0;
+  const unsigned long long neg = t < 0 ? (1ull << 63) : 0ull;
+  unsigned long long a = t < 0 ? (unsigned long long)(-t) : (unsigned long long)t;
+  const int lz = __clzll((long long)a);
+  a <<= lz;
+  const int ex = 63 - lz + E + 1023;
+  if (ex < 1 || ex > 2046) return ldexp((double)t, E);
+  const unsigned long long bits = ((unsigned long long)(ex - 1) << 52) + (a >> 11) + ((a >> 10) & 1ull);
+  return __longlong_as_double((long long)(bits | neg));
+}
+
+// U12 = L11^{-1} A12 for the panel's pivot rows (positions j0 .. j0 + B - 1),
+// written back into Y, and the digit planes of U12^T (row c = column c of the
+// trailing block) with their scales.  One warp per trailing column.
+template <int B>
+__global__ void __launch_bounds__(256) k_u12(double* __restrict__ Y, int l, int j0, int w,
+                                             const int64_t* __restrict__ perm, __nv_bfloat16* __restrict__ bdig,
+                                             int32_t* __restrict__ bexp) {
+  constexpr int KC = chunk_of(B);
+  constexpr int R = (B + 31) / 32;
+  __shared__ double LT[B][B + 1];  // LT[i][t] = L11[t][i] (t > i), the multiplier of pivot row t at panel column i
+  __shared__ int64_t prow[B];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int t = tid; t < B; t += blockDim.x) prow[t] = perm[j0 + t];
+  __syncthreads();
+  for (int e = tid; e < B * B; e += blockDim.x) {
+    const int t = e / B, i = e - t * B;
+    LT[i][t] = (i < t) ? Y[prow[t] * l + j0 + i] : 0.0;
+  }
+  __syncthreads();
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= w) return;
+  const int64_t col = (int64_t)j0 + B + c;
+  double a[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int t = lane + 32 * r;
+    a[r] = (t < B) ? Y[prow[t < B ? t : 0] * l + col] : 0.0;
+  }
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    const double ui = __shfl_sync(0xffffffffu, a[i / 32], i % 32);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int t = lane + 32 * r;
+      if (t > i && t < B) a[r] = fma(-LT[i][t], ui, a[r]);
+    }
+  }
+  int e = kNoExp;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int t = lane + 32 * r;
+    if (t < B) {
+      Y[prow[t] * l + col] = a[r];
+      e = max(e, exp_of(a[r]));
+    }
+  }
+  e = __reduce_max_sync(0xffffffffu, e);
+  if (e == kNoExp) e = 0;
+  if (lane == 0) bexp[c] = e;
+  __nv_bfloat16* row = bdig + (int64_t)c * (kD * B);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int t = lane + 32 * r;
+    if (t < B) {
+      int d[kD];
+      digits8(a[r], e, d);
+      const int base = (t / KC) * kD * KC + (t % KC);
+#pragma unroll
+      for (int s = 0; s < kD; ++s) row[base + s * KC] = __int2bfloat16_rn(d[s]);
+    }
+  }
+}
+
+// Digit planes of the multipliers L21 (panel columns j0 .. j0 + B - 1) of
+// every row with their scales; rows already pivoted get zero digits and the
+// skip mark.  One warp per row.
+template <int B>
+__global__ void __launch_bounds__(256) k_l21(const double* __restrict__ Y, int64_t m, int l, int j0,
+                                             const int32_t* __restrict__ pstep, __nv_bfloat16* __restrict__ adig,
+                                             int32_t* __restrict__ aexp) {
+  constexpr int KC = chunk_of(B);
+  constexpr int R = (B + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (r >= m) return;
+  const bool skip = pstep[r] >= 0;
+  double x[R];
+  int e = kNoExp;
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int i = lane + 32 * q;
+    x[q] = (!skip && i < B) ? Y[r * l + j0 + i] : 0.0;
+    e = max(e, exp_of(x[q]));
+  }
+  e = __reduce_max_sync(0xffffffffu, e);
+  if (e == kNoExp) e = 0;
+  if (lane == 0) aexp[r] = skip ? kSkip : e;
+  __nv_bfloat16* row = adig + r * (kD * B);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int i = lane + 32 * q;
+    if (i < B) {
+      int d[kD];
+      digits8(x[q], e, d);
+      const int base = (i / KC) * kD * KC + (i % KC);
+#pragma unroll
+      for (int s = 0; s < kD; ++s) row[base + s * KC] = __int2bfloat16_rn(d[s]);
+    }
+  }
+}
+
+// Y[row][c] -= (L21 U12)[row][c] for the M x N trailing block at Y (row
+// stride ldy) from the packed digit planes (nch chunks of KC columns).
+// Persistent: CTA b takes tiles b, b + gridDim.x, ... (128 rows x 32
+// columns, column tile fastest); a ring of nst stages runs across tiles; two
+// accumulator sets let the epilogue of one tile overlap the MMAs of the next.
+template <int KC>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_digit_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t M,
+                   int N, int nch, int nt, int64_t tiles, int nst, const int32_t* __restrict__ aexp,
+                   const int32_t* __restrict__ bexp, double* __restrict__ Y, int64_t ldy, unsigned int* status) {
+  constexpr int NBOX = kD * KC / 64;
+  constexpr uint32_t ABOX = kBM * 128, BBOX = kNT * 128;
+  constexpr uint32_t SB = stage_bytes<KC>();
+  constexpr uint32_t SET = kD * kNT;  // tensor-memory columns of one accumulator set
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto boxA = [&](int s, int j) { return smem + (uint32_t)s * SB + (uint32_t)j * ABOX; };
+  auto boxB = [&](int s, int j) { return smem + (uint32_t)s * SB + NBOX * ABOX + (uint32_t)j * BBOX; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nst; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&tfull[b], 1);
+      tc::mbar_init(&tempty[b], kEpiWarps);
+    }
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    // ---- TMA producer: all digits of one chunk of both operands per stage ----
+    if (lane == 0) {
+      int64_t it = 0;
+      for (int64_t tile = blockIdx.x; tile < tiles && !s_fail; tile += gridDim.x) {
+        const int row0 = (int)((tile / nt) * kBM), col0 = (int)(tile % nt) * kNT;
+        for (int q = 0; q < nch; ++q, ++it) {
+          const int s = (int)(it % nst);
+          if (it >= nst && !tc::mbar_wait(&empty[s], (uint32_t)(((it / nst) - 1) & 1))) {
+            s_fail = 1;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&full[s], SB);
+          for (int j = 0; j < NBOX; ++j) {
+            tma_load_3d(boxA(s, j), &mapA, &full[s], q * kD * KC + j * 64, row0);
+            tma_load_3d(boxB(s, j), &mapB, &full[s], q * kD * KC + j * 64, col0);
+          }
+        }
+      }
+      // every issued load has landed before the CTA may exit
+      for (int64_t j = it - nst < 0 ? 0 : it - nst; j < it; ++j)
+        if (!tc::mbar_wait(&full[j % nst], (uint32_t)((j / nst) & 1))) s_fail = 1;
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer: level v of set b in columns b * SET + v * kNT ----
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16(kBM, kNT);
+      int64_t it = 0, local = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++local) {
+        const int b = (int)(local & 1);
+        if (local >= 2 && !tc::mbar_wait(&tempty[b], (uint32_t)(((local >> 1) - 1) & 1))) { ok = false; break; }
+        tc::tc_fence_after();
+        for (int q = 0; q < nch; ++q, ++it) {
+          const int s = (int)(it % nst);
+          if (!tc::mbar_wait(&full[s], (uint32_t)((it / nst) & 1))) { ok = false; break; }
+          tc::tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < KC / 16; ++kk) {
+#pragma unroll
+            for (int v = 0; v < kD; ++v) {
+              const uint32_t dcol = tmem + (uint32_t)b * SET + (uint32_t)(v * kNT);
+#pragma unroll
+              for (int da = 0; da <= v; ++da) {
+                const int ka = da * KC + kk * 16, kb = (v - da) * KC + kk * 16;
+                const uint64_t aD = tc::sw128_desc(tc::smem_u32(boxA(s, ka >> 6)) + (uint32_t)(ka & 63) * 2u);
+                const uint64_t bD = tc::sw128_desc(tc::smem_u32(boxB(s, kb >> 6)) + (uint32_t)(kb & 63) * 2u);
+                tc::mma_bf16(dcol, aD, bD, idesc, (q == 0 && kk == 0 && da == 0) ? 0u : 1u);
+              }
+            }
+          }
+          tc::mma_commit(&empty[s]);
+        }
+        if (ok) tc::mma_commit(&tfull[b]);
+      }
+      if (!ok) s_fail = 1;
+    }
+  } else {
+    // ---- epilogue (warps 2..9): lane quarter warp mod 4, column half (warp - 2) / 4 ----
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    int64_t local = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
+      const int b = (int)(local & 1);
+      const int64_t row = (tile / nt) * kBM + quarter * 32 + lane;
+      const int cb = (int)(tile % nt) * kNT + half * 16;
+      // this thread's 16 entries of A22 and the column scales, loaded while
+      // the tile's products are still being computed
+      const int ea = row < M ? aexp[row] : kSkip;
+      double* yr = Y + row * ldy;
+      double y[16];
+      int eb[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int c = cb + i;
+        const bool on = ea != kSkip && c < N;
+        y[i] = on ? yr[c] : 0.0;
+        eb[i] = on ? ea + bexp[c] - 56 : 0;
+      }
+      if (!tc::mbar_wait(&tfull[b], (uint32_t)((local >> 1) & 1))) { s_fail = 1; break; }
+      tc::tc_fence_after();
+      const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * SET + (uint32_t)(half * 16);
+      // T = sum_{v <= 6} L_v 128^(6 - v) + floor(L_7 / 128): the product in
+      // units of 2^-56 of the two scales (|T| < 2^62.1 for b <= 64); the
+      // levels come in two batches of four loads with one wait each
+      long long T[16];
+      uint32_t v[4][16];
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tc::tmem_ld16_issue(tq + (uint32_t)((4 * g + q) * kNT), v[q]);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int lv = 4 * g + q;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int L = level_int(__uint_as_float(v[q][i]));
+            if (lv == 0) T[i] = L;
+            else if (lv < kD - 1) T[i] = T[i] * 128 + L;
+            else T[i] += (long long)(L >> 7);
+          }
+        }
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[b]);
+      if (ea != kSkip) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (cb + i < N) yr[cb + i] = y[i] - i64_scaled(T[i], eb[i]);
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+  if (threadIdx.x == 0 && s_fail) set_flag(status, FLAG_TIMEOUT);
+}
+
+template <int KC>
+int launch_update(const BluWs& w, int wi, int64_t M, int N, int nch, double* Yt, int64_t ldy, unsigned int* status,
+                  cudaStream_t st) {
+  constexpr uint32_t SB = stage_bytes<KC>();
+  const int nst = (int)min64(kMaxStages, (int64_t)(200 * 1024) / SB);
+  const size_t smem = (size_t)nst * SB + 1024;
+  auto kern = k_digit_update<KC>;
+  if (int rc = allow_dynamic_smem((const void*)kern, smem)) return rc;
+  const int nt = (int)cdiv(N, kNT);
+  const int64_t tiles = cdiv(M, kBM) * nt;
+  const unsigned grid = (unsigned)min64(tiles, (int64_t)w.num_sms);
+  kern<<<grid, kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap*>(w.mapA[wi]),
+                                     *reinterpret_cast<const CUtensorMap*>(w.mapB[wi]), M, N, nch, nt, tiles, nst,
+                                     w.aexp, w.bexp, Yt, ldy, status);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  return RLU_OK;
+}
+
+template <int B>
+int trailing(double* Y, int64_t m, int l, int j0, const PivLuWs& pw, const BluWs& w, unsigned int* status,
+             cudaStream_t st) {
+  const int wt = l - j0 - B;
+  k_u12<B><<<(unsigned)cdiv(wt, 8), 256, 0, st>>>(Y, l, j0, wt, pw.perm, w.bdig, w.bexp);
+  RLU_CUDA_TRY(cudaGetLastError());
+  k_l21<B><<<(unsigned)cdiv(m * 32, 256), 256, 0, st>>>(Y, m, l, j0, pw.pstep, w.adig, w.aexp);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch(2);
+  constexpr int KC = chunk_of(B);
+  return launch_update<KC>(w, width_index(B), m, wt, B / KC, Y + j0 + B, l, status, st);
+}
+
+// Widest panel whose rows fit the panel kernel's shared memory with `ctas` CTAs.
+int widest_fit(int64_t m, int l, int ctas, int cap) {
+  PivLuWs probe{};
+  probe.max_ctas = 1 << 20;
+  probe.max_cols = l;
+  for (int b : kBluWidths)
+    if (b <= cap && b < l && pivlu_panel_in_smem(m, b, l, probe, ctas)) return b;
+  return 0;
+}
+
+}  // namespace blu
+
+namespace {
+constexpr size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+int blu_bmax(int64_t m, int l, int num_sms) { return blu::widest_fit(m, l, num_sms, 64); }
+}  // namespace
+
+size_t blu_workspace_bytes(int64_t m, int l, int num_sms) {
+  const int b = blu_bmax(m, l, num_sms);
+  if (b == 0) return 0;
+  const size_t row = (size_t)blu::kD * b * 2;
+  return a256(row * (size_t)m) + a256(row * (size_t)l) + a256(4 * (size_t)m) + a256(4 * (size_t)l);
+}
+
+int blu_setup(BluWs& w, void* base, int64_t m, int l, int num_sms) {
+  w.ready = false;
+  w.m = m;
+  w.l = l;
+  w.num_sms = num_sms;
+  w.bmax = blu_bmax(m, l, num_sms);
+  if (w.bmax == 0) return RLU_OK;
+  const size_t row = (size_t)blu::kD * w.bmax * 2;
+  unsigned char* b = (unsigned char*)base;
+  w.adig = (__nv_bfloat16*)b;
+  b += a256(row * (size_t)m);
+  w.bdig = (__nv_bfloat16*)b;
+  b += a256(row * (size_t)l);
+  w.aexp = (int32_t*)b;
+  b += a256(4 * (size_t)m);
+  w.bexp = (int32_t*)b;
+  for (int bw : kBluWidths) {
+    if (bw > w.bmax) continue;
+    const int wi = blu::width_index(bw);
+    const uint64_t kp = (uint64_t)blu::kD * bw;  // packed row: 8 digits of bw columns
+    if (tc_encode_bf16_3d(w.mapA[wi], w.adig, kp, (uint64_t)m, 1, kp, 64, blu::kBM) != RLU_OK ||
+        tc_encode_bf16_3d(w.mapB[wi], w.bdig, kp, (uint64_t)l, 1, kp, 64, blu::kNT) != RLU_OK) {
+      cudaGetLastError();
+      return RLU_OK;  // no tensor maps: the unblocked LU runs
+    }
+  }
+  w.ready = true;
+  return RLU_OK;
+}
+
+int launch_lu_y(double* Y, int64_t m, int l, PivLuWs& pw, const BluWs& bw, int block, unsigned int* status,
+                int coop_sms, cudaStream_t st) {
+  // The form and the panel width depend only on the sizes and the device's SM
+  // count, never on a bound on the grid (coop_sms): results stay bit-for-bit
+  // the same under rlu_set_max_ctas (a panel whose rows no longer fit in
+  // shared memory runs the kernel's global-memory form, which performs the
+  // same operations in the same order).
+  const int sms = bw.num_sms > 0 ? bw.num_sms : coop_sms;
+  int b = 0;
+  if (block > 0) {
+    if ((block != 16 && block != 32 && block != 64) || !bw.ready || block > bw.bmax || block >= l)
+      return RLU_EINVAL;
+    b = block;
+  } else if (block == 0 && bw.ready && l >= 32 && !pivlu_panel_in_smem(m, l, l, pw, sms)) {
+    // blocked when the unblocked kernel could not keep Y in shared memory (its
+    // global-memory form is bound by the FP64 trailing updates); a Y that fits
+    // is bound by the per-step exchange, which blocking does not shorten
+    b = blu::widest_fit(m, l, min64(sms, pw.max_ctas), bw.bmax);
+    while (b > 16 && 2 * b > l) b /= 2;
+  }
+  if (b == 0) return launch_pivoted_lu<double>(Y, m, l, l, 1, l, pw, status, coop_sms, st);
+  for (int j0 = 0; j0 < l; j0 += b) {
+    const int wid = l - j0 < b ? l - j0 : b;
+    int rc = launch_pivoted_lu_panel<double>(Y + j0, m, wid, l, 1, wid, j0, l, pw, status, coop_sms, st);
+    if (rc) return rc;
+    if (l - j0 - wid == 0) break;
+    switch (b) {
+      case 64: rc = blu::trailing<64>(Y, m, l, j0, pw, bw, status, st); break;
+      case 32: rc = blu::trailing<32>(Y, m, l, j0, pw, bw, status, st); break;
+      default: rc = blu::trailing<16>(Y, m, l, j0, pw, bw, status, st); break;
+    }
+    if (rc) return rc;
+  }
+  return RLU_OK;
+}
+
+}  // namespace rlu

@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
                                                    int64_t cs, int steps, int64_t rpc, int32_t* __restrict__ pos_out,
                                                    int32_t* __restrict__ pstep_out, int64_t* __restrict__ perm_out,
                                                    Cand* __restrict__ cand, T* __restrict__ candrow,
-                                                   unsigned int* bar, unsigned int* status, int defer) {
+                                                   unsigned int* bar, unsigned int* status, int defer, int j0,
+                                                   int npos) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = NT / 32;
   const int G = gridDim.x;
@@ -97,19 +98,22 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
   const int nr = (int)max((int64_t)0, min(rpc, rows - r0));
   const int rp = (int)rpc;
   // shared layout
-  T* slab = reinterpret_cast<T*>(smem);                               // nr x cols (SMEM variant)
+  // slab row stride: odd, so that lanes on different rows of one column
+  // fall in different shared-memory banks
+  const int sst = cols | 1;
+  T* slab = reinterpret_cast<T*>(smem);                               // nr x sst (SMEM variant)
   // Pivot rows live in a ring of D + 1 slots (step t in slot t mod (D + 1)) and
   // the multipliers of the pending steps in D columns of lhist (step t in
   // column t mod D): the global-memory variant defers the trailing update and
   // applies D steps at once (D = 1 in shared memory: every step at once).
   const int D = SMEM ? 1 : defer;
   const int RU = D + 1;
-  T* ring = slab + (SMEM ? (size_t)rp * cols : 0);                    // RU x cols
+  T* ring = slab + (SMEM ? (size_t)rp * sst : 0);                     // RU x cols
   T* lhist = ring + (size_t)RU * cols;                                // D x rpc
   int32_t* lpos = reinterpret_cast<int32_t*>(lhist + (size_t)D * rp); // rpc
   int32_t* lstep = lpos + rp;                                         // rpc
   int32_t* ldone = lstep + rp;                                        // rpc: last step applied to the whole row
-  int32_t* pwin = ldone + rp;                                         // steps
+  int32_t* pwin = ldone + rp;                                         // npos
   __shared__ unsigned long long red_v[NW];
   __shared__ int red_p[NW];
   __shared__ int red_r[NW];
@@ -120,26 +124,56 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
 
   const bool row_fast = (cs == 1) ? false : true;  // B^T: consecutive rows are contiguous in memory
   auto at = [&](int r, int c) -> T& {
-    if (SMEM) return slab[(size_t)r * cols + c];
+    if (SMEM) return slab[(size_t)r * sst + c];
     return xref(X, rs, cs, r0 + r, c);
   };
 
-  // load slab, init bookkeeping
-  if (SMEM) {
+  // (row, column) of the e-th slab element in memory order (consecutive
+  // lanes, consecutive addresses)
+  auto slab_rc = [&](int e, int& r, int& c) {
     if (row_fast) {
-      for (int c = warp; c < cols; c += NW)
-        for (int r = lane; r < nr; r += 32) slab[(size_t)r * cols + c] = xref(X, rs, cs, r0 + r, c);
+      c = e / nr;
+      r = e - c * nr;
     } else {
-      for (int r = warp; r < nr; r += NW)
-        for (int c = lane; c < cols; c += 32) slab[(size_t)r * cols + c] = xref(X, rs, cs, r0 + r, c);
+      r = e / cols;
+      c = e - r * cols;
+    }
+  };
+  // load slab (several loads in flight per thread), init bookkeeping
+  if (SMEM) {
+    const int tot = nr * cols;
+    constexpr int U = 8;
+    for (int base = tid; base < tot; base += NT * U) {
+      T v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = base + u * NT;
+        if (e < tot) {
+          int r, c;
+          slab_rc(e, r, c);
+          v[u] = xref(X, rs, cs, r0 + r, c);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = base + u * NT;
+        if (e < tot) {
+          int r, c;
+          slab_rc(e, r, c);
+          slab[(size_t)r * sst + c] = v[u];
+        }
+      }
     }
   }
+  // j0 > 0: a later panel of a blocked LU (steps j0 .. j0 + steps - 1 on the
+  // columns passed here); positions, pivot steps and the occupants of
+  // positions 0 .. npos - 1 come from the previous panel's launch
   for (int r = tid; r < rp; r += NT) {
-    lpos[r] = (int32_t)(r0 + r);
-    lstep[r] = -1;
+    lpos[r] = (j0 > 0 && r < nr) ? pos_out[r0 + r] : (int32_t)(r0 + r);
+    lstep[r] = (j0 > 0 && r < nr) ? pstep_out[r0 + r] : -1;
     ldone[r] = -1;
   }
-  for (int t = tid; t < steps; t += NT) pwin[t] = t;
+  for (int t = tid; t < npos; t += NT) pwin[t] = j0 > 0 ? (int32_t)perm_out[t] : t;
   if (tid == 0) s_stop = 0;
   __syncthreads();
 
@@ -242,14 +276,15 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
         s_zero = zero ? 1 : 0;
         if (zero && blockIdx.x == 0) set_flag(status, FLAG_ZERO_PIVOT);
         s_rpiv = zero ? zero_<T>() : recip(ub[0]);
-        // getf2 swap of positions j and wpos
-        const int occ = pwin[j];
-        pwin[j] = w;
-        if (wpos < steps) pwin[wpos] = occ;
+        // getf2 swap of positions jg = j0 + j and wpos
+        const int jg = j0 + j;
+        const int occ = pwin[jg];
+        pwin[jg] = w;
+        if (wpos < npos) pwin[wpos] = occ;
         if (occ != w && occ >= r0 && occ < r0 + nr) lpos[occ - r0] = wpos;
         if (w >= r0 && w < r0 + nr) {
-          lpos[w - r0] = j;
-          lstep[w - r0] = j;
+          lpos[w - r0] = jg;
+          lstep[w - r0] = jg;
         }
       }
       __syncwarp();
@@ -296,6 +331,7 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
       unsigned long long bv = 0ull;
       int bp = 0x7fffffff, br = -1;
       for (int r = tw; r < nr; r += NTW) {
+        if (lstep[r] >= 0) continue;  // pivoted by an earlier panel
         const unsigned long long v = mag_key(at(r, 0));
         const int p = lpos[r];
         if (cand_better(v, p, bv, bp)) { bv = v; bp = p; br = r; }
@@ -367,7 +403,10 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
       if (flush && c0 < cols) {
         if (SMEM) {
           const T* ub = ring + (size_t)(j % RU) * cols;
-          if (!zero) {
+          const int width = cols - c0;
+          const int tot = nr * width;
+          if (!zero && width >= 32) {
+            // a warp per row, lanes along the row
             for (int r = wk; r < nr; r += NWK) {
               if (lstep[r] < 0 && r != rstar) {
                 const T lv = -lj[r];
@@ -375,6 +414,25 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
                   T& x = at(r, c);
                   x = mad(lv, ub[c - j], x);
                 }
+              }
+            }
+          } else if (!zero && tot > 0) {
+            // narrow blocks (panels of a blocked LU): a flat loop over (row,
+            // column) keeps every lane busy (an FP64 instruction costs the
+            // same issue time whatever its active lanes); (r, c) advance
+            // without divisions
+            const int dr = NTW / width, dc = NTW - dr * width;
+            int r = tw / width, c = tw - r * width;
+            for (int e = tw; e < tot; e += NTW) {
+              if (lstep[r] < 0 && r != rstar) {
+                T& x = at(r, c0 + c);
+                x = mad(-lj[r], ub[c0 + c - j], x);
+              }
+              r += dr;
+              c += dc;
+              if (c >= width) {
+                c -= width;
+                ++r;
               }
             }
           }
@@ -413,12 +471,10 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
 
   // write back
   if (SMEM) {
-    if (row_fast) {
-      for (int c = warp; c < cols; c += NW)
-        for (int r = lane; r < nr; r += 32) xref(X, rs, cs, r0 + r, c) = slab[(size_t)r * cols + c];
-    } else {
-      for (int r = warp; r < nr; r += NW)
-        for (int c = lane; c < cols; c += 32) xref(X, rs, cs, r0 + r, c) = slab[(size_t)r * cols + c];
+    for (int e = tid; e < nr * cols; e += NT) {
+      int r, c;
+      slab_rc(e, r, c);
+      xref(X, rs, cs, r0 + r, c) = slab[(size_t)r * sst + c];
     }
   }
   for (int r = tid; r < nr; r += NT) {
@@ -428,31 +484,35 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
   }
 }
 
+// Dynamic shared memory of the shared-memory variant (the per-block maximum is
+// 227 KB, less the kernel's few hundred bytes of static shared memory).
+constexpr size_t kSmemSlabBudget = 225 * 1024;
+
 // Shared memory: the slab (shared-memory variant), D + 1 pivot rows, D columns
 // of multipliers, and per-row position, pivot step and watermark.
 template <typename T, bool SMEM>
-static size_t pivlu_smem(int64_t rpc, int cols, int steps, int D) {
-  size_t b = (SMEM ? (size_t)rpc * cols * sizeof(T) : 0) + (size_t)(D + 1) * cols * sizeof(T) +
-             (size_t)D * rpc * sizeof(T) + (size_t)rpc * 12 + (size_t)steps * 4;
+static size_t pivlu_smem(int64_t rpc, int cols, int npos, int D) {
+  size_t b = (SMEM ? (size_t)rpc * (cols | 1) * sizeof(T) : 0) + (size_t)(D + 1) * cols * sizeof(T) +
+             (size_t)D * rpc * sizeof(T) + (size_t)rpc * 12 + (size_t)npos * 4;
   return (b + 15) & ~(size_t)15;
 }
 
 // Deferral depth of the global-memory variant: up to 16 steps per pass over
 // the trailing block, as many as fit in the shared-memory budget.
 template <typename T>
-static int pivlu_defer(int64_t rpc, int cols, int steps, size_t budget) {
+static int pivlu_defer(int64_t rpc, int cols, int npos, size_t budget) {
   int D = 16;
-  while (D > 1 && pivlu_smem<T, false>(rpc, cols, steps, D) > budget) --D;
+  while (D > 1 && pivlu_smem<T, false>(rpc, cols, npos, D) > budget) --D;
   return D;
 }
 
 template <typename T, bool SMEM>
-static int launch_cfg(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int steps, int G, PivLuWs& ws,
-                      unsigned int* status, cudaStream_t st) {
+static int launch_cfg(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int steps, int j0, int npos, int G,
+                      PivLuWs& ws, unsigned int* status, cudaStream_t st) {
   constexpr int NT = SMEM ? 256 : 1024;
   const int64_t rpc = cdiv(rows, G);
-  int defer = SMEM ? 1 : pivlu_defer<T>(rpc, cols, steps, 200 * 1024);
-  size_t smem = pivlu_smem<T, SMEM>(rpc, cols, steps, defer);
+  int defer = SMEM ? 1 : pivlu_defer<T>(rpc, cols, npos, 200 * 1024);
+  size_t smem = pivlu_smem<T, SMEM>(rpc, cols, npos, defer);
   auto kern = k_pivoted_lu<T, SMEM, NT>;
   if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
   int per_sm = 0;
@@ -462,7 +522,7 @@ static int launch_cfg(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int 
   Cand* cand = reinterpret_cast<Cand*>(ws.cand);
   T* candrow = reinterpret_cast<T*>(ws.candrow);
   void* args[] = {&X, &rows, &cols, &rs, &cs, &steps, (void*)&rpc, &ws.pos, &ws.pstep, &ws.perm,
-                  &cand, &candrow, &ws.bar, &status, &defer};
+                  &cand, &candrow, &ws.bar, &status, &defer, &j0, &npos};
   RLU_CUDA_TRY(launch_cooperative((void*)kern, G, NT, args, smem, st));
   note_launch();
   return RLU_OK;
@@ -470,17 +530,32 @@ static int launch_cfg(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int 
 
 size_t pivlu_cand_bytes(int max_ctas) { return (size_t)2 * max_ctas * sizeof(Cand); }
 
+// One CTA per SM, or fewer for small inputs (at least 8 rows per CTA).
+static int pivlu_grid(int64_t rows, const PivLuWs& ws, int num_sms) {
+  int G = (int)min64(num_sms, cdiv(rows, 8));
+  return G > ws.max_ctas ? ws.max_ctas : G;
+}
+
 template <typename T>
 int launch_pivoted_lu(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int steps, PivLuWs& ws,
                       unsigned int* status, int num_sms, cudaStream_t st) {
-  if (steps > cols || steps > rows || cols > ws.max_cols) return RLU_EINVAL;
-  // one CTA per SM, or fewer for small inputs (at least 8 rows per CTA)
-  int G = (int)min64(num_sms, cdiv(rows, 8));
-  if (G > ws.max_ctas) G = ws.max_ctas;
+  return launch_pivoted_lu_panel<T>(X, rows, cols, rs, cs, steps, 0, steps, ws, status, num_sms, st);
+}
+
+template <typename T>
+int launch_pivoted_lu_panel(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int steps, int j0, int npos,
+                            PivLuWs& ws, unsigned int* status, int num_sms, cudaStream_t st) {
+  if (steps > cols || j0 < 0 || j0 + steps > npos || npos > rows || cols > ws.max_cols) return RLU_EINVAL;
+  const int G = pivlu_grid(rows, ws, num_sms);
   const int64_t rpc = cdiv(rows, G);
-  size_t smem = pivlu_smem<T, true>(rpc, cols, steps, 1);
-  if (smem <= 200 * 1024) return launch_cfg<T, true>(X, rows, cols, rs, cs, steps, G, ws, status, st);
-  return launch_cfg<T, false>(X, rows, cols, rs, cs, steps, G, ws, status, st);
+  size_t smem = pivlu_smem<T, true>(rpc, cols, npos, 1);
+  if (smem <= kSmemSlabBudget) return launch_cfg<T, true>(X, rows, cols, rs, cs, steps, j0, npos, G, ws, status, st);
+  return launch_cfg<T, false>(X, rows, cols, rs, cs, steps, j0, npos, G, ws, status, st);
+}
+
+bool pivlu_panel_in_smem(int64_t rows, int cols, int npos, const PivLuWs& ws, int num_sms) {
+  const int G = pivlu_grid(rows, ws, num_sms);
+  return pivlu_smem<double, true>(cdiv(rows, G), cols, npos, 1) <= kSmemSlabBudget;
 }
 
 template int launch_pivoted_lu<double>(double*, int64_t, int, int64_t, int64_t, int, PivLuWs&, unsigned int*, int,
@@ -489,5 +564,7 @@ template int launch_pivoted_lu<float>(float*, int64_t, int, int64_t, int64_t, in
                                       cudaStream_t);
 template int launch_pivoted_lu<df32>(df32*, int64_t, int, int64_t, int64_t, int, PivLuWs&, unsigned int*, int,
                                      cudaStream_t);
+template int launch_pivoted_lu_panel<double>(double*, int64_t, int, int64_t, int64_t, int, int, int, PivLuWs&,
+                                             unsigned int*, int, cudaStream_t);
 
 }  // namespace rlu

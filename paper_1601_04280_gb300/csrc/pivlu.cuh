@@ -23,4 +23,17 @@ template <typename T>
 int launch_pivoted_lu(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int steps, PivLuWs& ws,
                       unsigned int* status, int num_sms, cudaStream_t st);
 
+// One panel of a blocked LU: elimination steps j0 .. j0 + steps - 1 on the
+// `cols` columns at X (column j0 of the whole matrix), over every row; rows
+// pivoted by earlier panels (ws.pstep >= 0) are neither candidates nor
+// updated.  Positions 0 .. npos - 1 are tracked (npos = the whole LU's
+// steps); for j0 > 0 ws.pos, ws.pstep and ws.perm hold the state the previous
+// panel left, and on return the state after this panel.
+template <typename T>
+int launch_pivoted_lu_panel(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int steps, int j0, int npos,
+                            PivLuWs& ws, unsigned int* status, int num_sms, cudaStream_t st);
+
+// Whether the panel kernel keeps a rows x cols panel in shared memory.
+bool pivlu_panel_in_smem(int64_t rows, int cols, int npos, const PivLuWs& ws, int num_sms);
+
 }  // namespace rlu
