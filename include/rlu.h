@@ -325,17 +325,20 @@ int rlu_debug_wait_timeout(int which, int* status);
  * Errors: RLU_EINVAL, RLU_ENOMEM, RLU_ECUDA. */
 int rlu_debug_alu_peak(int which, double* tflops);
 
-/* Test and measurement hook: how step 3 (P Y = L_Y U_Y, Algorithm 1) runs.
- * block = 0 (default): blocked in panels of 64, 32 or 16 columns when the
- * unblocked kernel cannot keep Y in shared memory and l >= 32 (the widest
- * panel whose rows fit the panel kernel's shared memory, at least two
- * panels), else one unblocked kernel;
- * -1: always the unblocked kernel; 16, 32, 64: that panel width.  The blocked
- * form makes the same pivot choices as the unblocked one wherever rounding
- * does not decide them (its trailing updates are FP64-accurate products on
- * the tensor cores, summed in another order).
+/* Test and measurement hook: how the two pivoted LUs run — step 3
+ * (P Y = L_Y U_Y, m x l) and step 6 (partial pivoting of B^T, n x k) of
+ * Algorithm 1.  block = 0 (default): each is blocked in panels of 64, 32 or
+ * 16 columns when the unblocked kernel cannot keep its matrix in shared
+ * memory and it has at least 32 columns (the widest panel whose rows fit the
+ * panel kernel's shared memory with one CTA per SM, at least two panels),
+ * else one unblocked kernel; -1: always the unblocked kernel; 16, 32, 64:
+ * that panel width for both.  The choice depends only on the sizes and the
+ * SM count.  The blocked form makes the same pivot choices as the unblocked
+ * one wherever rounding does not decide them: its trailing updates are exact
+ * digit products on the tensor cores (56 bits), subtracted in the LU's own
+ * arithmetic (FP64 for Y and in FP64 mode, float-float for B otherwise).
  * Errors: RLU_EINVAL (null handle, other values, a width above
- * rlu_debug_lu_block's maximum or >= l). */
+ * rlu_debug_lu_block's maximum or >= k). */
 int rlu_debug_set_lu_block(rlu_t h, int32_t block);
 
 /* Test hook: the result of step 3 of the last factorization — Y (m x l,

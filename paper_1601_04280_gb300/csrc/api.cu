@@ -230,7 +230,7 @@ Sizes plan_sizes(int64_t m, int64_t n, int k, int l, int l1, int num_sms) {
   s.add(ltc_workspace_bytes(m, k));                  // tensor-core L = L_y L_b: digit planes
   s.add(sizeof(int64_t) * kScanMaxParts);            // multi-CTA scan partials
   s.add(l1 <= kDirectMaxL1 ? sizeof(float) * l1 * l : 0);  // CSR sketch: table of D H R / sqrt(l1)
-  s.add(blu_workspace_bytes(m, l, num_sms));         // blocked LU of Y: digit planes of the trailing updates
+  s.add(blu_workspace_bytes(m, n, k, l, num_sms));   // blocked LUs of Y and B^T: digit planes of the trailing updates
   return s;
 }
 
@@ -493,11 +493,11 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   // step 6: B Q = L_b U_b as partial pivoting of B^T
   h->pw.perm = h->perm_b;
   if (f64)
-    rc = launch_pivoted_lu<double>(reinterpret_cast<double*>(h->B), n, k, 1, n, k, h->pw, h->status_dev,
-                                   coop_sms(h), st);
+    rc = launch_lu_b<double>(reinterpret_cast<double*>(h->B), n, k, h->pw, h->blu, h->lu_block, h->status_dev,
+                             coop_sms(h), st);
   else
-    rc = launch_pivoted_lu<df32>(reinterpret_cast<df32*>(h->B), n, k, 1, n, k, h->pw, h->status_dev, coop_sms(h),
-                                 st);
+    rc = launch_lu_b<df32>(reinterpret_cast<df32*>(h->B), n, k, h->pw, h->blu, h->lu_block, h->status_dev,
+                           coop_sms(h), st);
   if (rc) return rc;
   if ((rc = mark(h, 8, st))) return rc;
   // step 7: L = L_y L_b, U = U_b, p, q
@@ -575,11 +575,11 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Bdbg, h->B, 8 * (size_t)k * n, cudaMemcpyDeviceToDevice, st));
   h->pw.perm = h->perm_b;
   if (f64)
-    rc = launch_pivoted_lu<double>(reinterpret_cast<double*>(h->B), n, k, 1, n, k, h->pw, h->status_dev,
-                                   coop_sms(h), st);
+    rc = launch_lu_b<double>(reinterpret_cast<double*>(h->B), n, k, h->pw, h->blu, h->lu_block, h->status_dev,
+                             coop_sms(h), st);
   else
-    rc = launch_pivoted_lu<df32>(reinterpret_cast<df32*>(h->B), n, k, 1, n, k, h->pw, h->status_dev, coop_sms(h),
-                                 st);
+    rc = launch_lu_b<df32>(reinterpret_cast<df32*>(h->B), n, k, h->pw, h->blu, h->lu_block, h->status_dev,
+                           coop_sms(h), st);
   if (rc) return rc;
   if ((rc = mark(h, 8, st))) return rc;
   AssembleArgs aa{};
@@ -726,7 +726,7 @@ static int create_common(int64_t m, int64_t n, int32_t k, int32_t l, int32_t l1,
   h->fjl_table = (float*)next();
   void* blubase = next();
   if (tc_setup(h->tcw, tcbase, m, n, k, sms) != RLU_OK || ltc_setup(h->ltc, ltcbase, m, k, sms) != RLU_OK ||
-      blu_setup(h->blu, blubase, m, l, sms) != RLU_OK) {
+      blu_setup(h->blu, blubase, m, n, k, l, sms) != RLU_OK) {
     rlu_destroy(h);
     return RLU_ECUDA;
   }
@@ -863,7 +863,7 @@ int rlu_set_precision(rlu_t h, int prec) {
 int rlu_debug_set_lu_block(rlu_t h, int32_t block) {
   if (!h) return RLU_EINVAL;
   if (block != -1 && block != 0 && block != 16 && block != 32 && block != 64) return RLU_EINVAL;
-  if (block > 0 && (!h->blu.ready || block > h->blu.bmax || block >= h->l)) return RLU_EINVAL;
+  if (block > 0 && (!h->blu.ready || block > h->blu.bmax || block >= h->k)) return RLU_EINVAL;
   h->lu_block = block;
   return RLU_OK;
 }

@@ -113,41 +113,82 @@ __device__ __forceinline__ double i64_scaled(long long t, int E) {
   return __longlong_as_double((long long)(bits | neg));
 }
 
-// U12 = L11^{-1} A12 for the panel's pivot rows (positions j0 .. j0 + B - 1),
-// written back into Y, and the digit planes of U12^T (row c = column c of the
-// trailing block) with their scales.  One warp per trailing column.
-template <int B>
-__global__ void __launch_bounds__(256) k_u12(double* __restrict__ Y, int l, int j0, int w,
+// The digits and scale of a float-float value: the same balanced form from
+// the top (first digit rint(x 2^(7 - e)) in [-128, 128], the next ones in
+// [-64, 64]), every step exact in FP32.
+__device__ __forceinline__ void digits8(df32 x, int e, int (&d)[kD]) {
+  float yh = ldexpf(x.hi, 7 - e), yl = ldexpf(x.lo, 7 - e);
+#pragma unroll
+  for (int s = 0; s < kD; ++s) {
+    const float t = rintf(yh);
+    d[s] = (int)t;
+    const df32 r = two_sum(yh - t, yl);
+    yh = r.hi * 128.f;
+    yl = r.lo * 128.f;
+  }
+}
+__device__ __forceinline__ int exp_of(df32 x) {
+  const int ex = (int)((__float_as_uint(x.hi) >> 23) & 0xff);
+  return (ex == 0 || ex == 0xff) ? kNoExp : ex - 126;
+}
+
+// t 2^E as a float-float: t in three 24-bit pieces (each exact in FP32),
+// summed with TwoSum, scaled by 2^E.  FP32 and integer operations only.
+__device__ __forceinline__ df32 i64_scaled_df(long long t, int E) {
+  const float fa = (float)(int)(t >> 48) * 0x1p48f;
+  const float fb = (float)(int)((t >> 24) & 0xFFFFFF) * 0x1p24f;
+  const float fc = (float)(int)(t & 0xFFFFFF);
+  const df32 s = two_sum(fa, fb) + df_make(fc, 0.f);
+  return df_make(ldexpf(s.hi, E), ldexpf(s.lo, E));
+}
+
+__device__ __forceinline__ double scaled_product(long long t, int E, double) { return i64_scaled(t, E); }
+__device__ __forceinline__ df32 scaled_product(long long t, int E, df32) { return i64_scaled_df(t, E); }
+__device__ __forceinline__ double sub(double y, double c) { return y - c; }
+__device__ __forceinline__ df32 sub(df32 y, df32 c) { return y - c; }
+__device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ df32 shfl(df32 v, int src) {
+  return df_make(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
+template <typename T> __device__ __forceinline__ T zero_v() { return T(0); }
+template <> __device__ __forceinline__ df32 zero_v<df32>() { return df_make(0.f, 0.f); }
+
+// U12 = L11^{-1} A12 for the panel's pivot rows (positions j0 .. j0 + B - 1)
+// of X (element (i, c) at X[i rs + c cs]), written back into X, and the digit
+// planes of U12^T (row c = trailing column j0 + B + c) with their scales.
+// One warp per trailing column.
+template <int B, typename T>
+__global__ void __launch_bounds__(256) k_u12(T* __restrict__ X, int64_t rs, int64_t cs, int j0, int w,
                                              const int64_t* __restrict__ perm, __nv_bfloat16* __restrict__ bdig,
                                              int32_t* __restrict__ bexp) {
   constexpr int KC = chunk_of(B);
   constexpr int R = (B + 31) / 32;
-  __shared__ double LT[B][B + 1];  // LT[i][t] = L11[t][i] (t > i), the multiplier of pivot row t at panel column i
+  __shared__ T LT[B][B + 1];  // LT[i][t] = L11[t][i] (t > i), the multiplier of pivot row t at panel column i
   __shared__ int64_t prow[B];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int t = tid; t < B; t += blockDim.x) prow[t] = perm[j0 + t];
   __syncthreads();
   for (int e = tid; e < B * B; e += blockDim.x) {
     const int t = e / B, i = e - t * B;
-    LT[i][t] = (i < t) ? Y[prow[t] * l + j0 + i] : 0.0;
+    LT[i][t] = (i < t) ? X[prow[t] * rs + (int64_t)(j0 + i) * cs] : zero_v<T>();
   }
   __syncthreads();
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
   if (c >= w) return;
-  const int64_t col = (int64_t)j0 + B + c;
-  double a[R];
+  const int64_t col = ((int64_t)j0 + B + c) * cs;
+  T a[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int t = lane + 32 * r;
-    a[r] = (t < B) ? Y[prow[t < B ? t : 0] * l + col] : 0.0;
+    a[r] = (t < B) ? X[prow[t < B ? t : 0] * rs + col] : zero_v<T>();
   }
 #pragma unroll
   for (int i = 0; i < B; ++i) {
-    const double ui = __shfl_sync(0xffffffffu, a[i / 32], i % 32);
+    const T ui = shfl(a[i / 32], i % 32);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int t = lane + 32 * r;
-      if (t > i && t < B) a[r] = fma(-LT[i][t], ui, a[r]);
+      if (t > i && t < B) a[r] = mad(-LT[i][t], ui, a[r]);
     }
   }
   int e = kNoExp;
@@ -155,7 +196,7 @@ __global__ void __launch_bounds__(256) k_u12(double* __restrict__ Y, int l, int 
   for (int r = 0; r < R; ++r) {
     const int t = lane + 32 * r;
     if (t < B) {
-      Y[prow[t] * l + col] = a[r];
+      X[prow[t] * rs + col] = a[r];
       e = max(e, exp_of(a[r]));
     }
   }
@@ -177,10 +218,10 @@ __global__ void __launch_bounds__(256) k_u12(double* __restrict__ Y, int l, int 
 }
 
 // Digit planes of the multipliers L21 (panel columns j0 .. j0 + B - 1) of
-// every row with their scales; rows already pivoted get zero digits and the
-// skip mark.  One warp per row.
-template <int B>
-__global__ void __launch_bounds__(256) k_l21(const double* __restrict__ Y, int64_t m, int l, int j0,
+// every row of X with their scales; rows already pivoted get zero digits and
+// the skip mark.  One warp per row.
+template <int B, typename T>
+__global__ void __launch_bounds__(256) k_l21(const T* __restrict__ X, int64_t rs, int64_t cs, int64_t m, int j0,
                                              const int32_t* __restrict__ pstep, __nv_bfloat16* __restrict__ adig,
                                              int32_t* __restrict__ aexp) {
   constexpr int KC = chunk_of(B);
@@ -189,12 +230,12 @@ __global__ void __launch_bounds__(256) k_l21(const double* __restrict__ Y, int64
   const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (r >= m) return;
   const bool skip = pstep[r] >= 0;
-  double x[R];
+  T x[R];
   int e = kNoExp;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const int i = lane + 32 * q;
-    x[q] = (!skip && i < B) ? Y[r * l + j0 + i] : 0.0;
+    x[q] = (!skip && i < B) ? X[r * rs + (int64_t)(j0 + i) * cs] : zero_v<T>();
     e = max(e, exp_of(x[q]));
   }
   e = __reduce_max_sync(0xffffffffu, e);
@@ -214,16 +255,18 @@ __global__ void __launch_bounds__(256) k_l21(const double* __restrict__ Y, int64
   }
 }
 
-// Y[row][c] -= (L21 U12)[row][c] for the M x N trailing block at Y (row
-// stride ldy) from the packed digit planes (nch chunks of KC columns).
-// Persistent: CTA b takes tiles b, b + gridDim.x, ... (128 rows x 32
-// columns, column tile fastest); a ring of nst stages runs across tiles; two
-// accumulator sets let the epilogue of one tile overlap the MMAs of the next.
-template <int KC>
+// X(i, c) -= (L21 U12)(i, c) for the M x N trailing block whose element
+// (i, c) sits at X[i rs + c cs] (FP64 or float-float), from the packed digit
+// planes (nch chunks of KC columns).  Persistent: CTA b takes tiles b,
+// b + gridDim.x, ... (128 rows x 32 columns, column tile fastest); a ring of
+// nst stages runs across tiles; two accumulator sets let the epilogue of one
+// tile overlap the MMAs of the next.
+template <int KC, typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_digit_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t M,
                    int N, int nch, int nt, int64_t tiles, int nst, const int32_t* __restrict__ aexp,
-                   const int32_t* __restrict__ bexp, double* __restrict__ Y, int64_t ldy, unsigned int* status) {
+                   const int32_t* __restrict__ bexp, T* __restrict__ X, int64_t rs, int64_t cs,
+                   unsigned int* status) {
   constexpr int NBOX = kD * KC / 64;
   constexpr uint32_t ABOX = kBM * 128, BBOX = kNT * 128;
   constexpr uint32_t SB = stage_bytes<KC>();
@@ -329,23 +372,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       // this thread's 16 entries of A22 and the column scales, loaded while
       // the tile's products are still being computed
       const int ea = row < M ? aexp[row] : kSkip;
-      double* yr = Y + row * ldy;
-      double y[16];
+      T* xr = X + row * rs;
+      T y[16];
       int eb[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int c = cb + i;
         const bool on = ea != kSkip && c < N;
-        y[i] = on ? yr[c] : 0.0;
+        y[i] = on ? xr[(int64_t)c * cs] : zero_v<T>();
         eb[i] = on ? ea + bexp[c] - 56 : 0;
       }
       if (!tc::mbar_wait(&tfull[b], (uint32_t)((local >> 1) & 1))) { s_fail = 1; break; }
       tc::tc_fence_after();
       const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * SET + (uint32_t)(half * 16);
-      // T = sum_{v <= 6} L_v 128^(6 - v) + floor(L_7 / 128): the product in
+      // P = sum_{v <= 6} L_v 128^(6 - v) + floor(L_7 / 128): the product in
       // units of 2^-56 of the two scales (|T| < 2^62.1 for b <= 64); the
       // levels come in two batches of four loads with one wait each
-      long long T[16];
+      long long P[16];
       uint32_t v[4][16];
 #pragma unroll
       for (int g = 0; g < 2; ++g) {
@@ -358,9 +401,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const int L = level_int(__uint_as_float(v[q][i]));
-            if (lv == 0) T[i] = L;
-            else if (lv < kD - 1) T[i] = T[i] * 128 + L;
-            else T[i] += (long long)(L >> 7);
+            if (lv == 0) P[i] = L;
+            else if (lv < kD - 1) P[i] = P[i] * 128 + L;
+            else P[i] += (long long)(L >> 7);
           }
         }
       }
@@ -370,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (ea != kSkip) {
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-          if (cb + i < N) yr[cb + i] = y[i] - i64_scaled(T[i], eb[i]);
+          if (cb + i < N) xr[(int64_t)(cb + i) * cs] = sub(y[i], scaled_product(P[i], eb[i], y[i]));
       }
     }
   }
@@ -383,86 +426,146 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0 && s_fail) set_flag(status, FLAG_TIMEOUT);
 }
 
-template <int KC>
-int launch_update(const BluWs& w, int wi, int64_t M, int N, int nch, double* Yt, int64_t ldy, unsigned int* status,
-                  cudaStream_t st) {
+template <int KC, typename T>
+int launch_update(const BluWs& w, int wi, int64_t M, int N, int nch, T* Xt, int64_t rs, int64_t cs,
+                  unsigned int* status, cudaStream_t st) {
   constexpr uint32_t SB = stage_bytes<KC>();
   const int nst = (int)min64(kMaxStages, (int64_t)(200 * 1024) / SB);
   const size_t smem = (size_t)nst * SB + 1024;
-  auto kern = k_digit_update<KC>;
+  auto kern = k_digit_update<KC, T>;
   if (int rc = allow_dynamic_smem((const void*)kern, smem)) return rc;
   const int nt = (int)cdiv(N, kNT);
   const int64_t tiles = cdiv(M, kBM) * nt;
   const unsigned grid = (unsigned)min64(tiles, (int64_t)w.num_sms);
   kern<<<grid, kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap*>(w.mapA[wi]),
                                      *reinterpret_cast<const CUtensorMap*>(w.mapB[wi]), M, N, nch, nt, tiles, nst,
-                                     w.aexp, w.bexp, Yt, ldy, status);
+                                     w.aexp, w.bexp, Xt, rs, cs, status);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
   return RLU_OK;
 }
 
-template <int B>
-int trailing(double* Y, int64_t m, int l, int j0, const PivLuWs& pw, const BluWs& w, unsigned int* status,
-             cudaStream_t st) {
-  const int wt = l - j0 - B;
-  k_u12<B><<<(unsigned)cdiv(wt, 8), 256, 0, st>>>(Y, l, j0, wt, pw.perm, w.bdig, w.bexp);
+// The trailing update after the panel at column j0 (width B) of the rows x
+// cols matrix X (element (i, c) at X[i rs + c cs]).
+template <int B, typename T>
+int trailing(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int j0, const PivLuWs& pw, const BluWs& w,
+             unsigned int* status, cudaStream_t st) {
+  const int wt = cols - j0 - B;
+  k_u12<B, T><<<(unsigned)cdiv(wt, 8), 256, 0, st>>>(X, rs, cs, j0, wt, pw.perm, w.bdig, w.bexp);
   RLU_CUDA_TRY(cudaGetLastError());
-  k_l21<B><<<(unsigned)cdiv(m * 32, 256), 256, 0, st>>>(Y, m, l, j0, pw.pstep, w.adig, w.aexp);
+  k_l21<B, T><<<(unsigned)cdiv(rows * 32, 256), 256, 0, st>>>(X, rs, cs, rows, j0, pw.pstep, w.adig, w.aexp);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch(2);
   constexpr int KC = chunk_of(B);
-  return launch_update<KC>(w, width_index(B), m, wt, B / KC, Y + j0 + B, l, status, st);
+  return launch_update<KC, T>(w, width_index(B), rows, wt, B / KC, X + (int64_t)(j0 + B) * cs, rs, cs, status, st);
 }
 
 // Widest panel whose rows fit the panel kernel's shared memory with `ctas` CTAs.
-int widest_fit(int64_t m, int l, int ctas, int cap) {
+int widest_fit(int64_t rows, int cols, int ctas, int cap) {
   PivLuWs probe{};
   probe.max_ctas = 1 << 20;
-  probe.max_cols = l;
+  probe.max_cols = cols;
   for (int b : kBluWidths)
-    if (b <= cap && b < l && pivlu_panel_in_smem(m, b, l, probe, ctas)) return b;
+    if (b <= cap && b < cols && pivlu_panel_in_smem(rows, b, cols, probe, ctas)) return b;
   return 0;
+}
+
+// Panel width for the rows x cols LU: `block` forced (> 0), unblocked (-1),
+// or chosen (0).  The form and the width depend only on the sizes and the
+// device's SM count, never on a bound on the grid (coop_sms): results stay
+// bit-for-bit the same under rlu_set_max_ctas (a panel whose rows no longer
+// fit in shared memory runs the kernel's global-memory form, which performs
+// the same operations in the same order).  Returns -1 for an invalid block.
+int choose_width(int64_t rows, int cols, const PivLuWs& pw, const BluWs& bw, int block, int coop_sms) {
+  const int sms = bw.num_sms > 0 ? bw.num_sms : coop_sms;
+  if (block > 0) {
+    if ((block != 16 && block != 32 && block != 64) || !bw.ready || block > bw.bmax || block >= cols ||
+        rows > bw.rows_a)
+      return -1;
+    return block;
+  }
+  if (block < 0 || !bw.ready || cols < 32 || rows > bw.rows_a || pivlu_panel_in_smem(rows, cols, cols, pw, sms))
+    return 0;
+  // blocked when the unblocked kernel could not keep the matrix in shared
+  // memory (its global-memory form is bound by the trailing updates); a
+  // matrix that fits is bound by the per-step exchange, which blocking does
+  // not shorten
+  int b = widest_fit(rows, cols, (int)min64(sms, pw.max_ctas), bw.bmax);
+  while (b > 16 && 2 * b > cols) b /= 2;
+  return b;
+}
+
+template <typename T>
+int blocked_lu(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int b, PivLuWs& pw, const BluWs& bw,
+               unsigned int* status, int coop_sms, cudaStream_t st) {
+  for (int j0 = 0; j0 < cols; j0 += b) {
+    const int wid = cols - j0 < b ? cols - j0 : b;
+    int rc = launch_pivoted_lu_panel<T>(X + (int64_t)j0 * cs, rows, wid, rs, cs, wid, j0, cols, pw, status,
+                                        coop_sms, st);
+    if (rc) return rc;
+    if (cols - j0 - wid == 0) break;
+    switch (b) {
+      case 64: rc = trailing<64, T>(X, rows, cols, rs, cs, j0, pw, bw, status, st); break;
+      case 32: rc = trailing<32, T>(X, rows, cols, rs, cs, j0, pw, bw, status, st); break;
+      default: rc = trailing<16, T>(X, rows, cols, rs, cs, j0, pw, bw, status, st); break;
+    }
+    if (rc) return rc;
+  }
+  return RLU_OK;
 }
 
 }  // namespace blu
 
 namespace {
 constexpr size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
-int blu_bmax(int64_t m, int l, int num_sms) { return blu::widest_fit(m, l, num_sms, 64); }
+struct BluDims {
+  int64_t rows_a;
+  int rows_b;
+  int bmax;
+};
+BluDims blu_dims(int64_t m, int64_t n, int k, int l, int num_sms) {
+  BluDims d;
+  d.rows_a = m > n ? m : n;
+  d.rows_b = l;
+  const int by = blu::widest_fit(m, l, num_sms, 64), bb = blu::widest_fit(n, k, num_sms, 64);
+  d.bmax = by > bb ? by : bb;
+  return d;
+}
 }  // namespace
 
-size_t blu_workspace_bytes(int64_t m, int l, int num_sms) {
-  const int b = blu_bmax(m, l, num_sms);
-  if (b == 0) return 0;
-  const size_t row = (size_t)blu::kD * b * 2;
-  return a256(row * (size_t)m) + a256(row * (size_t)l) + a256(4 * (size_t)m) + a256(4 * (size_t)l);
+size_t blu_workspace_bytes(int64_t m, int64_t n, int k, int l, int num_sms) {
+  const BluDims d = blu_dims(m, n, k, l, num_sms);
+  if (d.bmax == 0) return 0;
+  const size_t row = (size_t)blu::kD * d.bmax * 2;
+  return a256(row * (size_t)d.rows_a) + a256(row * (size_t)d.rows_b) + a256(4 * (size_t)d.rows_a) +
+         a256(4 * (size_t)d.rows_b);
 }
 
-int blu_setup(BluWs& w, void* base, int64_t m, int l, int num_sms) {
+int blu_setup(BluWs& w, void* base, int64_t m, int64_t n, int k, int l, int num_sms) {
   w.ready = false;
-  w.m = m;
-  w.l = l;
   w.num_sms = num_sms;
-  w.bmax = blu_bmax(m, l, num_sms);
+  const BluDims d = blu_dims(m, n, k, l, num_sms);
+  w.rows_a = d.rows_a;
+  w.rows_b = d.rows_b;
+  w.bmax = d.bmax;
   if (w.bmax == 0) return RLU_OK;
   const size_t row = (size_t)blu::kD * w.bmax * 2;
   unsigned char* b = (unsigned char*)base;
   w.adig = (__nv_bfloat16*)b;
-  b += a256(row * (size_t)m);
+  b += a256(row * (size_t)w.rows_a);
   w.bdig = (__nv_bfloat16*)b;
-  b += a256(row * (size_t)l);
+  b += a256(row * (size_t)w.rows_b);
   w.aexp = (int32_t*)b;
-  b += a256(4 * (size_t)m);
+  b += a256(4 * (size_t)w.rows_a);
   w.bexp = (int32_t*)b;
   for (int bw : kBluWidths) {
     if (bw > w.bmax) continue;
     const int wi = blu::width_index(bw);
     const uint64_t kp = (uint64_t)blu::kD * bw;  // packed row: 8 digits of bw columns
-    if (tc_encode_bf16_3d(w.mapA[wi], w.adig, kp, (uint64_t)m, 1, kp, 64, blu::kBM) != RLU_OK ||
-        tc_encode_bf16_3d(w.mapB[wi], w.bdig, kp, (uint64_t)l, 1, kp, 64, blu::kNT) != RLU_OK) {
+    if (tc_encode_bf16_3d(w.mapA[wi], w.adig, kp, (uint64_t)w.rows_a, 1, kp, 64, blu::kBM) != RLU_OK ||
+        tc_encode_bf16_3d(w.mapB[wi], w.bdig, kp, (uint64_t)w.rows_b, 1, kp, 64, blu::kNT) != RLU_OK) {
       cudaGetLastError();
-      return RLU_OK;  // no tensor maps: the unblocked LU runs
+      return RLU_OK;  // no tensor maps: the unblocked LUs run
     }
   }
   w.ready = true;
@@ -471,38 +574,24 @@ int blu_setup(BluWs& w, void* base, int64_t m, int l, int num_sms) {
 
 int launch_lu_y(double* Y, int64_t m, int l, PivLuWs& pw, const BluWs& bw, int block, unsigned int* status,
                 int coop_sms, cudaStream_t st) {
-  // The form and the panel width depend only on the sizes and the device's SM
-  // count, never on a bound on the grid (coop_sms): results stay bit-for-bit
-  // the same under rlu_set_max_ctas (a panel whose rows no longer fit in
-  // shared memory runs the kernel's global-memory form, which performs the
-  // same operations in the same order).
-  const int sms = bw.num_sms > 0 ? bw.num_sms : coop_sms;
-  int b = 0;
-  if (block > 0) {
-    if ((block != 16 && block != 32 && block != 64) || !bw.ready || block > bw.bmax || block >= l)
-      return RLU_EINVAL;
-    b = block;
-  } else if (block == 0 && bw.ready && l >= 32 && !pivlu_panel_in_smem(m, l, l, pw, sms)) {
-    // blocked when the unblocked kernel could not keep Y in shared memory (its
-    // global-memory form is bound by the FP64 trailing updates); a Y that fits
-    // is bound by the per-step exchange, which blocking does not shorten
-    b = blu::widest_fit(m, l, min64(sms, pw.max_ctas), bw.bmax);
-    while (b > 16 && 2 * b > l) b /= 2;
-  }
+  const int b = blu::choose_width(m, l, pw, bw, block, coop_sms);
+  if (b < 0) return RLU_EINVAL;
   if (b == 0) return launch_pivoted_lu<double>(Y, m, l, l, 1, l, pw, status, coop_sms, st);
-  for (int j0 = 0; j0 < l; j0 += b) {
-    const int wid = l - j0 < b ? l - j0 : b;
-    int rc = launch_pivoted_lu_panel<double>(Y + j0, m, wid, l, 1, wid, j0, l, pw, status, coop_sms, st);
-    if (rc) return rc;
-    if (l - j0 - wid == 0) break;
-    switch (b) {
-      case 64: rc = blu::trailing<64>(Y, m, l, j0, pw, bw, status, st); break;
-      case 32: rc = blu::trailing<32>(Y, m, l, j0, pw, bw, status, st); break;
-      default: rc = blu::trailing<16>(Y, m, l, j0, pw, bw, status, st); break;
-    }
-    if (rc) return rc;
-  }
-  return RLU_OK;
+  return blu::blocked_lu<double>(Y, m, l, l, 1, b, pw, bw, status, coop_sms, st);
 }
+
+template <typename T>
+int launch_lu_b(T* B, int64_t n, int k, PivLuWs& pw, const BluWs& bw, int block, unsigned int* status,
+                int coop_sms, cudaStream_t st) {
+  // B^T (n x k): element (i, c) at B[c n + i]
+  const int b = blu::choose_width(n, k, pw, bw, block, coop_sms);
+  if (b < 0) return RLU_EINVAL;
+  if (b == 0) return launch_pivoted_lu<T>(B, n, k, 1, n, k, pw, status, coop_sms, st);
+  return blu::blocked_lu<T>(B, n, k, 1, n, b, pw, bw, status, coop_sms, st);
+}
+
+template int launch_lu_b<double>(double*, int64_t, int, PivLuWs&, const BluWs&, int, unsigned int*, int,
+                                 cudaStream_t);
+template int launch_lu_b<df32>(df32*, int64_t, int, PivLuWs&, const BluWs&, int, unsigned int*, int, cudaStream_t);
 
 }  // namespace rlu

@@ -566,5 +566,7 @@ template int launch_pivoted_lu<df32>(df32*, int64_t, int, int64_t, int64_t, int,
                                      cudaStream_t);
 template int launch_pivoted_lu_panel<double>(double*, int64_t, int, int64_t, int64_t, int, int, int, PivLuWs&,
                                              unsigned int*, int, cudaStream_t);
+template int launch_pivoted_lu_panel<df32>(df32*, int64_t, int, int64_t, int64_t, int, int, int, PivLuWs&,
+                                           unsigned int*, int, cudaStream_t);
 
 }  // namespace rlu

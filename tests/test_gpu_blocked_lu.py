@@ -128,3 +128,43 @@ def test_blocked_lu_does_not_depend_on_the_grid(rg):
     for o in outs[1:]:
         for a, b in zip(o, outs[0]):
             assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_blocked_lu_of_B(rg, prec):
+    """Step 6, B Q = L_b U_b by partial pivoting of B^T: with 45000 columns B^T
+    does not fit the unblocked kernel's shared memory, so the default runs it
+    blocked (float-float trailing updates in the FP32 form, FP64 in the FP64
+    form).  Against the unblocked kernel on the same input: the same row
+    pivots (the LU of Y is unblocked in both), the same column pivots on every
+    step the oracle separates, L and U entry by entry where all column pivots
+    agree; both within the oracle's bars."""
+    m, n, k, l, l1 = 1200, 45000, 100, 120, 960
+    A = ri.dense_low_rank_plus_noise(m, n, 110, 1e-5, seed=21, dtype=np.float64)
+    Ain = A if prec == "f64" else A.astype(np.float32)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    Ad = torch.from_numpy(np.ascontiguousarray(Ain)).to("cuda", dt)
+    res = {}
+    for block in (-1, 0):
+        h = rg.RandLU(m, n, k, l, l1, 17, prec=prec)
+        h.set_lu_block(block)
+        f = h.factor(Ad, check=False)
+        torch.cuda.synchronize()
+        res[block] = dict(L=f.L.double().cpu().numpy(), U=f.U.double().cpu().numpy(), p=f.p.cpu().numpy(),
+                          q=f.q.cpu().numpy(), status=f.status)
+        h.close()
+    u, b = res[-1], res[0]
+    assert u["status"] == 0 and b["status"] == 0
+    assert np.array_equal(u["p"], b["p"])
+    o = oracle.factor(Ain.astype(np.float64), k, l, l1, seed=17)
+    sb = separated_prefix(o.top_b, np.abs(o.B).max(), 1e-9 if prec == "f64" else 1e-4)
+    assert sb >= 1
+    assert np.array_equal(u["q"][:sb], b["q"][:sb]) and np.array_equal(b["q"][:sb], o.q[:sb])
+    if np.array_equal(u["q"], b["q"]):
+        tol = 1e-11 if prec == "f64" else 1e-6
+        assert np.abs(u["U"] - b["U"]).max() <= tol * np.abs(u["U"]).max()
+        assert np.abs(u["L"] - b["L"]).max() <= tol * np.abs(u["L"]).max()
+    e_o = oracle.relative_residual(Ain.astype(np.float64), o.L, o.U, o.p, o.q)
+    for g in (u, b):
+        e_g = oracle.relative_residual(Ain.astype(np.float64), g["L"], g["U"], g["p"], g["q"])
+        assert abs(e_g - e_o) <= (1e-12 if prec == "f64" else 1e-5), (e_g, e_o)
