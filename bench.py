@@ -56,7 +56,11 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
 # of the current kernels (profiles/top_kernels_dense_f32_8192.md: k_pivoted_lu of Y);
 # a workload without a capture of its current dominant kernel reports null.
-MEASURED_TRAFFIC = {("dense_f32_8192x8192_k200", "panel_lu"): 14491392 + 768}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant
+# kernel from an ncu capture (profiles/panel_lu_f64_200000x16.md: a 16-wide
+# panel over 200000 rows, the same launch shape as the sparse workload's
+# panels); null for workloads without a capture of the current kernel
+MEASURED_TRAFFIC = {("csr_f32_200000x50000_k100", "panel_lu"): 25674496 + 77568}
 
 # FP64 vector peak from unit counts, used only when the measurement below is
 # unavailable: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz = 1.259 TFLOP/s.
@@ -238,6 +242,21 @@ def algorithmic_flops_panel_lu(m, l):
     return sum(2.0 * (m - j - 1) * (l - j - 1) + (m - j - 1) for j in range(l))
 
 
+def lu_panels(l, b):
+    """(first column, width) of the pivoted-LU kernel's launches: one over all
+    l columns when unblocked (b = 0), else panels of b columns."""
+    return [(0, l)] if b == 0 else [(j0, min(b, l - j0)) for j0 in range(0, l, b)]
+
+
+def algorithmic_flops_lu_panels(m, l, b):
+    """FP64 work of the pivoted-LU kernel's launches for the m x l LU with panel
+    width b: each panel's own elimination (the unblocked count on the rows not
+    yet pivoted and the panel's columns); the trailing updates between panels
+    run in other kernels, on the tensor cores."""
+    return sum(2.0 * (m - j0 - j - 1) * (wid - j - 1) + (m - j0 - j - 1)
+               for j0, wid in lu_panels(l, b) for j in range(wid))
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -412,11 +431,14 @@ def main():
     # per-stage device times (events on the same stream between the stages)
     h.debug_timing(True)
     stage_acc = {}
+    panel_ms = 0.0
     reps = min(args.steps, 10)
     for _ in range(reps):
         factor()
         for kname, v in h.debug_stage_ms().items():
             stage_acc[kname] = stage_acc.get(kname, 0.0) + v / reps
+        panel_width, panel_launches, pms = h.debug_lu_panels(0)
+        panel_ms += pms / reps
     h.debug_timing(False)
 
     # end to end through the public API with pinned host buffers: H2D of the
@@ -519,9 +541,21 @@ def main():
         dom = max(stage_acc, key=stage_acc.get)
         roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": MEASURED_TRAFFIC.get((args.workload, dom)) if prec == prec_default else None}
+        if dom == "panel_lu":
+            # the dominant kernel: the pivoted-LU kernel's launches in the LU of
+            # Y, per launch (their own FP64 work over their own event times)
+            works["panel_lu"] = (algorithmic_flops_lu_panels(m, l, panel_width) / panel_launches,
+                                 "fp64_flops", "alu")
+            roof.update(kernel="k_pivoted_lu<double> (LU of Y: %d launch%s, panel width %s)"
+                        % (panel_launches, "es" if panel_launches > 1 else "", panel_width or "l, unblocked"),
+                        launches=panel_launches, stage_ms=stage_acc[dom],
+                        note="achieved = the launch's algorithmic FP64 flop / its mean CUDA-event time; the "
+                             "blocked form's trailing updates run on the tensor cores in other kernels")
         if dom in works:
             amount, unit, bound = works[dom]
             secs = stage_acc[dom] / 1e3
+            if dom == "panel_lu":
+                secs = panel_ms / panel_launches / 1e3
             if bound == "hbm":
                 ach = amount / secs / 1e9
                 roof.update(bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",

@@ -349,6 +349,17 @@ int rlu_debug_set_lu_block(rlu_t h, int32_t block);
  * host buffers.  Synchronous.  Errors: RLU_EINVAL, RLU_ECUDA. */
 int rlu_debug_lu_Y(rlu_t h, double* Y_host, int64_t* perm_host);
 
+/* Measurement hook: the launches of the pivoted-LU kernel in the last timed
+ * factorization (rlu_debug_timing on) of LU `which` (0: step 3, the sketch
+ * Y; 1: step 6, B^T): *width = the panel width (0 when unblocked: one launch
+ * over all l or k columns), *launches = the kernel's launches, *ms = their
+ * summed device time from CUDA events recorded around each launch on the
+ * handle's stream.  The blocked form's other kernels (the U12 solve and the
+ * tensor-core trailing updates) are not included.  Synchronous.
+ * Errors: RLU_EINVAL (null argument, which not 0 or 1, timing off or no
+ * timed factorization yet), RLU_ECUDA. */
+int rlu_debug_lu_panels(rlu_t h, int which, int32_t* width, int32_t* launches, double* ms);
+
 /* The block setting of rlu_debug_set_lu_block (return value) and, in
  * *block_max (may be null), the widest panel this handle's workspace holds
  * (0: the blocked form is unavailable).  RLU_EINVAL for a null handle. */

@@ -34,7 +34,7 @@ C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_
              "rlu_graph_destroy", "rlu_copy_block_async", "rlu_set_max_ctas",
              "rlu_debug_recip", "rlu_set_second_sketch", "rlu_debug_status_of_flags", "rlu_debug_wait_timeout",
              "rlu_debug_alu_peak", "rlu_set_transform", "rlu_set_column_pivoting", "rlu_debug_set_lu_block",
-             "rlu_debug_lu_block", "rlu_debug_lu_Y")
+             "rlu_debug_lu_block", "rlu_debug_lu_Y", "rlu_debug_lu_panels")
 
 #: stage names reported by rlu_debug_stage_ms, in order
 STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
@@ -94,6 +94,8 @@ def load(reload=False):
         "rlu_debug_set_lu_block": ([vp, c.c_int32], c.c_int),
         "rlu_debug_lu_block": ([vp, c.POINTER(c.c_int32)], c.c_int),
         "rlu_debug_lu_Y": ([vp, vp, vp], c.c_int),
+        "rlu_debug_lu_panels": ([vp, c.c_int, c.POINTER(c.c_int32), c.POINTER(c.c_int32), c.POINTER(c.c_double)],
+                                c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -416,6 +418,14 @@ class RandLU:
         perm = np.empty(self.m, np.int64)
         _check(load().rlu_debug_lu_Y(self.h, Y.ctypes.data, perm.ctypes.data), "rlu_debug_lu_Y")
         return Y, perm
+
+    def debug_lu_panels(self, which=0):
+        """(panel width or 0, launches, summed ms) of the pivoted-LU kernel in the
+        last timed factorization: which = 0 the LU of Y, 1 the LU of B^T."""
+        w, n, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+        _check(load().rlu_debug_lu_panels(self.h, int(which), ctypes.byref(w), ctypes.byref(n), ctypes.byref(ms)),
+               "rlu_debug_lu_panels")
+        return int(w.value), int(n.value), float(ms.value)
 
     def debug_B(self):
         import numpy as np

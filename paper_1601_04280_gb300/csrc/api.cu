@@ -121,7 +121,8 @@ struct rlu_ctx {
   TcWs tcw{};
   LtcWs ltc{};  // digit planes of the tensor-core L = L_y L_b
   BluWs blu{};  // digit planes of the blocked LU's trailing updates
-  int lu_block = 0;  // panel width of the LU of Y: 0 automatic, -1 unblocked
+  int lu_block = 0;  // panel width of the LUs of Y and B^T: 0 automatic, -1 unblocked
+  PanelTimer ptimer[2];  // panel launch times of the two LUs (timing on)
   float* fjl_table = nullptr;  // l1 x l table of the CSR sketch's direct evaluation
   int colpiv = 0;                 // rank-revealing column order of the sketch
   void* cp_buf = nullptr;
@@ -438,7 +439,9 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Ydbg, h->Y, sizeof(double) * m * l, cudaMemcpyDeviceToDevice, st));
   // step 3: P Y = L_Y U_Y (FP64, l steps)
   h->pw.perm = h->perm_y;
-  if ((rc = launch_lu_y(h->Y, m, l, h->pw, h->blu, h->lu_block, h->status_dev, coop_sms(h), st))) return rc;
+  if ((rc = launch_lu_y(h->Y, m, l, h->pw, h->blu, h->lu_block, h->status_dev, coop_sms(h), st,
+                        h->timing ? &h->ptimer[0] : nullptr)))
+    return rc;
   if ((rc = mark(h, 3, st))) return rc;
   // W = L_y^+ P
   PinvArgs pa{};
@@ -494,10 +497,10 @@ int enqueue_dense(rlu_ctx* h, const void* A, int64_t lda, int dtype, void* L, vo
   h->pw.perm = h->perm_b;
   if (f64)
     rc = launch_lu_b<double>(reinterpret_cast<double*>(h->B), n, k, h->pw, h->blu, h->lu_block, h->status_dev,
-                             coop_sms(h), st);
+                             coop_sms(h), st, h->timing ? &h->ptimer[1] : nullptr);
   else
     rc = launch_lu_b<df32>(reinterpret_cast<df32*>(h->B), n, k, h->pw, h->blu, h->lu_block, h->status_dev,
-                           coop_sms(h), st);
+                           coop_sms(h), st, h->timing ? &h->ptimer[1] : nullptr);
   if (rc) return rc;
   if ((rc = mark(h, 8, st))) return rc;
   // step 7: L = L_y L_b, U = U_b, p, q
@@ -549,7 +552,9 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   if (h->debug && h->Ydbg)
     RLU_CUDA_TRY(cudaMemcpyAsync(h->Ydbg, h->Y, sizeof(double) * m * l, cudaMemcpyDeviceToDevice, st));
   h->pw.perm = h->perm_y;
-  if ((rc = launch_lu_y(h->Y, m, l, h->pw, h->blu, h->lu_block, h->status_dev, coop_sms(h), st))) return rc;
+  if ((rc = launch_lu_y(h->Y, m, l, h->pw, h->blu, h->lu_block, h->status_dev, coop_sms(h), st,
+                        h->timing ? &h->ptimer[0] : nullptr)))
+    return rc;
   if ((rc = mark(h, 3, st))) return rc;
   PinvArgs pa{};
   pa.m = m; pa.k = k; pa.l = l;
@@ -576,10 +581,10 @@ int enqueue_csr(rlu_ctx* h, const int64_t* rowptr, const int32_t* colind, const 
   h->pw.perm = h->perm_b;
   if (f64)
     rc = launch_lu_b<double>(reinterpret_cast<double*>(h->B), n, k, h->pw, h->blu, h->lu_block, h->status_dev,
-                             coop_sms(h), st);
+                             coop_sms(h), st, h->timing ? &h->ptimer[1] : nullptr);
   else
     rc = launch_lu_b<df32>(reinterpret_cast<df32*>(h->B), n, k, h->pw, h->blu, h->lu_block, h->status_dev,
-                           coop_sms(h), st);
+                           coop_sms(h), st, h->timing ? &h->ptimer[1] : nullptr);
   if (rc) return rc;
   if ((rc = mark(h, 8, st))) return rc;
   AssembleArgs aa{};
@@ -924,6 +929,9 @@ int rlu_destroy(rlu_t h) {
   }
   for (int i = 0; i <= kNumStages; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  for (PanelTimer& t : h->ptimer)
+    for (cudaEvent_t e : t.ev)
+      if (e) cudaEventDestroy(e);
   delete h;
   return RLU_OK;
 }
@@ -1072,6 +1080,9 @@ int rlu_debug_timing(rlu_t h, int on) {
   if (!h) return RLU_EINVAL;
   if (on && !h->ev[0])
     for (int i = 0; i <= kNumStages; ++i) RLU_CUDA_TRY(cudaEventCreate(&h->ev[i]));
+  if (on && !h->ptimer[0].ev[0])
+    for (PanelTimer& t : h->ptimer)
+      for (cudaEvent_t& e : t.ev) RLU_CUDA_TRY(cudaEventCreate(&e));
   h->timing = on ? 1 : 0;
   h->ev_recorded = 0;
   return RLU_OK;
@@ -1085,6 +1096,23 @@ int rlu_debug_stage_ms(rlu_t h, float* ms, int max_stages, int* count) {
   int cnt = max_stages < kNumStages ? max_stages : kNumStages;
   for (int i = 0; i < cnt; ++i) RLU_CUDA_TRY(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
   *count = cnt;
+  return RLU_OK;
+}
+
+int rlu_debug_lu_panels(rlu_t h, int which, int32_t* width, int32_t* launches, double* ms) {
+  if (!h || which < 0 || which > 1 || !width || !launches || !ms) return RLU_EINVAL;
+  if (!h->timing || !h->ev_recorded) return RLU_EINVAL;
+  const PanelTimer& t = h->ptimer[which];
+  RLU_CUDA_TRY(cudaEventSynchronize(h->ev[kNumStages]));
+  double tot = 0.0;
+  for (int i = 0; i < t.n; ++i) {
+    float x = 0.f;
+    RLU_CUDA_TRY(cudaEventElapsedTime(&x, t.ev[2 * i], t.ev[2 * i + 1]));
+    tot += x;
+  }
+  *width = t.width;
+  *launches = t.n;
+  *ms = tot;
   return RLU_OK;
 }
 

@@ -495,13 +495,27 @@ int choose_width(int64_t rows, int cols, const PivLuWs& pw, const BluWs& bw, int
   return b;
 }
 
+// One launch of the pivoted-LU kernel, between two timer events when timed.
+template <typename T>
+int timed_panel(T* X, int64_t rows, int wid, int64_t rs, int64_t cs, int j0, int cols, PivLuWs& pw,
+                unsigned int* status, int coop_sms, cudaStream_t st, PanelTimer* timer) {
+  const bool rec = timer && timer->n < kMaxPanels && timer->ev[2 * timer->n];
+  if (rec) RLU_CUDA_TRY(cudaEventRecord(timer->ev[2 * timer->n], st));
+  const int rc = launch_pivoted_lu_panel<T>(X, rows, wid, rs, cs, wid, j0, cols, pw, status, coop_sms, st);
+  if (rc) return rc;
+  if (rec) {
+    RLU_CUDA_TRY(cudaEventRecord(timer->ev[2 * timer->n + 1], st));
+    ++timer->n;
+  }
+  return RLU_OK;
+}
+
 template <typename T>
 int blocked_lu(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int b, PivLuWs& pw, const BluWs& bw,
-               unsigned int* status, int coop_sms, cudaStream_t st) {
+               unsigned int* status, int coop_sms, cudaStream_t st, PanelTimer* timer) {
   for (int j0 = 0; j0 < cols; j0 += b) {
     const int wid = cols - j0 < b ? cols - j0 : b;
-    int rc = launch_pivoted_lu_panel<T>(X + (int64_t)j0 * cs, rows, wid, rs, cs, wid, j0, cols, pw, status,
-                                        coop_sms, st);
+    int rc = timed_panel<T>(X + (int64_t)j0 * cs, rows, wid, rs, cs, j0, cols, pw, status, coop_sms, st, timer);
     if (rc) return rc;
     if (cols - j0 - wid == 0) break;
     switch (b) {
@@ -572,26 +586,35 @@ int blu_setup(BluWs& w, void* base, int64_t m, int64_t n, int k, int l, int num_
   return RLU_OK;
 }
 
-int launch_lu_y(double* Y, int64_t m, int l, PivLuWs& pw, const BluWs& bw, int block, unsigned int* status,
-                int coop_sms, cudaStream_t st) {
-  const int b = blu::choose_width(m, l, pw, bw, block, coop_sms);
+// The rows x cols LU of X (element (i, c) at X[i rs + c cs]), blocked or not.
+template <typename T>
+static int run_lu(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, PivLuWs& pw, const BluWs& bw, int block,
+                  unsigned int* status, int coop_sms, cudaStream_t st, PanelTimer* timer) {
+  const int b = blu::choose_width(rows, cols, pw, bw, block, coop_sms);
   if (b < 0) return RLU_EINVAL;
-  if (b == 0) return launch_pivoted_lu<double>(Y, m, l, l, 1, l, pw, status, coop_sms, st);
-  return blu::blocked_lu<double>(Y, m, l, l, 1, b, pw, bw, status, coop_sms, st);
+  if (timer) {
+    timer->n = 0;
+    timer->width = b;
+  }
+  if (b == 0) return blu::timed_panel<T>(X, rows, cols, rs, cs, 0, cols, pw, status, coop_sms, st, timer);
+  return blu::blocked_lu<T>(X, rows, cols, rs, cs, b, pw, bw, status, coop_sms, st, timer);
+}
+
+int launch_lu_y(double* Y, int64_t m, int l, PivLuWs& pw, const BluWs& bw, int block, unsigned int* status,
+                int coop_sms, cudaStream_t st, PanelTimer* timer) {
+  return run_lu<double>(Y, m, l, l, 1, pw, bw, block, status, coop_sms, st, timer);
 }
 
 template <typename T>
 int launch_lu_b(T* B, int64_t n, int k, PivLuWs& pw, const BluWs& bw, int block, unsigned int* status,
-                int coop_sms, cudaStream_t st) {
+                int coop_sms, cudaStream_t st, PanelTimer* timer) {
   // B^T (n x k): element (i, c) at B[c n + i]
-  const int b = blu::choose_width(n, k, pw, bw, block, coop_sms);
-  if (b < 0) return RLU_EINVAL;
-  if (b == 0) return launch_pivoted_lu<T>(B, n, k, 1, n, k, pw, status, coop_sms, st);
-  return blu::blocked_lu<T>(B, n, k, 1, n, b, pw, bw, status, coop_sms, st);
+  return run_lu<T>(B, n, k, 1, n, pw, bw, block, status, coop_sms, st, timer);
 }
 
 template int launch_lu_b<double>(double*, int64_t, int, PivLuWs&, const BluWs&, int, unsigned int*, int,
-                                 cudaStream_t);
-template int launch_lu_b<df32>(df32*, int64_t, int, PivLuWs&, const BluWs&, int, unsigned int*, int, cudaStream_t);
+                                 cudaStream_t, PanelTimer*);
+template int launch_lu_b<df32>(df32*, int64_t, int, PivLuWs&, const BluWs&, int, unsigned int*, int, cudaStream_t,
+                               PanelTimer*);
 
 }  // namespace rlu

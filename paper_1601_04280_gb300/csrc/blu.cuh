@@ -31,6 +31,15 @@ struct BluWs {
   bool ready;
 };
 
+// Device times of the panel launches of one LU (measurement hook): events
+// around each launch of the pivoted-LU kernel (one launch when unblocked).
+constexpr int kMaxPanels = 64;  // l <= 1024 in panels of 16 or more
+struct PanelTimer {
+  cudaEvent_t ev[2 * kMaxPanels] = {};
+  int n = 0;      // launches recorded
+  int width = 0;  // panel width, 0 when unblocked
+};
+
 size_t blu_workspace_bytes(int64_t m, int64_t n, int k, int l, int num_sms);
 // Carve the workspace; ready = false (the unblocked LUs run) when tensor maps
 // are unavailable or no panel fits.
@@ -42,13 +51,13 @@ int blu_setup(BluWs& w, void* base, int64_t m, int64_t n, int k, int l, int num_
 // the unblocked kernel), -1 forces the unblocked kernel, 16/32/64 force that
 // width.
 int launch_lu_y(double* Y, int64_t m, int l, PivLuWs& pw, const BluWs& bw, int block, unsigned int* status,
-                int coop_sms, cudaStream_t st);
+                int coop_sms, cudaStream_t st, PanelTimer* timer = nullptr);
 
 // B Q = L_b U_b by partial pivoting of B^T (n x k, element (i, c) at
 // B[c n + i]), k steps (step 6 of Algorithm 1), in FP64 or float-float; the
 // same choices of form and width as launch_lu_y.
 template <typename T>
 int launch_lu_b(T* B, int64_t n, int k, PivLuWs& pw, const BluWs& bw, int block, unsigned int* status,
-                int coop_sms, cudaStream_t st);
+                int coop_sms, cudaStream_t st, PanelTimer* timer = nullptr);
 
 }  // namespace rlu

@@ -35,6 +35,39 @@ def test_panel_lu_count_matches_the_algorithm(m, l):
     assert bench.algorithmic_flops_panel_lu(m, l) == counted_panel_lu_flops(m, l)
 
 
+def counted_blocked_panel_flops(m, l, b, seed=0):
+    """The operations inside the panels of a blocked partial-pivoted LU (panel
+    width b), counted one by one: each panel's steps on the rows not yet
+    pivoted and the panel's own columns (the trailing updates are counted
+    apart)."""
+    X = np.random.default_rng(seed).standard_normal((m, l))
+    flops = 0
+    for j0 in range(0, l, b):
+        wid = min(b, l - j0)
+        for j in range(j0, j0 + wid):
+            p = j + int(np.argmax(np.abs(X[j:, j])))
+            X[[j, p]] = X[[p, j]]
+            for i in range(j + 1, m):
+                X[i, j] /= X[j, j]
+                flops += 1
+                for c in range(j + 1, j0 + wid):
+                    X[i, c] -= X[i, j] * X[j, c]
+                    flops += 2
+        # trailing update of the columns right of the panel (not counted)
+        if j0 + wid < l:
+            L11 = np.tril(X[j0:j0 + wid, j0:j0 + wid], -1) + np.eye(wid)
+            X[j0:j0 + wid, j0 + wid:] = np.linalg.solve(L11, X[j0:j0 + wid, j0 + wid:])
+            X[j0 + wid:, j0 + wid:] -= X[j0 + wid:, j0:j0 + wid] @ X[j0:j0 + wid, j0 + wid:]
+    return flops
+
+
+@pytest.mark.parametrize("m,l,b", [(40, 10, 4), (33, 16, 16), (25, 9, 0), (50, 20, 8)])
+def test_panel_launch_count_matches_the_algorithm(m, l, b):
+    expect = counted_panel_lu_flops(m, l) if b == 0 else counted_blocked_panel_flops(m, l, b)
+    assert bench.algorithmic_flops_lu_panels(m, l, b) == expect
+    assert bench.lu_panels(l, b)[-1][0] + bench.lu_panels(l, b)[-1][1] == l
+
+
 def test_dense_fp32_workload_figures():
     w = ri.DENSE_F32_8K
     a_bytes = 4 * w.m * w.n
