@@ -41,8 +41,9 @@ namespace blu {
 constexpr int kD = 8;            // digits of 7 bits
 constexpr int kBM = 128;         // rows per tile (MMA M)
 constexpr int kNT = 32;          // columns per tile: two sets of 8 levels x 32 columns fill tensor memory
-constexpr int kThreads = 320;    // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;    // four per tensor-memory lane quarter
+constexpr int kEpiCols = kNT / (kEpiWarps / 4);  // columns of a tile per epilogue thread
+constexpr int kThreads = 64 + 32 * kEpiWarps;    // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 constexpr int kMaxStages = 4;
 constexpr uint32_t kTmemCols = 512;
 constexpr int32_t kSkip = INT_MIN;
@@ -260,7 +261,9 @@ __global__ void __launch_bounds__(256) k_l21(const T* __restrict__ X, int64_t rs
 // planes (nch chunks of KC columns).  Persistent: CTA b takes tiles b,
 // b + gridDim.x, ... (128 rows x 32 columns, column tile fastest); a ring of
 // nst stages runs across tiles; two accumulator sets let the epilogue of one
-// tile overlap the MMAs of the next.
+// tile overlap the MMAs of the next.  The epilogue (about a hundred integer
+// and FP64 instructions per entry) is issue- and latency-bound: sixteen warps,
+// each thread owning eight entries of one row.
 template <int KC, typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_digit_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t M,
@@ -362,21 +365,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) s_fail = 1;
     }
   } else {
-    // ---- epilogue (warps 2..9): lane quarter warp mod 4, column half (warp - 2) / 4 ----
-    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    // ---- epilogue (warps 2..): lane quarter warp mod 4, column group (warp - 2) / 4 ----
+    const int quarter = warp & 3, grp = (warp - 2) >> 2;
     int64_t local = 0;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
       const int b = (int)(local & 1);
       const int64_t row = (tile / nt) * kBM + quarter * 32 + lane;
-      const int cb = (int)(tile % nt) * kNT + half * 16;
-      // this thread's 16 entries of A22 and the column scales, loaded while
-      // the tile's products are still being computed
+      const int cb = (int)(tile % nt) * kNT + grp * kEpiCols;
+      // this thread's entries of A22 and the column scales, loaded while the
+      // tile's products are still being computed
       const int ea = row < M ? aexp[row] : kSkip;
       T* xr = X + row * rs;
-      T y[16];
-      int eb[16];
+      T y[kEpiCols];
+      int eb[kEpiCols];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < kEpiCols; ++i) {
         const int c = cb + i;
         const bool on = ea != kSkip && c < N;
         y[i] = on ? xr[(int64_t)c * cs] : zero_v<T>();
@@ -384,22 +387,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!tc::mbar_wait(&tfull[b], (uint32_t)((local >> 1) & 1))) { s_fail = 1; break; }
       tc::tc_fence_after();
-      const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * SET + (uint32_t)(half * 16);
+      const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * SET + (uint32_t)(grp * kEpiCols);
       // P = sum_{v <= 6} L_v 128^(6 - v) + floor(L_7 / 128): the product in
-      // units of 2^-56 of the two scales (|T| < 2^62.1 for b <= 64); the
+      // units of 2^-56 of the two scales (|P| < 2^62.1 for b <= 64); the
       // levels come in two batches of four loads with one wait each
-      long long P[16];
-      uint32_t v[4][16];
+      long long P[kEpiCols];
+      uint32_t v[4][kEpiCols];
 #pragma unroll
       for (int g = 0; g < 2; ++g) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) tc::tmem_ld16_issue(tq + (uint32_t)((4 * g + q) * kNT), v[q]);
+        for (int q = 0; q < 4; ++q) tc::tmem_ld8_issue(tq + (uint32_t)((4 * g + q) * kNT), v[q]);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int lv = 4 * g + q;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
+          for (int i = 0; i < kEpiCols; ++i) {
             const int L = level_int(__uint_as_float(v[q][i]));
             if (lv == 0) P[i] = L;
             else if (lv < kD - 1) P[i] = P[i] * 128 + L;
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
       if (ea != kSkip) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
+        for (int i = 0; i < kEpiCols; ++i)
           if (cb + i < N) xr[(int64_t)(cb + i) * cs] = sub(y[i], scaled_product(P[i], eb[i], y[i]));
       }
     }
