@@ -57,7 +57,6 @@ inline size_t smem_bytes(int ntile) {
 }
 
 enum { kEpiRows = 0, kEpiTransposed = 1 };
-constexpr int kMaxGramN = 16;  // columns per tile of the Gram product
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
   asm volatile(
@@ -318,15 +317,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0 && s_fail) set_flag(status, FLAG_TIMEOUT);
 }
 
-// Digit planes of Lk^T (k x ldm each) from Lk (m x k float-float, row-major),
-// unscaled: every column of Lk holds a 1 (its pivot row) and no entry above 1
-// in magnitude (partial pivoting), so its power-of-two scale is 2^0.  A 32 x 32
-// tile per CTA through shared memory; columns m .. ldm-1 are written as zeros.
+// Digit planes of Lk^T from Lk (m x k float-float, row-major), unscaled:
+// every column of Lk holds a 1 (its pivot row) and no entry above 1 in
+// magnitude (partial pivoting), so its power-of-two scale is 2^0.  Row c of
+// the output is column c of Lk packed by 32-row chunk, then digit:
+// dig[c][q D 32 + s 32 + r] = digit s of Lk[32 q + r][c] (ldm = m rounded up
+// to 32 rows; rows m .. ldm-1 are zeros).  A 32 x 32 tile per CTA through
+// shared memory.
 template <int D>
 __global__ void __launch_bounds__(256) k_digits_cols(int64_t m, int k, int64_t ldm, const df32* __restrict__ Lk,
                                                      __nv_bfloat16* __restrict__ dig) {
   __shared__ df32 t[32][33];
-  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int64_t r0 = (int64_t)blockIdx.x * 32;  // chunk q = blockIdx.x
   const int c0 = blockIdx.y * 32;
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
     const int64_t r = r0 + y;
@@ -334,57 +336,72 @@ __global__ void __launch_bounds__(256) k_digits_cols(int64_t m, int k, int64_t l
     t[y][threadIdx.x] = (r < m && c < k) ? Lk[r * k + c] : df_make(0.f, 0.f);
   }
   __syncthreads();
-  const int64_t plane = (int64_t)k * ldm;
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
     const int c = c0 + y;
-    const int64_t r = r0 + threadIdx.x;
-    if (c >= k || r >= ldm) continue;
+    if (c >= k) continue;
     const df32 v = t[threadIdx.x][y];
     __nv_bfloat16 d[D];
     digits<D>(v.hi, v.lo, 0, d);
+    __nv_bfloat16* row = dig + (int64_t)c * D * ldm + (int64_t)blockIdx.x * D * 32 + threadIdx.x;
 #pragma unroll
-    for (int s = 0; s < D; ++s) dig[s * plane + (int64_t)c * ldm + r] = d[s];
+    for (int s = 0; s < D; ++s) row[s * 32] = d[s];
   }
 }
 
-// G = Lk^T Lk (k x k) from D digit planes of Lk^T: work item = (row tile of
-// 128, column tile of ntile, split of the m-long contraction).  A split runs
-// over its rows in chunks of at most kGramChunk (exact FP32 level sums); the
-// MMAs of a chunk fill one of two TMEM accumulator sets while the epilogue
-// combines the previous chunk's levels (TwoSum) and adds them to float-float
-// running sums; after its last chunk an item writes its FP64 partial
-// part[split][c][c'].
-constexpr int kGramChunkKb = 7;  // 448 rows per exact chunk
+// G = Lk^T Lk (k x k) from the packed digit planes of Lk^T: work item = (row
+// tile of 128, column tile of 32, split of the m-long contraction); tiles
+// wholly below the diagonal are skipped (G is symmetric).  A pipeline stage
+// holds all D digits of a 32-row chunk of both operands (three 128-byte
+// boxes each for D = 6).  A split runs over its rows in exact chunks of at
+// most kGramExactQ x 32 rows (every level sum below 2^24): the MMAs of a
+// chunk fill one of two TMEM accumulator sets while the epilogue combines the
+// previous chunk's levels (TwoSum) and adds them to float-float running sums;
+// after its last chunk an item writes its FP64 partial part[split][c][c'].
+constexpr int kGramN = 32;       // columns per tile
+constexpr int kGramQ = 32;       // rows of Lk per pipeline stage
+constexpr int kGramExactQ = 14;  // 448 rows per exact chunk
+constexpr int kGramStages = 3;
+
+__host__ __device__ inline bool gram_tile_below(int im, int in) { return in * kGramN + kGramN - 1 < im * kBM; }
+
+template <int D>
+__host__ __device__ constexpr uint32_t gram_stage_bytes() {
+  return (uint32_t)(D * kGramQ / 64) * (uint32_t)(kBM * 128 + kGramN * 128);
+}
+
 template <int D>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_digit_gram(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t m,
-                 int k, int ntile, int tm, int tn, int S, int64_t kb_per_split, double* __restrict__ part,
-                 unsigned int* status) {
+    k_digit_gram(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int k, int tm,
+                 int tn, int S, int64_t nq, int64_t q_per_split, double* __restrict__ part, unsigned int* status) {
+  static_assert((D * kGramQ) % 64 == 0, "a stage is whole 128-byte boxes");
+  constexpr int NBOX = D * kGramQ / 64;
+  constexpr uint32_t ABOX = kBM * 128, BBOX = kGramN * 128;
+  constexpr uint32_t SB = gram_stage_bytes<D>();
+  constexpr uint32_t SET = D * kGramN;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2];
+  __shared__ __align__(8) uint64_t full[kGramStages], empty[kGramStages], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t nkb_all = cdiv(m, kBK);
   const int64_t items = (int64_t)tm * tn * S;
-  const uint32_t sb = stage_bytes<D>(ntile), bt = b_tile_bytes(ntile);
-  const uint32_t set_cols = (uint32_t)(D * ntile);
-  auto tileA = [&](int s, int d) { return smem + s * sb + d * kATile; };
-  auto tileB = [&](int s, int d) { return smem + s * sb + D * kATile + d * bt; };
-  // item -> (row tile, column tile, split) and its K-block range
-  auto decode = [&](int64_t item, int& it_m, int& it_n, int64_t& kb0, int64_t& kb1) {
+  auto boxA = [&](int s, int j) { return smem + (uint32_t)s * SB + (uint32_t)j * ABOX; };
+  auto boxB = [&](int s, int j) { return smem + (uint32_t)s * SB + NBOX * ABOX + (uint32_t)j * BBOX; };
+  // item -> (row tile, column tile, split) and its chunk range; false for a
+  // tile below the diagonal (every role skips it alike)
+  auto decode = [&](int64_t item, int& it_m, int& it_n, int64_t& q0, int64_t& q1) -> bool {
     const int sp = (int)(item / ((int64_t)tm * tn));
     const int rest = (int)(item - (int64_t)sp * tm * tn);
     it_m = rest / tn;
     it_n = rest - it_m * tn;
-    kb0 = (int64_t)sp * kb_per_split;
-    kb1 = min64(nkb_all, kb0 + kb_per_split);
+    q0 = (int64_t)sp * q_per_split;
+    q1 = min64(nq, q0 + q_per_split);
+    return !gram_tile_below(it_m, it_n) && q0 < q1;
   };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < kGramStages; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
@@ -411,54 +428,54 @@ __global__ void __launch_bounds__(kThreads, 1)
       int64_t it = 0;
       for (int64_t item = blockIdx.x; item < items && !s_fail; item += gridDim.x) {
         int im, in_;
-        int64_t kb0, kb1;
-        decode(item, im, in_, kb0, kb1);
-        for (int64_t kb = kb0; kb < kb1; ++kb, ++it) {
-          const int s = (int)(it % kStages);
-          if (it >= kStages && !tc::mbar_wait(&empty[s], (uint32_t)(((it / kStages) - 1) & 1))) {
+        int64_t q0, q1;
+        if (!decode(item, im, in_, q0, q1)) continue;
+        for (int64_t q = q0; q < q1; ++q, ++it) {
+          const int s = (int)(it % kGramStages);
+          if (it >= kGramStages && !tc::mbar_wait(&empty[s], (uint32_t)(((it / kGramStages) - 1) & 1))) {
             s_fail = 1;
             break;
           }
-          tc::mbar_arrive_expect_tx(&full[s], D * (kATile + bt));
-          for (int d = 0; d < D; ++d) {
-            tma_load_3d(tileA(s, d), &mapA, &full[s], (int)(kb * kBK), im * kBM, d);
-            tma_load_3d(tileB(s, d), &mapB, &full[s], (int)(kb * kBK), in_ * ntile, d);
+          tc::mbar_arrive_expect_tx(&full[s], SB);
+          for (int j = 0; j < NBOX; ++j) {
+            const int x = (int)(q * D * kGramQ) + j * 64;
+            tma_load_3d(boxA(s, j), &mapA, &full[s], x, im * kBM, 0);
+            tma_load_3d(boxB(s, j), &mapB, &full[s], x, in_ * kGramN, 0);
           }
         }
       }
-      for (int64_t j = it - kStages < 0 ? 0 : it - kStages; j < it; ++j)
-        if (!tc::mbar_wait(&full[j % kStages], (uint32_t)((j / kStages) & 1))) s_fail = 1;
+      for (int64_t j = it - kGramStages < 0 ? 0 : it - kGramStages; j < it; ++j)
+        if (!tc::mbar_wait(&full[j % kGramStages], (uint32_t)((j / kGramStages) & 1))) s_fail = 1;
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_bf16(kBM, ntile);
+      const uint32_t idesc = tc::idesc_bf16(kBM, kGramN);
       int64_t it = 0, unit = 0;
       bool ok = true;
       for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
         int im, in_;
-        int64_t kb0, kb1;
-        decode(item, im, in_, kb0, kb1);
-        for (int64_t c0 = kb0; c0 < kb1 && ok; c0 += kGramChunkKb, ++unit) {
+        int64_t q0, q1;
+        if (!decode(item, im, in_, q0, q1)) continue;
+        for (int64_t c0 = q0; c0 < q1 && ok; c0 += kGramExactQ, ++unit) {
           const int b = (int)(unit & 1);
           if (unit >= 2 && !tc::mbar_wait(&tempty[b], (uint32_t)(((unit >> 1) - 1) & 1))) { ok = false; break; }
           tc::tc_fence_after();
-          const int64_t c1 = min64(kb1, c0 + kGramChunkKb);
-          for (int64_t kb = c0; kb < c1; ++kb, ++it) {
-            const int s = (int)(it % kStages);
-            if (!tc::mbar_wait(&full[s], (uint32_t)((it / kStages) & 1))) { ok = false; break; }
+          const int64_t c1 = min64(q1, c0 + kGramExactQ);
+          for (int64_t q = c0; q < c1; ++q, ++it) {
+            const int s = (int)(it % kGramStages);
+            if (!tc::mbar_wait(&full[s], (uint32_t)((it / kGramStages) & 1))) { ok = false; break; }
             tc::tc_fence_after();
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk) {
-              const uint32_t koff = kk * 32;
-              const bool first = (kb == c0 && kk == 0);
+            for (int kk = 0; kk < kGramQ / 16; ++kk) {
 #pragma unroll
               for (int v = 0; v < D; ++v) {
-                const uint32_t dcol = tmem + (uint32_t)b * set_cols + (uint32_t)(v * ntile);
+                const uint32_t dcol = tmem + (uint32_t)b * SET + (uint32_t)(v * kGramN);
 #pragma unroll
                 for (int da = 0; da <= v; ++da) {
-                  const uint64_t aD = tc::sw128_desc(tc::smem_u32(tileA(s, da)) + koff);
-                  const uint64_t bD = tc::sw128_desc(tc::smem_u32(tileB(s, v - da)) + koff);
-                  tc::mma_bf16(dcol, aD, bD, idesc, (first && da == 0) ? 0u : 1u);
+                  const int ka = da * kGramQ + kk * 16, kb = (v - da) * kGramQ + kk * 16;
+                  const uint64_t aD = tc::sw128_desc(tc::smem_u32(boxA(s, ka >> 6)) + (uint32_t)(ka & 63) * 2u);
+                  const uint64_t bD = tc::sw128_desc(tc::smem_u32(boxB(s, kb >> 6)) + (uint32_t)(kb & 63) * 2u);
+                  tc::mma_bf16(dcol, aD, bD, idesc, (q == c0 && kk == 0 && da == 0) ? 0u : 1u);
                 }
               }
             }
@@ -475,42 +492,45 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
       int im, in_;
-      int64_t kb0, kb1;
-      decode(item, im, in_, kb0, kb1);
+      int64_t q0, q1;
+      if (!decode(item, im, in_, q0, q1)) continue;
       const int sp = (int)(item / ((int64_t)tm * tn));
-      float rh[kMaxGramN], rl[kMaxGramN];  // running float-float sums of this row's ntile columns
+      float rh[kGramN], rl[kGramN];  // running float-float sums of this row's columns
 #pragma unroll
-      for (int i = 0; i < kMaxGramN; ++i) rh[i] = rl[i] = 0.f;
-      for (int64_t c0 = kb0; c0 < kb1; c0 += kGramChunkKb, ++unit) {
+      for (int i = 0; i < kGramN; ++i) rh[i] = rl[i] = 0.f;
+      for (int64_t c0 = q0; c0 < q1; c0 += kGramExactQ, ++unit) {
         const int b = (int)(unit & 1);
         if (!tc::mbar_wait(&tfull[b], (uint32_t)((unit >> 1) & 1))) { s_fail = 1; ok = false; break; }
         tc::tc_fence_after();
-        const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * set_cols;
-        float v[D][kMaxGramN];
+        const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * SET;
 #pragma unroll
-        for (int lv = 0; lv < D; ++lv) tc::tmem_ld16(tq + (uint32_t)(lv * ntile), v[lv]);
+        for (int h = 0; h < kGramN / 16; ++h) {
+          float v[D][16];
+#pragma unroll
+          for (int lv = 0; lv < D; ++lv) tc::tmem_ld16(tq + (uint32_t)(lv * kGramN + h * 16), v[lv]);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const df32 head = two_sum(v[0][i] * 0x1p-14f, v[1][i] * 0x1p-21f);
+            float corr = 0.f;
+#pragma unroll
+            for (int lv = D - 1; lv >= 2; --lv) corr += v[lv][i] * ldexpf(1.f, -7 * (lv + 2));
+            const df32 chunk = quick_two_sum(head.hi, head.lo + corr);
+            const df32 acc = df_make(rh[h * 16 + i], rl[h * 16 + i]) + chunk;
+            rh[h * 16 + i] = acc.hi;
+            rl[h * 16 + i] = acc.lo;
+          }
+        }
         tc::tc_fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&tempty[b]);
-#pragma unroll
-        for (int i = 0; i < kMaxGramN; ++i) {
-          const df32 head = two_sum(v[0][i] * 0x1p-14f, v[1][i] * 0x1p-21f);
-          float corr = 0.f;
-#pragma unroll
-          for (int lv = D - 1; lv >= 2; --lv) corr += v[lv][i] * ldexpf(1.f, -7 * (lv + 2));
-          const df32 chunk = quick_two_sum(head.hi, head.lo + corr);
-          const df32 acc = df_make(rh[i], rl[i]) + chunk;
-          rh[i] = acc.hi;
-          rl[i] = acc.lo;
-        }
       }
       if (!ok) break;
       const int c = im * kBM + quarter * 32 + lane;
       if (c < k) {
         double* out = part + (int64_t)sp * k * k + (int64_t)c * k;
 #pragma unroll
-        for (int i = 0; i < kMaxGramN; ++i) {
-          const int c2 = in_ * ntile + i;
+        for (int i = 0; i < kGramN; ++i) {
+          const int c2 = in_ * kGramN + i;
           if (c2 < k) out[c2] = (double)rh[i] + (double)rl[i];
         }
       }
@@ -523,6 +543,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
   if (threadIdx.x == 0 && s_fail) set_flag(status, FLAG_TIMEOUT);
+}
+
+// G[c][c'] = the sum over the S splits of the partials, in split order; an
+// entry whose tile was skipped (below the diagonal) takes its transpose's.
+__global__ void k_sum_gram(int k, int S, const double* __restrict__ part, double* __restrict__ G) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)k * k) return;
+  const int r = (int)(e / k), c = (int)(e - (int64_t)r * k);
+  const int64_t src = gram_tile_below(r / kBM, c / kGramN) ? (int64_t)c * k + r : e;
+  double s = 0.0;
+  for (int z = 0; z < S; ++z) s += part[(int64_t)z * k * k + src];
+  G[e] = s;
 }
 
 // Columns per tile for N output columns: equal tiles, multiples of 16, at
@@ -561,7 +593,7 @@ constexpr int kDigG = 6;  // digits of the Gram product
 // the M-side planes: row layout (m x ldk) for L and W, transposed (k x ldm) for G
 size_t adig_bytes(int64_t m, int k) {
   const size_t rows = (size_t)kDigW * m * ltc_ldk(k) * 2;
-  const size_t cols = (size_t)kDigG * k * (size_t)(cdiv(m, 8) * 8) * 2;
+  const size_t cols = (size_t)kDigG * k * (size_t)(cdiv(m, 32) * 32) * 2;
   return a256(rows > cols ? rows : cols);
 }
 }  // namespace
@@ -577,7 +609,7 @@ int ltc_setup(LtcWs& w, void* base, int64_t m, int k, int num_sms) {
   w.k = k;
   w.num_sms = num_sms;
   w.ldk = ltc_ldk(k);
-  w.ldm = cdiv(m, 8) * 8;
+  w.ldm = cdiv(m, 32) * 32;
   unsigned char* b = (unsigned char*)base;
   w.adig = (__nv_bfloat16*)b;
   b += adig_bytes(m, k);
@@ -595,10 +627,10 @@ int ltc_setup(LtcWs& w, void* base, int64_t m, int k, int num_sms) {
       tc_encode_bf16_3d(w.mapBL, w.bdig, ldk, (uint64_t)k, kDigL, ldk, ltc::kBK, (uint32_t)w.ntileL) != RLU_OK ||
       tc_encode_bf16_3d(w.mapAW, w.adig, ldk, (uint64_t)m, kDigW, ldk, ltc::kBK, ltc::kBM) != RLU_OK ||
       tc_encode_bf16_3d(w.mapBW, w.bdig, ldk, (uint64_t)k, kDigW, ldk, ltc::kBK, (uint32_t)w.ntileW) != RLU_OK ||
-      tc_encode_bf16_3d(w.mapAG, w.adig, (uint64_t)w.ldm, (uint64_t)k, kDigG, (uint64_t)w.ldm, ltc::kBK,
+      tc_encode_bf16_3d(w.mapAG, w.adig, (uint64_t)kDigG * w.ldm, (uint64_t)k, 1, (uint64_t)kDigG * w.ldm, 64,
                         ltc::kBM) != RLU_OK ||
-      tc_encode_bf16_3d(w.mapBG, w.adig, (uint64_t)w.ldm, (uint64_t)k, kDigG, (uint64_t)w.ldm, ltc::kBK,
-                        ltc::kMaxGramN) != RLU_OK) {
+      tc_encode_bf16_3d(w.mapBG, w.adig, (uint64_t)kDigG * w.ldm, (uint64_t)k, 1, (uint64_t)kDigG * w.ldm, 64,
+                        ltc::kGramN) != RLU_OK) {
     cudaGetLastError();
     return RLU_OK;  // no tensor maps: the callers keep the SIMT products
   }
@@ -647,35 +679,39 @@ int launch_w_tc(const LtcWs& w, const df32* Ginv, const df32* Lk, float* W, __nv
                                                       status, w.num_sms, st);
 }
 
-int launch_gram_tc(const LtcWs& w, const df32* Lk, double* part, int max_splits, int* splits, unsigned int* status,
+int launch_gram_tc(const LtcWs& w, const df32* Lk, double* part, int max_splits, double* G, unsigned int* status,
                    cudaStream_t st) {
   if (!w.ready) return RLU_EINVAL;
   const int64_t m = w.m;
   const int k = w.k;
-  const dim3 gd((unsigned)cdiv(w.ldm, 32), (unsigned)cdiv(k, 32));
+  const dim3 gd((unsigned)(w.ldm / 32), (unsigned)cdiv(k, 32));
   ltc::k_digits_cols<kDigG><<<gd, dim3(32, 8), 0, st>>>(m, k, w.ldm, Lk, w.adig);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
-  const int tm = (int)cdiv(k, ltc::kBM), tn = (int)cdiv(k, ltc::kMaxGramN);
-  const int64_t nkb = cdiv(m, ltc::kBK);
+  const int tm = (int)cdiv(k, ltc::kBM), tn = (int)cdiv(k, ltc::kGramN);
+  int64_t kept = 0;
+  for (int im = 0; im < tm; ++im)
+    for (int in = 0; in < tn; ++in) kept += ltc::gram_tile_below(im, in) ? 0 : 1;
+  const int64_t nq = w.ldm / ltc::kGramQ;
   // splits: about two work items per SM, each at least one exact chunk deep
-  int64_t S = cdiv(2 * (int64_t)w.num_sms, (int64_t)tm * tn);
+  int64_t S = cdiv(2 * (int64_t)w.num_sms, kept);
   S = min64(S, (int64_t)max_splits);
-  S = min64(S, cdiv(nkb, ltc::kGramChunkKb));
+  S = min64(S, cdiv(nq, ltc::kGramExactQ));
   S = max64(S, 1);
-  const int64_t kbps = cdiv(nkb, S);
-  S = cdiv(nkb, kbps);
-  *splits = (int)S;
-  const size_t smem = ltc::smem_bytes<kDigG>(ltc::kMaxGramN);
+  const int64_t qps = cdiv(nq, S);
+  S = cdiv(nq, qps);
+  const size_t smem = (size_t)ltc::kGramStages * ltc::gram_stage_bytes<kDigG>() + 1024;
   auto kern = ltc::k_digit_gram<kDigG>;
   if (int rc = allow_dynamic_smem((const void*)kern, smem)) return rc;
   const int64_t items = (int64_t)tm * tn * S;
   const unsigned grid = (unsigned)min64(items, (int64_t)w.num_sms);
   kern<<<grid, ltc::kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap*>(w.mapAG),
-                                          *reinterpret_cast<const CUtensorMap*>(w.mapBG), m, k, ltc::kMaxGramN, tm,
-                                          tn, (int)S, kbps, part, status);
+                                          *reinterpret_cast<const CUtensorMap*>(w.mapBG), k, tm, tn, (int)S, nq, qps,
+                                          part, status);
   RLU_CUDA_TRY(cudaGetLastError());
-  note_launch();
+  ltc::k_sum_gram<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(k, (int)S, part, G);
+  RLU_CUDA_TRY(cudaGetLastError());
+  note_launch(2);
   return RLU_OK;
 }
 

@@ -21,7 +21,7 @@ struct LtcWs {
   int64_t m;
   int k;
   int64_t ldk;          // row stride of the planes (k rounded up to 8)
-  int64_t ldm;          // row stride of the transposed planes of the Gram product (m rounded up to 8)
+  int64_t ldm;          // rows of Lk in the Gram product's packed planes (m rounded up to 32)
   int ntileL, ntileW;   // columns per tile of the L and W products (multiples of 16)
   int num_sms;
   alignas(64) unsigned char mapAL[128];
@@ -47,10 +47,10 @@ int ltc_setup(LtcWs& w, void* base, int64_t m, int k, int num_sms);
 int launch_l_tc(const LtcWs& w, const df32* Lk, const int64_t* perm_y, const df32* Bp, const int64_t* perm_b,
                 int64_t n, float* L, unsigned int* status, cudaStream_t st);
 
-// G = Lk^T Lk (k x k) as six-digit products of Lk^T's digit planes, split
-// over the m rows: FP64 partials part[s][c][c'] for s < *splits (at most
-// max_splits); their sum is G.
-int launch_gram_tc(const LtcWs& w, const df32* Lk, double* part, int max_splits, int* splits, unsigned int* status,
+// G = Lk^T Lk (k x k, FP64) as six-digit products of Lk^T's digit planes,
+// split over the m rows (partials in part, at most max_splits x k x k) and
+// summed in split order; tiles below the diagonal come from their transposes.
+int launch_gram_tc(const LtcWs& w, const df32* Lk, double* part, int max_splits, double* G, unsigned int* status,
                    cudaStream_t st);
 
 // W (k x m, row-major FP32) = G^{-1} Lk^T with G^{-1} (k x k) and Lk (m x k)

@@ -329,13 +329,7 @@ int launch_gram(const PinvArgs& a, cudaStream_t st) {
     note_launch();
     if (a.ltc && a.ltc->ready) {
       // six-digit products on the tensor cores, FP64 partials per split of the rows
-      int Sg = 0;
-      if ((rc = launch_gram_tc(*a.ltc, Lk, a.gram_part, a.max_gram_splits, &Sg, a.status, st))) return rc;
-      k_sum_slices<double><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>((int64_t)k * k, Sg, a.gram_part,
-                                                                                a.G);
-      RLU_CUDA_TRY(cudaGetLastError());
-      note_launch();
-      return RLU_OK;
+      return launch_gram_tc(*a.ltc, Lk, a.gram_part, a.max_gram_splits, a.G, a.status, st);
     }
     // G is symmetric: only the tiles on and above the diagonal are computed
     rc = gemm_simt<df32, df32, double, df32>(st, k, k, m, Lk, 1, k, Lk, k, 1, a.gram_part, k, 1, S,
