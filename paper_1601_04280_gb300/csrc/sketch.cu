@@ -1401,11 +1401,33 @@ __global__ void __launch_bounds__(512) k_csr_densify(const int64_t* __restrict__
       for (int64_t c = threadIdx.x; c < n; c += blockDim.x) drow[c] = TV(0);
     __syncthreads();
     int inc = 1;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int c = colind[e];
-      if (c < 0 || (int64_t)c >= n) { bad_csr = true; continue; }
-      if (e > e0 && colind[e - 1] >= c) inc = 0;
-      drow[c] = val[e];
+    // eight independent entries per thread in flight: all loads, then the stores
+    constexpr int U = 8;
+    for (int64_t base = e0 + threadIdx.x; base < e1; base += (int64_t)blockDim.x * U) {
+      int cu[U], cp[U];
+      TV vu[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t e = base + (int64_t)u * blockDim.x;
+        if (e < e1) {
+          cu[u] = colind[e];
+          cp[u] = e > e0 ? colind[e - 1] : -1;
+          vu[u] = val[e];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t e = base + (int64_t)u * blockDim.x;
+        if (e < e1) {
+          const int c = cu[u];
+          if (c < 0 || (int64_t)c >= n) {
+            bad_csr = true;
+            continue;
+          }
+          if (cp[u] >= c) inc = 0;
+          drow[c] = vu[u];
+        }
+      }
     }
     if (!__syncthreads_and(inc)) {  // repeated or unordered columns: rebuild with sums
       for (int64_t c = threadIdx.x; c < n; c += blockDim.x) drow[c] = TV(0);
