@@ -220,39 +220,40 @@ __global__ void __launch_bounds__(256) k_u12(T* __restrict__ X, int64_t rs, int6
 
 // Digit planes of the multipliers L21 (panel columns j0 .. j0 + B - 1) of
 // every row of X with their scales; rows already pivoted get zero digits and
-// the skip mark.  One warp per row.
+// the skip mark.  min(B, 32) lanes per row (two rows per warp for B = 16).
 template <int B, typename T>
 __global__ void __launch_bounds__(256) k_l21(const T* __restrict__ X, int64_t rs, int64_t cs, int64_t m, int j0,
                                              const int32_t* __restrict__ pstep, __nv_bfloat16* __restrict__ adig,
                                              int32_t* __restrict__ aexp) {
   constexpr int KC = chunk_of(B);
-  constexpr int R = (B + 31) / 32;
-  const int lane = threadIdx.x & 31;
-  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (r >= m) return;
-  const bool skip = pstep[r] >= 0;
+  constexpr int LPR = B < 32 ? B : 32;  // lanes per row
+  constexpr int R = B / LPR;
+  const int lane = threadIdx.x & 31, sub_ = lane % LPR;
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LPR;
+  const bool valid = r < m;  // every lane stays for the shuffles
+  const bool skip = !valid || pstep[valid ? r : 0] >= 0;
   T x[R];
   int e = kNoExp;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    const int i = lane + 32 * q;
-    x[q] = (!skip && i < B) ? X[r * rs + (int64_t)(j0 + i) * cs] : zero_v<T>();
+    const int i = sub_ + LPR * q;
+    x[q] = !skip ? X[r * rs + (int64_t)(j0 + i) * cs] : zero_v<T>();
     e = max(e, exp_of(x[q]));
   }
-  e = __reduce_max_sync(0xffffffffu, e);
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
   if (e == kNoExp) e = 0;
-  if (lane == 0) aexp[r] = skip ? kSkip : e;
+  if (!valid) return;
+  if (sub_ == 0) aexp[r] = skip ? kSkip : e;
   __nv_bfloat16* row = adig + r * (kD * B);
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    const int i = lane + 32 * q;
-    if (i < B) {
-      int d[kD];
-      digits8(x[q], e, d);
-      const int base = (i / KC) * kD * KC + (i % KC);
+    const int i = sub_ + LPR * q;
+    int d[kD];
+    digits8(x[q], e, d);
+    const int base = (i / KC) * kD * KC + (i % KC);
 #pragma unroll
-      for (int s = 0; s < kD; ++s) row[base + s * KC] = __int2bfloat16_rn(d[s]);
-    }
+    for (int s = 0; s < kD; ++s) row[base + s * KC] = __int2bfloat16_rn(d[s]);
   }
 }
 
@@ -367,24 +368,30 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---- epilogue (warps 2..): lane quarter warp mod 4, column group (warp - 2) / 4 ----
     const int quarter = warp & 3, grp = (warp - 2) >> 2;
+    // this thread's entries of A22 and its row's scale for a tile: loaded one
+    // tile ahead, so their latency overlaps the previous tile's work
+    T yn[kEpiCols];
+    int ean = kSkip;
+    auto prefetch = [&](int64_t tile) {
+      const int64_t row = (tile / nt) * kBM + quarter * 32 + lane;
+      const int cb = (int)(tile % nt) * kNT + grp * kEpiCols;
+      ean = (tile < tiles && row < M) ? aexp[row] : kSkip;
+      const T* xr = X + row * rs;
+#pragma unroll
+      for (int i = 0; i < kEpiCols; ++i)
+        yn[i] = (ean != kSkip && cb + i < N) ? xr[(int64_t)(cb + i) * cs] : zero_v<T>();
+    };
+    prefetch(blockIdx.x);
     int64_t local = 0;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
       const int b = (int)(local & 1);
       const int64_t row = (tile / nt) * kBM + quarter * 32 + lane;
       const int cb = (int)(tile % nt) * kNT + grp * kEpiCols;
-      // this thread's entries of A22 and the column scales, loaded while the
-      // tile's products are still being computed
-      const int ea = row < M ? aexp[row] : kSkip;
-      T* xr = X + row * rs;
+      const int ea = ean;
       T y[kEpiCols];
-      int eb[kEpiCols];
 #pragma unroll
-      for (int i = 0; i < kEpiCols; ++i) {
-        const int c = cb + i;
-        const bool on = ea != kSkip && c < N;
-        y[i] = on ? xr[(int64_t)c * cs] : zero_v<T>();
-        eb[i] = on ? ea + bexp[c] - 56 : 0;
-      }
+      for (int i = 0; i < kEpiCols; ++i) y[i] = yn[i];
+      prefetch(tile + gridDim.x);
       if (!tc::mbar_wait(&tfull[b], (uint32_t)((local >> 1) & 1))) { s_fail = 1; break; }
       tc::tc_fence_after();
       const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * SET + (uint32_t)(grp * kEpiCols);
@@ -414,9 +421,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
       if (ea != kSkip) {
+        T* xr = X + row * rs;
 #pragma unroll
-        for (int i = 0; i < kEpiCols; ++i)
-          if (cb + i < N) xr[(int64_t)(cb + i) * cs] = sub(y[i], scaled_product(P[i], eb[i], y[i]));
+        for (int i = 0; i < kEpiCols; ++i) {
+          const int c = cb + i;
+          if (c < N) xr[(int64_t)c * cs] = sub(y[i], scaled_product(P[i], ea + bexp[c] - 56, y[i]));
+        }
       }
     }
   }
@@ -456,7 +466,8 @@ int trailing(T* X, int64_t rows, int cols, int64_t rs, int64_t cs, int j0, const
   const int wt = cols - j0 - B;
   k_u12<B, T><<<(unsigned)cdiv(wt, 8), 256, 0, st>>>(X, rs, cs, j0, wt, pw.perm, w.bdig, w.bexp);
   RLU_CUDA_TRY(cudaGetLastError());
-  k_l21<B, T><<<(unsigned)cdiv(rows * 32, 256), 256, 0, st>>>(X, rs, cs, rows, j0, pw.pstep, w.adig, w.aexp);
+  k_l21<B, T><<<(unsigned)cdiv(rows * (B < 32 ? B : 32), 256), 256, 0, st>>>(X, rs, cs, rows, j0, pw.pstep, w.adig,
+                                                                             w.aexp);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch(2);
   constexpr int KC = chunk_of(B);
