@@ -1752,7 +1752,9 @@ int launch_sketch_dense(const void* A, int64_t lda, int dtype, bool acc64, int64
     return launch_dense_cfg<double, double, 1024, 16, 2>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
   }
   if (acc64) return RLU_EINVAL;
+  // l1 <= 1024: one bucket of 16 rows per thread (each bucket-list read serves 16 rows)
   if (dtype == RLU_F32) {
+    if (l1 <= 1024) return launch_dense_cfg<float, float, 1024, 1, 16>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
     if (l1 <= 2048) return launch_dense_cfg<float, float, 1024, 2, 8>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
     if (l1 <= 4096) return launch_dense_cfg<float, float, 1024, 4, 8>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
     if (l1 <= 8192) return launch_dense_cfg<float, float, 1024, 8, 4>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
@@ -1760,6 +1762,7 @@ int launch_sketch_dense(const void* A, int64_t lda, int dtype, bool acc64, int64
   }
   if (dtype == RLU_BF16) {
     using B = __nv_bfloat16;
+    if (l1 <= 1024) return launch_dense_cfg<B, float, 1024, 1, 16>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
     if (l1 <= 2048) return launch_dense_cfg<B, float, 1024, 2, 8>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
     if (l1 <= 4096) return launch_dense_cfg<B, float, 1024, 4, 8>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
     if (l1 <= 8192) return launch_dense_cfg<B, float, 1024, 8, 4>(A, lda, m, n, l1, l, ws, Y, rowmap, status, num_sms, st);
