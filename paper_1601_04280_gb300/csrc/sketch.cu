@@ -1571,8 +1571,9 @@ int launch_scan_i32(int64_t count, const int32_t* cnt, int32_t* start, int64_t* 
     note_launch();
     return RLU_OK;
   }
-  // at least 8 rounds of 1024 values per CTA, at most kScanMaxParts CTAs
-  const int64_t per = max64(8192, cdiv(cdiv(max64(count, 1), kScanMaxParts), 1024) * 1024);
+  // rounds of 1024 values, as few per CTA as kScanMaxParts CTAs allow (the
+  // rounds of one CTA run one after another)
+  const int64_t per = max64(1024, cdiv(cdiv(max64(count, 1), kScanMaxParts), 1024) * 1024);
   const int64_t parts = max64(1, cdiv(count, per));
   k_scan_part<<<(unsigned)parts, 1024, 0, st>>>(count, per, cnt, tmp);
   k_scan_final<<<(unsigned)parts, 1024, 0, st>>>(count, per, cnt, tmp, start);
