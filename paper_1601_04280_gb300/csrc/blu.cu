@@ -368,29 +368,55 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---- epilogue (warps 2..): lane quarter warp mod 4, column group (warp - 2) / 4 ----
     const int quarter = warp & 3, grp = (warp - 2) >> 2;
-    // this thread's entries of A22 and its row's scale for a tile: loaded one
+    // Row-major X (cs == 1): this warp's 32 x 8 block of A22 is read and
+    // written row-contiguously (lane -> row 4 it + lane / 8, column lane % 8:
+    // four 64-byte row pieces per instruction) and turned around through a
+    // 32 x 9 staging block in shared memory, because a thread owns a row in
+    // tensor memory and row-per-lane accesses cost a transaction per row.
+    // Otherwise (B^T) the lanes' rows are adjacent in memory already.
+    const bool rowmaj = (cs == 1);
+    T* stg = reinterpret_cast<T*>(smem + (uint32_t)nst * SB) + (warp - 2) * 32 * 9;
+    const int sr = lane >> 3, sc = lane & 7;
+    // this warp's entries of A22 and its rows' scales for a tile: loaded one
     // tile ahead, so their latency overlaps the previous tile's work
     T yn[kEpiCols];
     int ean = kSkip;
     auto prefetch = [&](int64_t tile) {
-      const int64_t row = (tile / nt) * kBM + quarter * 32 + lane;
+      const int64_t rbase = (tile / nt) * kBM + quarter * 32;
       const int cb = (int)(tile % nt) * kNT + grp * kEpiCols;
-      ean = (tile < tiles && row < M) ? aexp[row] : kSkip;
-      const T* xr = X + row * rs;
+      ean = (tile < tiles && rbase + lane < M) ? aexp[rbase + lane] : kSkip;
+      if (rowmaj) {
 #pragma unroll
-      for (int i = 0; i < kEpiCols; ++i)
-        yn[i] = (ean != kSkip && cb + i < N) ? xr[(int64_t)(cb + i) * cs] : zero_v<T>();
+        for (int it = 0; it < kEpiCols; ++it) {
+          const int64_t r = rbase + it * 4 + sr;
+          yn[it] = (tile < tiles && r < M && cb + sc < N) ? X[r * rs + cb + sc] : zero_v<T>();
+        }
+      } else {
+        const T* xr = X + (rbase + lane) * rs;
+#pragma unroll
+        for (int i = 0; i < kEpiCols; ++i)
+          yn[i] = (ean != kSkip && cb + i < N) ? xr[(int64_t)(cb + i) * cs] : zero_v<T>();
+      }
     };
     prefetch(blockIdx.x);
     int64_t local = 0;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
       const int b = (int)(local & 1);
-      const int64_t row = (tile / nt) * kBM + quarter * 32 + lane;
+      const int64_t rbase = (tile / nt) * kBM + quarter * 32;
       const int cb = (int)(tile % nt) * kNT + grp * kEpiCols;
       const int ea = ean;
       T y[kEpiCols];
+      if (rowmaj) {
 #pragma unroll
-      for (int i = 0; i < kEpiCols; ++i) y[i] = yn[i];
+        for (int it = 0; it < kEpiCols; ++it) stg[(it * 4 + sr) * 9 + sc] = yn[it];
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < kEpiCols; ++i) y[i] = stg[lane * 9 + i];
+        __syncwarp();
+      } else {
+#pragma unroll
+        for (int i = 0; i < kEpiCols; ++i) y[i] = yn[i];
+      }
       prefetch(tile + gridDim.x);
       if (!tc::mbar_wait(&tfull[b], (uint32_t)((local >> 1) & 1))) { s_fail = 1; break; }
       tc::tc_fence_after();
@@ -420,8 +446,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
-      if (ea != kSkip) {
-        T* xr = X + row * rs;
+      if (rowmaj) {
+        // results by row into the staging block, then out row-contiguously
+        // (rows already pivoted are not written)
+#pragma unroll
+        for (int i = 0; i < kEpiCols; ++i) {
+          const int c = cb + i;
+          stg[lane * 9 + i] = (ea != kSkip && c < N) ? sub(y[i], scaled_product(P[i], ea + bexp[c] - 56, y[i])) : y[i];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < kEpiCols; ++it) {
+          const int rr = it * 4 + sr;
+          const int64_t r = rbase + rr;
+          const int ear = __shfl_sync(0xffffffffu, ea, rr);
+          if (ear != kSkip && r < M && cb + sc < N) X[r * rs + cb + sc] = stg[rr * 9 + sc];
+        }
+        __syncwarp();
+      } else if (ea != kSkip) {
+        T* xr = X + (rbase + lane) * rs;
 #pragma unroll
         for (int i = 0; i < kEpiCols; ++i) {
           const int c = cb + i;
@@ -444,7 +487,7 @@ int launch_update(const BluWs& w, int wi, int64_t M, int N, int nch, T* Xt, int6
                   unsigned int* status, cudaStream_t st) {
   constexpr uint32_t SB = stage_bytes<KC>();
   const int nst = (int)min64(kMaxStages, (int64_t)(200 * 1024) / SB);
-  const size_t smem = (size_t)nst * SB + 1024;
+  const size_t smem = (size_t)nst * SB + (size_t)kEpiWarps * 32 * 9 * sizeof(T) + 1024;  // stages, staging blocks
   auto kern = k_digit_update<KC, T>;
   if (int rc = allow_dynamic_smem((const void*)kern, smem)) return rc;
   const int nt = (int)cdiv(N, kNT);
