@@ -145,10 +145,37 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
   const int64_t base = (int64_t)blockIdx.x * kRadixThreads * it;
+  // the keys of the first kPre rounds are loaded before the rounds start (the
+  // rounds are separated by block barriers, so a load issued inside a round
+  // waits out its full latency)
+  constexpr int kPre = 8;
+  int kpre[kPre], rpre[kPre];
+  TV vpre[kPre];
+#pragma unroll
+  for (int r = 0; r < kPre; ++r) {
+    const int64_t e = base + (int64_t)r * kRadixThreads + tid;
+    const bool ok = r < it && e < N;
+    kpre[r] = ok ? kin[e] : 0;
+    rpre[r] = ok ? rin[e] : 0;
+    vpre[r] = ok ? vin[e] : TV(0);
+  }
   for (int r = 0; r < it; ++r) {
     const int64_t e = base + (int64_t)r * kRadixThreads + tid;
     const bool valid = e < N;
-    const int kv = valid ? kin[e] : 0;
+    int kv = 0, rv = 0;
+    TV vv = TV(0);
+#pragma unroll
+    for (int q = 0; q < kPre; ++q)
+      if (q == r) {
+        kv = kpre[q];
+        rv = rpre[q];
+        vv = vpre[q];
+      }
+    if (r >= kPre && valid) {
+      kv = kin[e];
+      rv = rin[e];
+      vv = vin[e];
+    }
     const int d = valid ? ((kv >> shift) & 255) : 256 + lane;  // lanes without an entry never match
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int rank = __popc(peers & lt);
@@ -158,8 +185,8 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
       int dest = run[d] + rank;
       for (int w = 0; w < warp; ++w) dest += wc[w][d];
       kout[dest] = kv;
-      rout[dest] = rin[e];
-      vout[dest] = vin[e];
+      rout[dest] = rv;
+      vout[dest] = vv;
     }
     __syncthreads();
     int tot = 0;
