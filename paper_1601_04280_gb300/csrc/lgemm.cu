@@ -263,12 +263,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---- epilogue (warps 2..5): TMEM lane quarter = warp mod 4 ----
     const int quarter = warp & 3;
+    // rows layout: each 32 x 16 piece goes out through a staging block in
+    // shared memory (a thread owns a row in tensor memory; lanes writing their
+    // own rows would cost a transaction per row), two 64-byte row pieces per
+    // store instruction
+    float* stg = reinterpret_cast<float*>(smem + (uint32_t)kStages * sb) + (warp - 2) * 32 * 17;
     int64_t local = 0;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
       const int b = (int)(local & 1);
       if (!tc::mbar_wait(&tfull[b], (uint32_t)((local >> 1) & 1))) { s_fail = 1; break; }
       tc::tc_fence_after();
-      const int64_t row = (tile / nt) * kBM + quarter * 32 + lane;
+      const int64_t rbase = (tile / nt) * kBM + quarter * 32;
+      const int64_t row = rbase + lane;
       const int col0 = (int)(tile % nt) * ntile;
       const int ea = row < M ? aexp[row] : 0;
       const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * set_cols;
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int lv = D - 1; lv >= 2; --lv) corr += v[lv][i] * ldexpf(1.f, -7 * (lv + 2));
           const float r = (row < M) ? ldexpf(sum.hi + (sum.lo + corr), ea + bexp[c]) : 0.f;
           if (EPI == kEpiRows) {
-            if (row < M) eo.out[row * eo.ldo + c] = r;
+            stg[lane * 17 + i] = r;
           } else {
             if (row < M) eo.out[(int64_t)c * eo.ldo + row] = r;
             if (eo.pl[0] && row < eo.ldp) {
@@ -301,6 +307,16 @@ __global__ void __launch_bounds__(kThreads, 1)
               eo.pl[2][o] = __float2bfloat16_rn(r1 - __bfloat162float(h2));
             }
           }
+        }
+        if (EPI == kEpiRows) {
+          __syncwarp();
+#pragma unroll
+          for (int it = 0; it < 16; ++it) {
+            const int rr = it * 2 + (lane >> 4), cc = lane & 15;
+            const int c = col0 + c0 + cc;
+            if (rbase + rr < M && c < N) eo.out[(rbase + rr) * eo.ldo + c] = stg[rr * 17 + cc];
+          }
+          __syncwarp();
         }
       }
       tc::tc_fence_before();
@@ -568,7 +584,8 @@ inline int tile_cols(int N, int D) {
 template <int D, int EPI>
 int launch_gemm(const void* mapA, const void* mapB, int64_t M, int N, int K, int ntile, const int32_t* aexp,
                 const int32_t* bexp, const EpiOut& eo, unsigned int* status, int num_sms, cudaStream_t st) {
-  const size_t smem = smem_bytes<D>(ntile);
+  // the rows layout's staging blocks (four epilogue warps, 32 x 17 floats each) after the stages
+  const size_t smem = smem_bytes<D>(ntile) + (EPI == kEpiRows ? (size_t)4 * 32 * 17 * sizeof(float) : 0);
   auto kern = k_digit_gemm<D, EPI>;
   if (int rc = allow_dynamic_smem((const void*)kern, smem)) return rc;
   const int nt = (int)cdiv(N, ntile);
