@@ -360,6 +360,15 @@ int rlu_debug_lu_Y(rlu_t h, double* Y_host, int64_t* perm_host);
  * timed factorization yet), RLU_ECUDA. */
 int rlu_debug_lu_panels(rlu_t h, int which, int32_t* width, int32_t* launches, double* ms);
 
+/* Test hook: how the tensor-core product B = W A (step 6 of Algorithm 1)
+ * reads a BF16 A.  on = 1 (the default): by TMA, as it lies in memory (the
+ * MMA's A operand MN-major), whenever A's base address and row stride are
+ * multiples of 16 bytes; on = 0: by the converter warps (global loads into
+ * the K-major swizzled layout), the form used for FP32 A and unaligned BF16
+ * A.  Both forms issue the same products in the same order.
+ * Errors: RLU_EINVAL (null handle, on not 0 or 1). */
+int rlu_debug_set_tma_a(rlu_t h, int on);
+
 /* The block setting of rlu_debug_set_lu_block (return value) and, in
  * *block_max (may be null), the widest panel this handle's workspace holds
  * (0: the blocked form is unavailable).  RLU_EINVAL for a null handle. */

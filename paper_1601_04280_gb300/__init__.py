@@ -34,7 +34,7 @@ C_SYMBOLS = ("rlu_create", "rlu_create_in", "rlu_set_precision", "rlu_workspace_
              "rlu_graph_destroy", "rlu_copy_block_async", "rlu_set_max_ctas",
              "rlu_debug_recip", "rlu_set_second_sketch", "rlu_debug_status_of_flags", "rlu_debug_wait_timeout",
              "rlu_debug_alu_peak", "rlu_set_transform", "rlu_set_column_pivoting", "rlu_debug_set_lu_block",
-             "rlu_debug_lu_block", "rlu_debug_lu_Y", "rlu_debug_lu_panels")
+             "rlu_debug_lu_block", "rlu_debug_lu_Y", "rlu_debug_lu_panels", "rlu_debug_set_tma_a")
 
 #: stage names reported by rlu_debug_stage_ms, in order
 STAGES = ("params", "sketch", "panel_lu", "gram", "chol", "wform", "bgemm", "lu_b", "assemble")
@@ -94,6 +94,7 @@ def load(reload=False):
         "rlu_debug_set_lu_block": ([vp, c.c_int32], c.c_int),
         "rlu_debug_lu_block": ([vp, c.POINTER(c.c_int32)], c.c_int),
         "rlu_debug_lu_Y": ([vp, vp, vp], c.c_int),
+        "rlu_debug_set_tma_a": ([vp, c.c_int], c.c_int),
         "rlu_debug_lu_panels": ([vp, c.c_int, c.POINTER(c.c_int32), c.POINTER(c.c_int32), c.POINTER(c.c_double)],
                                 c.c_int),
     }
@@ -149,6 +150,10 @@ def rlu_set_column_pivoting(h, on):
 
 def rlu_debug_set_lu_block(h, block):
     return _check(load().rlu_debug_set_lu_block(h, int(block)), "rlu_debug_set_lu_block")
+
+
+def rlu_debug_set_tma_a(h, on):
+    return _check(load().rlu_debug_set_tma_a(h, int(on)), "rlu_debug_set_tma_a")
 
 
 def rlu_debug_lu_block(h):
@@ -319,6 +324,10 @@ class RandLU:
     def set_lu_block(self, block):
         """Panel width of the LU of the sketch: 0 automatic, -1 unblocked, 16/32/64."""
         rlu_debug_set_lu_block(self.h, block)
+
+    def set_tma_a(self, on):
+        """BF16 A of B = W A fed by TMA where aligned (True, the default) or by the converter warps."""
+        rlu_debug_set_tma_a(self.h, 1 if on else 0)
 
     def set_max_ctas(self, max_ctas):
         """Bound the CTAs of the grid-synchronised kernels (0: one per SM)."""

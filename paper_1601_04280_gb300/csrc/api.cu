@@ -873,6 +873,12 @@ int rlu_debug_set_lu_block(rlu_t h, int32_t block) {
   return RLU_OK;
 }
 
+int rlu_debug_set_tma_a(rlu_t h, int on) {
+  if (!h || (on != 0 && on != 1)) return RLU_EINVAL;
+  h->tcw.a_tma = on != 0;
+  return RLU_OK;
+}
+
 int rlu_debug_lu_block(rlu_t h, int32_t* block_max) {
   if (!h) return RLU_EINVAL;
   if (block_max) *block_max = h->blu.ready ? h->blu.bmax : 0;

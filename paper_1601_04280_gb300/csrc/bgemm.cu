@@ -88,6 +88,7 @@ int tc_setup(TcWs& w, void* base, int64_t m, int64_t n, int k, int num_sms) {
   for (int q = 0; q < 3; ++q) w.wp[q] = (__nv_bfloat16*)(b + q * plane);
   w.part = (float*)(b + 3 * plane);
   w.ready = false;
+  w.a_tma = true;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return RLU_OK;  // no tensor-map support: the caller uses the SIMT path
   for (int q = 0; q < 3; ++q) {
@@ -130,11 +131,33 @@ __global__ void k_sum_parts(int64_t kn, int S, const float* __restrict__ part, d
   B[e] = acc;
 }
 
+// TMA descriptor of BF16 A (m rows x n columns, row stride lda) in boxes of 64
+// columns x 64 rows with the 128-byte swizzle: the MN-major operand tiles of
+// k_bgemm_tc.  False when A's base or row stride is not 16-byte aligned.
+static bool encode_a_bf16(CUtensorMap* map, const __nv_bfloat16* A, int64_t lda, int64_t m, int64_t n) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc || ((uintptr_t)A & 15) || (lda & 7) || lda < n) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+  cuuint64_t strides[1] = {(cuuint64_t)(lda * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)(tc::kBM / 2), (cuuint32_t)tc::kBK};
+  cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(A), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename TA>
 static int launch_cfg(const TcWs& w, int wplanes, const TA* A, int64_t lda, int64_t m, int64_t n, int k,
                       int64_t kps, int splits, unsigned int* status, cudaStream_t st) {
   constexpr int P = std::is_same<TA, float>::value ? 2 : 1;
   const TcPlan& p = w.plan;
+  const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(w.map);
+  CUtensorMap tmA = maps[0];  // unused unless A is fed by TMA
+  int a_tma = 0;
+  if constexpr (P == 1) {
+    if (w.a_tma && encode_a_bf16(&tmA, A, lda, m, n)) a_tma = 1;
+    else tmA = maps[0];
+  }
   int dev = 0, optin = 0;
   RLU_CUDA_TRY(cudaGetDevice(&dev));
   RLU_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -142,10 +165,9 @@ static int launch_cfg(const TcWs& w, int wplanes, const TA* A, int64_t lda, int6
   const size_t smem = tc::smem_bytes(P, wplanes, p.npad, nst);
   auto kern = tc::k_bgemm_tc<TA>;
   if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
-  dim3 grid((unsigned)cdiv(n, tc::kBM), (unsigned)splits, (unsigned)p.nz);
-  const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(w.map);
-  kern<<<grid, tc::kThreads, smem, st>>>(maps[0], maps[1], maps[2], wplanes, A, lda, m, n, k, p.npad, kps, w.part,
-                                         status, nst);
+  dim3 grid((unsigned)(cdiv(n, tc::kBM) * p.nz), (unsigned)splits, 1);
+  kern<<<grid, tc::kThreads, smem, st>>>(maps[0], maps[1], maps[2], tmA, a_tma, wplanes, A, lda, m, n, k, p.npad,
+                                         p.nz, kps, w.part, status, nst);
   RLU_CUDA_TRY(cudaGetLastError());
   note_launch();
   return RLU_OK;

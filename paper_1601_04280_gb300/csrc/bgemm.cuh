@@ -23,6 +23,7 @@ struct TcWs {
   alignas(64) unsigned char map[3][128];  // TMA descriptors of the planes
   int num_sms;
   bool ready;
+  bool a_tma;  // BF16 A fed by TMA where its alignment allows (else by the converter warps)
 };
 
 void tc_plan(int64_t m, int64_t n, int k, int num_sms, TcPlan& p);

@@ -9,17 +9,20 @@
 //   W = W1 + W2 + W3, three BF16 planes (24 significant bits), prepared once
 //     per factorization and fed by TMA (128-byte swizzle, K-major).
 //   A = A1 + A2, two BF16 pieces (16 bits) formed on chip from FP32 A, or A1
-//     alone when A is stored in BF16.
+//     alone when A is stored in BF16; BF16 A with 16-byte aligned rows is
+//     fed by TMA as it lies in memory (MN-major: the 128 columns of a tile
+//     are contiguous in each row of A).
 //   D += W1 A1 + W2 A1 + W3 A1 + W1 A2 + W2 A2 (the products of order <= 2^-16).
 // The rounding of A to 16 bits enters B as W dA, whose effect on L_y B is the
 // projection of dA onto range(L_y); W's rounding is amplified by cond(L_y),
 // so W keeps 24 bits.
 //
-// Warp roles (320 threads): warp 0 = TMA producer for the W planes, warp 1 =
-// TMEM owner and single-thread MMA issuer, warps 2..9 = two groups of four
-// converters of A into the K-major swizzled BF16 layout (group g takes the
-// k-blocks kb = g mod 2, so the global loads of two k-blocks are in flight at
-// once), then the epilogue (TMEM -> registers -> FP32 split-K partials in
+// Warp roles (320 threads): warp 0 = TMA producer for the W planes (and for
+// A when A is fed by TMA), warp 1 = TMEM owner and single-thread MMA issuer,
+// warps 2..9 = two groups of four converters of A into the K-major swizzled
+// BF16 layout (group g takes the k-blocks kb = g mod 2, so the global loads
+// of two k-blocks are in flight at once; idle when TMA feeds A), then the
+// epilogue (TMEM -> registers -> FP32 split-K partials in
 // global memory, each group half of the columns).  A k-block is 64 rows of A;
 // two to four pipeline stages.  Every mbarrier wait is bounded; on timeout the kernel
 // raises FLAG_TIMEOUT, drains and frees its tensor memory, and returns.
@@ -95,6 +98,19 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;                         // swizzle mode: 128 B
   return d;
 }
+// Shared-memory matrix descriptor: MN-major, 128-byte swizzle.  Each 128-byte
+// row holds 64 consecutive MN elements of one K index, 8 K rows form a
+// 1024-byte swizzle atom; `lbo` = bytes between 64-element MN blocks, `sbo` =
+// bytes between 8-row K groups.
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
 // Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4)                    // D format: F32
@@ -103,6 +119,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          | ((uint32_t)(N >> 3) << 17) // N
          | ((uint32_t)(M >> 4) << 24);// M
 }
+// The same with A MN-major (the transpose-A bit).
+__host__ __device__ constexpr uint32_t idesc_bf16_amn(int M, int N) { return idesc_bf16(M, N) | (1u << 15); }
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
@@ -186,15 +204,18 @@ struct ALoader<__nv_bfloat16> {
   }
 };
 
-// Grid: x = column tile of A (128 columns), y = split of the m rows (kps rows
-// each), z = block of npad rows of W (of B).  part[y][c][j] (c < k, j < n)
-// receives the FP32 partial sum of that split.  wplanes: BF16 planes of W used.
+// Grid: x = (column tile of A (128 columns)) * nz + (block of npad rows of W,
+// of B), so the nz CTAs that read one tile of A run side by side and share it
+// through L2; y = split of the m rows (kps rows each, a multiple of 64).
+// part[y][c][j] (c < k, j < n) receives the FP32 partial sum of that split.
+// wplanes: BF16 planes of W used.  a_tma (BF16 A only): A fed by TMA through
+// tmA (boxes of 64 columns x 64 rows, 128-byte swizzle, zeros outside A).
 template <typename TA>
 __global__ void __launch_bounds__(kThreads, 1)
     k_bgemm_tc(const __grid_constant__ CUtensorMap tmW1, const __grid_constant__ CUtensorMap tmW2,
-               const __grid_constant__ CUtensorMap tmW3, int wplanes, const TA* __restrict__ A, int64_t lda,
-               int64_t m, int64_t n, int k, int npad, int64_t kps, float* __restrict__ part, unsigned int* status,
-               int nst) {
+               const __grid_constant__ CUtensorMap tmW3, const __grid_constant__ CUtensorMap tmA, int a_tma,
+               int wplanes, const TA* __restrict__ A, int64_t lda, int64_t m, int64_t n, int k, int npad, int nz,
+               int64_t kps, float* __restrict__ part, unsigned int* status, int nst) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_w[kMaxStages], full_a[kMaxStages], empty[kMaxStages], accum_full;
@@ -202,12 +223,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t j0 = (int64_t)blockIdx.x * kBM;
-  const int crow0 = blockIdx.z * npad;  // first row of W (of B) handled here
+  const int64_t j0 = (int64_t)(blockIdx.x / nz) * kBM;
+  const int crow0 = (int)(blockIdx.x % nz) * npad;  // first row of W (of B) handled here
   const int64_t kbeg = (int64_t)blockIdx.y * kps;
   const int64_t kend = min64(m, kbeg + kps);
   const int nkb = (int)cdiv(kend - kbeg, kBK);
   constexpr int P = ALoader<TA>::kPieces;
+  const bool atma = P == 1 && a_tma != 0;
   const uint32_t wbytes = w_tile_bytes(npad);
 
   if (threadIdx.x == 0) {
@@ -236,18 +258,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto stageW = [&](int s, int plane) { return smem + s * sbytes + P * kATile + plane * w_tile_bytes(npad); };
 
   if (warp == 0) {
-    // ---- TMA producer: W planes ----
+    // ---- TMA producer: W planes (and A: two boxes of 64 columns) ----
     if (lane == 0) {
       int issued = 0;
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % nst;
         if (kb >= nst && !mbar_wait(&empty[s], ((kb / nst) - 1) & 1)) { s_fail = 1; break; }
         if (s_fail) break;
-        mbar_arrive_expect_tx(&full_w[s], wbytes * wplanes);
+        mbar_arrive_expect_tx(&full_w[s], wbytes * wplanes + (atma ? kATile : 0u));
         const int x = (int)(kbeg + (int64_t)kb * kBK);
         tma_load_2d(stageW(s, 0), &tmW1, &full_w[s], x, crow0);
         if (wplanes > 1) tma_load_2d(stageW(s, 1), &tmW2, &full_w[s], x, crow0);
         if (wplanes > 2) tma_load_2d(stageW(s, 2), &tmW3, &full_w[s], x, crow0);
+        if (atma) {
+          tma_load_2d(stageA(s, 0), &tmA, &full_w[s], (int)j0, x);
+          tma_load_2d(stageA(s, 0) + kATile / 2, &tmA, &full_w[s], (int)j0 + kBM / 2, x);
+        }
         issued = kb + 1;
       }
       // drain: every issued load has landed before the CTA may exit
@@ -257,18 +283,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kBM, npad);
+      const uint32_t idesc = atma ? idesc_bf16_amn(kBM, npad) : idesc_bf16(kBM, npad);
       bool ok = true;
       for (int kb = 0; kb < nkb && ok; ++kb) {
         const int s = kb % nst;
         const uint32_t par = (kb / nst) & 1;
-        if (!mbar_wait(&full_w[s], par) || !mbar_wait(&full_a[s], par)) { ok = false; break; }
+        if (!mbar_wait(&full_w[s], par) || (!atma && !mbar_wait(&full_a[s], par))) { ok = false; break; }
         tc_fence_after();
         const uint32_t a1 = smem_u32(stageA(s, 0)), a2 = smem_u32(stageA(s, P - 1));
 #pragma unroll
         for (int kk = 0; kk < kBK / 16; ++kk) {
           const uint32_t koff = kk * 32;  // 16 BF16 = 32 bytes along K inside the swizzle atom
-          const uint64_t dA1 = sw128_desc(a1 + koff), dA2 = sw128_desc(a2 + koff);
+          // MN-major A: 16 K rows = two 1024-byte atoms; the two 64-column boxes kATile / 2 apart
+          const uint64_t dA1 = atma ? sw128_mn_desc(a1 + kk * 2048u, kATile / 2, 1024u) : sw128_desc(a1 + koff);
+          const uint64_t dA2 = sw128_desc(a2 + koff);
           uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
           for (int q = 0; q < wplanes; ++q) {
             const uint64_t dW = sw128_desc(smem_u32(stageW(s, q)) + koff);
@@ -297,6 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // the loads are in flight while the tensor cores finish the stage's
     // previous k-block
     TA vals[kBK];
+    const int nkb_conv = atma ? 0 : nkb;  // nothing to convert when TMA feeds A
     auto load_kb = [&](int kb) {
       const int64_t k0 = kbeg + (int64_t)kb * kBK;
 #pragma unroll
@@ -305,8 +334,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         vals[e] = (row < kend && j < n) ? A[row * lda + j] : (TA)0.f;
       }
     };
-    if (grp < nkb) load_kb(grp);
-    for (int kb = grp; kb < nkb; kb += kConvGroups) {
+    if (grp < nkb_conv) load_kb(grp);
+    for (int kb = grp; kb < nkb_conv; kb += kConvGroups) {
       const int s = kb % nst;
       if (kb >= nst && !mbar_wait(&empty[s], ((kb / nst) - 1) & 1)) { s_fail = 1; break; }
       if (s_fail) break;
@@ -323,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       fence_proxy_async();
       mbar_arrive(&full_a[s]);
-      if (kb + kConvGroups < nkb) load_kb(kb + kConvGroups);
+      if (kb + kConvGroups < nkb_conv) load_kb(kb + kConvGroups);
     }
     // ---- epilogue: TMEM -> FP32 partials part[y][c][j] ----
     const bool ok = mbar_wait(&accum_full, 0);
