@@ -131,6 +131,175 @@ __global__ void k_sum_parts(int64_t kn, int S, const float* __restrict__ part, d
   B[e] = acc;
 }
 
+namespace tc {
+
+// The persistent form of the product for BF16 A fed by TMA (one or two W
+// planes): one CTA per SM walks the tiles t = blockIdx.x, blockIdx.x +
+// gridDim.x, ..., where tile t is W block z = t mod nz, column tile x =
+// (t / nz) mod xt and split y = t / (nz xt) (the CTAs running at one time
+// share their W rows and, across z, their A tiles in L2).  The stage ring runs
+// on from tile to tile, and the tile's FP32 sums alternate between two
+// accumulators in tensor memory (columns 0 and 256), so the epilogue of one
+// tile overlaps the products of the next.  Products and their order within a
+// tile are those of k_bgemm_tc.  Warps: 0 = TMA producer, 1 = TMEM owner and
+// MMA issuer, 2..9 = epilogue (two groups of four, each half of the columns).
+// Every wait is bounded; on timeout the kernel raises FLAG_TIMEOUT.
+constexpr int kEpiWarpsP = 8;
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_bgemm_tc_persist(const __grid_constant__ CUtensorMap tmW1, const __grid_constant__ CUtensorMap tmW2,
+                       const __grid_constant__ CUtensorMap tmA, int wplanes, int64_t m, int64_t n, int k, int npad,
+                       int nz, int64_t xt, int64_t kps, int splits, float* __restrict__ part,
+                       unsigned int* status, int nst) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (int64_t)nz * xt * splits;
+  const uint32_t wbytes = w_tile_bytes(npad);
+  const uint32_t sbytes = stage_bytes(1, wplanes, npad);
+  auto stageA = [&](int s) { return smem + (size_t)s * sbytes; };
+  auto stageW = [&](int s, int q) { return smem + (size_t)s * sbytes + kATile + (size_t)q * wbytes; };
+  // tile t: W block z, first column j0 of A, split y with its rows kbeg.. and k-blocks
+  auto tile = [&](int64_t t, int& z, int64_t& j0, int& y, int64_t& kbeg, int& nkb) {
+    z = (int)(t % nz);
+    const int64_t r = t / nz;
+    j0 = (r % xt) * kBM;
+    y = (int)(r / xt);
+    kbeg = (int64_t)y * kps;
+    nkb = (int)cdiv(min64(m, kbeg + kps) - kbeg, kBK);
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kEpiWarpsP);
+    }
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(2 * kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  volatile int* fail = &s_fail;
+
+  if (warp == 0) {
+    // ---- TMA producer ----
+    if (lane == 0) {
+      int64_t it = 0;  // k-blocks issued so far (all tiles)
+      for (int64_t t = blockIdx.x; t < ntiles && !*fail; t += gridDim.x) {
+        int z, y, nkb;
+        int64_t j0, kbeg;
+        tile(t, z, j0, y, kbeg, nkb);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % nst);
+          if (it >= nst && !mbar_wait(&empty[s], (uint32_t)((it / nst) - 1) & 1)) { *fail = 1; break; }
+          if (*fail) break;
+          mbar_arrive_expect_tx(&full[s], wbytes * wplanes + kATile);
+          const int x = (int)(kbeg + (int64_t)kb * kBK);
+          tma_load_2d(stageW(s, 0), &tmW1, &full[s], x, z * npad);
+          if (wplanes > 1) tma_load_2d(stageW(s, 1), &tmW2, &full[s], x, z * npad);
+          tma_load_2d(stageA(s), &tmA, &full[s], (int)j0, x);
+          tma_load_2d(stageA(s) + kATile / 2, &tmA, &full[s], (int)j0 + kBM / 2, x);
+        }
+      }
+      // drain: every issued load has landed before the CTA may exit
+      for (int64_t q = it > nst ? it - nst : 0; q < it; ++q)
+        if (!mbar_wait(&full[q % nst], (uint32_t)(q / nst) & 1)) *fail = 1;
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16_amn(kBM, npad);
+      int64_t it = 0;
+      int i = 0;  // tiles of this CTA so far
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        int z, y, nkb;
+        int64_t j0, kbeg;
+        tile(t, z, j0, y, kbeg, nkb);
+        const int b = i & 1;
+        // accumulator b is free once the epilogue has read tile i - 2 out of it
+        if (i >= 2 && !mbar_wait(&tempty[b], (uint32_t)((i >> 1) - 1) & 1)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t acc_t = tmem + (uint32_t)(b * kTmemCols);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % nst);
+          if (!mbar_wait(&full[s], (uint32_t)(it / nst) & 1)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a1 = smem_u32(stageA(s));
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint64_t dA = sw128_mn_desc(a1 + kk * 2048u, kATile / 2, 1024u);
+            uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+            for (int q = 0; q < wplanes; ++q) {
+              mma_bf16(acc_t, dA, sw128_desc(smem_u32(stageW(s, q)) + kk * 32u), idesc, acc);
+              acc = 1u;
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[b]);
+      }
+      if (!ok) *fail = 1;
+    }
+  } else {
+    // ---- epilogue: accumulator -> FP32 partials part[y][c][j] ----
+    const int grp = (warp - 2) >> 2;  // column half
+    const int quarter = warp & 3;     // TMEM lanes 32*quarter .. +31
+    const int nch = npad / 16, half = (nch + 1) / 2;
+    const int cb = grp == 0 ? 0 : half * 16, ce = grp == 0 ? half * 16 : npad;
+    int i = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      int z, y, nkb;
+      int64_t j0, kbeg;
+      tile(t, z, j0, y, kbeg, nkb);
+      const int b = i & 1;
+      if (!mbar_wait(&tfull[b], (uint32_t)(i >> 1) & 1)) { *fail = 1; break; }
+      tc_fence_after();
+      if (*fail) break;
+      const int64_t jj = j0 + quarter * 32 + lane;
+      float* out = part + (int64_t)y * k * n;
+      for (int c0 = cb; c0 < ce; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTmemCols + c0), v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int c = z * npad + c0 + e;
+          if (c < k && jj < n) out[(int64_t)c * n + jj] = v[e];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols) : "memory");
+  }
+  if (threadIdx.x == 0 && s_fail) set_flag(status, FLAG_TIMEOUT);
+}
+
+}  // namespace tc
+
 // TMA descriptor of BF16 A (m rows x n columns, row stride lda) in boxes of 64
 // columns x 64 rows with the 128-byte swizzle: the MN-major operand tiles of
 // k_bgemm_tc.  False when A's base or row stride is not 16-byte aligned.
@@ -164,6 +333,19 @@ static int launch_cfg(const TcWs& w, int wplanes, const TA* A, int64_t lda, int6
   const int nst = tc::stages_for(P, wplanes, p.npad, (size_t)optin - 2048);  // room for the static barriers
   const size_t smem = tc::smem_bytes(P, wplanes, p.npad, nst);
   auto kern = tc::k_bgemm_tc<TA>;
+  if (a_tma && wplanes <= 2) {
+    // persistent: one CTA per SM over every (W block, column tile, split)
+    auto pk = tc::k_bgemm_tc_persist;
+    if (int rc_ = allow_dynamic_smem((const void*)pk, smem)) return rc_;
+    const int64_t xt = cdiv(n, tc::kBM);
+    const int64_t ntiles = xt * p.nz * splits;
+    const unsigned g = (unsigned)min64(ntiles, (int64_t)w.num_sms);
+    pk<<<g, tc::kThreads, smem, st>>>(maps[0], maps[1], tmA, wplanes, m, n, k, p.npad, p.nz, xt, kps, splits,
+                                      w.part, status, nst);
+    RLU_CUDA_TRY(cudaGetLastError());
+    note_launch();
+    return RLU_OK;
+  }
   if (int rc_ = allow_dynamic_smem((const void*)kern, smem)) return rc_;
   dim3 grid((unsigned)(cdiv(n, tc::kBM) * p.nz), (unsigned)splits, 1);
   kern<<<grid, tc::kThreads, smem, st>>>(maps[0], maps[1], maps[2], tmA, a_tma, wplanes, A, lda, m, n, k, p.npad,

@@ -6,7 +6,9 @@ in the same order into FP32 accumulators, so B agrees to FP32 rounding at
 most (in practice bit for bit); a wrong descriptor, swizzle or box offset
 moves whole entries of B.  The shapes cover W in one and in two blocks of
 rows, a last column tile of 80 columns (second 64-column box partly outside
-A) and one of 40 (second box wholly outside), and one or two W planes."""
+A) and one of 40 (second box wholly outside), and one, two or three W planes.
+With one or two planes the TMA form runs persistent (one CTA per SM over all
+tiles, two accumulators in tensor memory)."""
 import numpy as np
 import pytest
 
@@ -41,6 +43,7 @@ def factor_B(rg, A, k, l, l1, seed, prec, tma):
 @pytest.mark.parametrize("m,n,k,l,l1,prec", [
     (3000, 2000, 60, 80, 640, "bf16_refine"),   # one W block; last tile 80 columns
     (3000, 2000, 60, 80, 640, "bf16"),          # one W plane
+    (3000, 2000, 60, 80, 640, "f32"),           # three W planes (the non-persistent kernel)
     (5000, 1960, 300, 320, 1600, "bf16_refine"),  # two W blocks of 160 rows; last tile 40 columns
 ])
 def test_tma_feed_equals_converters(rg, m, n, k, l, l1, prec):
@@ -58,7 +61,7 @@ def test_tma_feed_equals_converters(rg, m, n, k, l, l1, prec):
     e_o = oracle.relative_residual(A.astype(np.float64), o.L, o.U, o.p, o.q)
     for g in (t, c):
         e_g = oracle.relative_residual(A.astype(np.float64), g["L"], g["U"], g["p"], g["q"])
-        assert e_g <= (1.05 if prec == "bf16_refine" else 2.0) * e_o, (e_g, e_o)
+        assert e_g <= (2.0 if prec == "bf16" else 1.05) * e_o, (e_g, e_o)
 
 
 def test_tma_switch_validation(rg):
