@@ -32,6 +32,10 @@ __host__ __device__ __forceinline__ int status_of_flags(unsigned int f) {
 
 // Spin limit for every device wait: about a second at GB300 clocks.
 constexpr long long kSpinLimitCycles = 2000000000ll;
+// A spinning wait also reads the status word (to leave once another block has
+// timed out) on one poll in 16 (mask 15), so its polls of the awaited word are
+// one L2 round trip apart rather than two.
+constexpr unsigned int kStatusPollEvery = 15u;
 
 __device__ __forceinline__ void set_flag(unsigned int* status, unsigned int bit) {
   atomicOr(status, bit);
@@ -55,7 +59,8 @@ __device__ __forceinline__ void red_release_gpu_add(unsigned int* p, unsigned in
 // at zero for the launch; barrier number e (1, 2, ...) waits until all
 // gridDim.x blocks have arrived e times.  The wait is bounded: on timeout it
 // sets FLAG_TIMEOUT and returns false, and the caller must leave the kernel.
-// Once any block has timed out, every later barrier returns false at once.
+// Once any block has timed out, every later barrier returns false within 16
+// polls.
 __device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int epoch,
                                              unsigned int* status) {
   __shared__ int s_ok;
@@ -65,10 +70,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int
     const unsigned int target = epoch * gridDim.x;
     long long t0 = clock64();
     int ok = 1;
-    while (true) {
+    for (unsigned int it = 0;; ++it) {
       unsigned int v = ld_acquire_gpu(counter);
       if ((int)(v - target) >= 0) break;
-      if (ld_acquire_gpu(status) & FLAG_TIMEOUT) { ok = 0; break; }
+      if ((it & kStatusPollEvery) == kStatusPollEvery && (ld_acquire_gpu(status) & FLAG_TIMEOUT)) { ok = 0; break; }
       if (clock64() - t0 > kSpinLimitCycles) {
         set_flag(status, FLAG_TIMEOUT);
         ok = 0;
@@ -95,10 +100,10 @@ __device__ __forceinline__ bool grid_wait(unsigned int* counter, unsigned int ep
     const unsigned int target = epoch * gridDim.x;
     long long t0 = clock64();
     int ok = 1;
-    while (true) {
+    for (unsigned int it = 0;; ++it) {
       unsigned int v = ld_acquire_gpu(counter);
       if ((int)(v - target) >= 0) break;
-      if (ld_acquire_gpu(status) & FLAG_TIMEOUT) { ok = 0; break; }
+      if ((it & kStatusPollEvery) == kStatusPollEvery && (ld_acquire_gpu(status) & FLAG_TIMEOUT)) { ok = 0; break; }
       if (clock64() - t0 > kSpinLimitCycles) {
         set_flag(status, FLAG_TIMEOUT);
         ok = 0;
