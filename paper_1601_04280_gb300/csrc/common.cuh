@@ -32,9 +32,9 @@ __host__ __device__ __forceinline__ int status_of_flags(unsigned int f) {
 
 // Spin limit for every device wait: about a second at GB300 clocks.
 constexpr long long kSpinLimitCycles = 2000000000ll;
-// A spinning wait also reads the status word (to leave once another block has
-// timed out) on one poll in 16 (mask 15), so its polls of the awaited word are
-// one L2 round trip apart rather than two.
+// A spinning grid barrier also reads the status word (to leave once another
+// block has timed out) on one poll in 16 (mask 15), so its polls of the
+// awaited counter are one L2 round trip apart rather than two.
 constexpr unsigned int kStatusPollEvery = 15u;
 
 __device__ __forceinline__ void set_flag(unsigned int* status, unsigned int bit) {

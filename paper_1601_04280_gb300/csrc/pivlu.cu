@@ -215,13 +215,10 @@ __global__ void __launch_bounds__(NT) k_pivoted_lu(T* __restrict__ X, int64_t ro
       if (lane == 0) {
         const unsigned int target = (unsigned)(j + 1) * (unsigned)G;
         const long long t0 = clock64();
-        for (unsigned int it = 0;; ++it) {
+        while (true) {
           const unsigned int v = ld_acquire_gpu(bar);
           if ((int)(v - target) >= 0) break;
-          if ((it & kStatusPollEvery) == kStatusPollEvery && (ld_acquire_gpu(status) & FLAG_TIMEOUT)) {
-            ok = 0;
-            break;
-          }
+          if (ld_acquire_gpu(status) & FLAG_TIMEOUT) { ok = 0; break; }
           if (clock64() - t0 > kSpinLimitCycles) { set_flag(status, FLAG_TIMEOUT); ok = 0; break; }
         }
       }
